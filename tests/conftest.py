@@ -1,0 +1,28 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a); runs the CUDA path through the C-ABI")
+    config.addinivalue_line("markers", "slow: long-running; still part of its marker's suite")
+
+
+@pytest.fixture(scope="session")
+def oracle_mod():
+    import oracle
+
+    return oracle
+
+
+@pytest.fixture(scope="session")
+def k0():
+    import kernel0
+
+    kernel0.lib()
+    return kernel0
