@@ -1,0 +1,415 @@
+"""Benchmark of the PageRank pipeline hot path on GB300.
+
+One step = Kernel 1 (sort) + Kernel 2 (build/filter/normalise) + Kernel 3
+(20 PageRank iterations, binary32 ranks) on one synthetic Kronecker graph
+of scale 24 (N = 2^24 vertices, M = 2^28 edges, initiator
+0.57/0.19/0.19/0.05), with the edge list already resident in HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  `value` is the whole-pipeline rate M / (time of one
+K1+K2+K3 step), summed over ranks; per-kernel rates (K1: M/t, K2: M/t, K3:
+20 M/t, as the paper defines them) are under "kernels".  With --gpus N > 1
+(launched by torchrun) every rank runs its own independent graph (different
+seed): weak scaling, no collective on the data path.
+
+--impl reference times the CPU oracle (single thread) on a bounded sample of
+the same workload instead.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "K3 PageRank edges/s and K1-K3 edges/s at scale 24; FP32 vs FP64 at L1 err<=1e-6"
+SCALE = 24
+ITERS = 20
+DAMPING = 0.85
+SEED = 1
+WORKLOAD = ("Kronecker graph, scale 24 (N=2^24, M=16N=268,435,456 edges, initiator A/B/C/D=0.57/0.19/0.19/0.05, "
+            "seeded Philox), Kernel 1 sort + Kernel 2 filter/normalise + Kernel 3 20 damped iterations (c=0.85)")
+
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from an ncu capture
+# (profiles/), valid only while the kernel's source file is unchanged.
+TRAFFIC = {}
+
+
+def _sha(path):
+    with open(os.path.join(ROOT, path), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=5)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def k3_bytes_per_iter(nnz, N, dtype):
+    """Algorithmic bytes of one Kernel 3 iteration: packed entries, column ends,
+    one read of each gathered x, 1/d_out, the new x."""
+    xs = {"fp64": 8, "fp32": 4, "bf16": 2}[dtype]
+    inv = 8 if dtype == "fp64" else 4
+    return 4 * nnz + 4 * N + xs * N + inv * N + xs * N
+
+
+def k1_bytes(M, scale):
+    P = -(-2 * scale // 8)
+    return M * (8 + 16 * P), P
+
+
+def k2_bytes(M, N, nnz0, nnz, scale):
+    P2 = -(-scale // 8)
+    b = 8 * M + 8 * nnz0 + 16 * N          # unique pass: read edges, write entries, degree words
+    b += 12 * N + 17 * N                   # max reduction; mask + column pointers + d_out reset
+    b += 8 * nnz0 + N + 8 * N              # pre-pass: entries, mask, d_out
+    if P2 == 1:
+        b += 8 * nnz0 + 4 * nnz
+    else:
+        b += 8 * nnz0 + 8 * nnz + 16 * nnz * (P2 - 2) + 12 * nnz
+    b += 16 * N                            # 1/d_out in two precisions
+    return b
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import kernel0
+    import paper_1603_01876_gb300 as pp
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    scale, iters = args.scale, ITERS
+    N = 1 << scale
+    M = 16 * N
+    seed = SEED + rank
+    u, v = kernel0.edges_device(scale, seed, device=dev)
+    r0h = kernel0.r0_host(N, seed)
+    r0 = torch.from_numpy(r0h).to(dev)
+    us = torch.empty_like(u)
+    vs = torch.empty_like(v)
+    g = pp.Graph(M, scale, dev)
+    ws_bytes = max(pp.workspace_bytes("sort", M, scale), pp.workspace_bytes("build", M, scale),
+                   pp.workspace_bytes("pagerank", M, scale, iters, "fp64"))
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    r_out = torch.empty(N, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(ev=None, dtype=args.dtype, out=r_out):
+        if ev:
+            ev[0].record(stream)
+        pp.sort_edges(u, v, scale, out=(us, vs), workspace=ws)
+        if ev:
+            ev[1].record(stream)
+        pp.build_filter_normalize(us, vs, scale, "lowest", graph=g, workspace=ws)
+        if ev:
+            ev[2].record(stream)
+        pp.pagerank(g, r0, iters, DAMPING, dtype, out=out, workspace=ws)
+        if ev:
+            ev[3].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    err = pp.last_device_error()
+    if err:
+        raise RuntimeError("device error word %#x during warm-up" % err)
+    info = g.info_dict()
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = pp.launch_count()
+    with ClockSampler(local) as clocks:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for k in range(args.steps):
+            step(evs[k])
+        t1.record(stream)
+        torch.cuda.synchronize()
+    launches = pp.launch_count() - launches0
+    total_ms = t0.elapsed_time(t1)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    k1 = [e[0].elapsed_time(e[1]) for e in evs]
+    k2 = [e[1].elapsed_time(e[2]) for e in evs]
+    k3 = [e[2].elapsed_time(e[3]) for e in evs]
+    err = pp.last_device_error()
+    if err:
+        raise RuntimeError("device error word %#x in the timed region" % err)
+    ms_step = total_ms / args.steps
+
+    # Kernel 3 in binary64 on the same graph, and the binary32 error against it
+    r64 = torch.empty(N, dtype=torch.float64, device=dev)
+    pp.pagerank(g, r0, iters, DAMPING, "fp64", out=r64, workspace=ws)
+    torch.cuda.synchronize()
+    ev64 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev64[0].record(stream)
+    for _ in range(3):
+        pp.pagerank(g, r0, iters, DAMPING, "fp64", out=r64, workspace=ws)
+    ev64[1].record(stream)
+    torch.cuda.synchronize()
+    k3_64 = ev64[0].elapsed_time(ev64[1]) / 3
+    d = (r_out.double() - r64).abs()
+    l1_fp32 = float(d.sum() / r64.abs().sum())
+    maxrel_fp32 = float((d / r64.abs()).max())
+
+    # end to end through the host-buffer entry point
+    uh = u.cpu().pin_memory()
+    vh = v.cpu().pin_memory()
+    r0p = torch.from_numpy(r0h).pin_memory()
+    rh = torch.empty(N, dtype=torch.float32).pin_memory()
+    infoh = torch.zeros(pp.INFO_LEN, dtype=torch.int64).pin_memory()
+    del ws
+    torch.cuda.empty_cache()
+    pws = torch.empty(pp.workspace_bytes("pipeline", M, scale, iters, args.dtype), dtype=torch.uint8, device=dev)
+    pp.pipeline_host(uh, vh, scale, r0p, iters, DAMPING, args.dtype, out=rh, info=infoh, workspace=pws)
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 5))
+    te = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    te[0].record(stream)
+    for _ in range(e2e_steps):
+        pp.pipeline_host(uh, vh, scale, r0p, iters, DAMPING, args.dtype, out=rh, info=infoh, workspace=pws)
+    te[1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = te[0].elapsed_time(te[1]) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    nnz, nnz0 = info["nnz"], info["nnz0"]
+    peak, peak_kind = _peaks()
+    b1, P = k1_bytes(M, scale)
+    b2 = k2_bytes(M, N, nnz0, nnz, scale)
+    b3 = k3_bytes_per_iter(nnz, N, args.dtype) * iters
+    med = statistics.median
+    stages = {"k1_sort": (med(k1), b1), "k2_filter": (med(k2), b2), "k3_pagerank": (med(k3), b3)}
+    dom = max(stages, key=lambda s: stages[s][0])
+    dom_ms, dom_bytes = stages[dom]
+    if dom == "k3_pagerank":
+        kname, launches_per_stage = "k3 iterate_kernel (merge-path pull SpMV)", iters
+    elif dom == "k1_sort":
+        kname, launches_per_stage = "k1 onesweep pass_kernel (8-bit LSD pass)", P
+    else:
+        kname, launches_per_stage = "k2 stage (unique + transpose passes)", 1
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    tr = TRAFFIC.get(dom)
+    traffic = None
+    if tr and tr.get("sha") == _sha(tr["source"]):
+        traffic = tr["bytes_per_launch"]
+
+    out = {
+        "metric": METRIC,
+        "value": world * M / (ms_step * 1e-3),
+        "unit": "edges/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if args.dtype == "fp32" else args.dtype,
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "scale": scale, "vertices": N, "edges": M, "iters": iters,
+                   "rank_dtype": args.dtype, "supernode_rule": "lowest", "nnz0": nnz0, "nnz": nnz,
+                   "l2": "inputs larger than L2 (2 GiB edge list; 126 MB L2), no flush",
+                   "parallelism": "independent graph per GPU" if world > 1 else "single GPU"},
+        "kernels": {
+            "k1_sort": {"ms": med(k1), "edges_per_s": M / (med(k1) * 1e-3), "gbs": b1 / med(k1) / 1e6},
+            "k2_filter": {"ms": med(k2), "edges_per_s": M / (med(k2) * 1e-3), "gbs": b2 / med(k2) / 1e6},
+            "k3_pagerank": {"ms": med(k3), "edges_per_s": iters * M / (med(k3) * 1e-3), "gbs": b3 / med(k3) / 1e6},
+            "k3_pagerank_fp64": {"ms": k3_64, "edges_per_s": iters * M / (k3_64 * 1e-3),
+                                 "gbs": k3_bytes_per_iter(nnz, N, "fp64") * iters / k3_64 / 1e6},
+        },
+        "accuracy": {"fp32_vs_gpu_fp64_l1": l1_fp32, "fp32_vs_gpu_fp64_max_rel": maxrel_fp32},
+        "roofline": {"bound": "hbm", "kernel": kname, "stage": dom, "launches_per_step": launches_per_stage,
+                     "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "algorithmic_bytes_per_step": dom_bytes},
+        "e2e": {"value": world * M / (e2e_ms * 1e-3), "unit": "edges/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": 8 * M + 8 * N, "d2h_bytes_per_step": 4 * N + 8 * pp.INFO_LEN},
+        "gpu_launches": launches,
+        "clocks": clocks.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(scale, seed, max_seconds=args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline(scale, seed, max_seconds=20.0, sample_div=16):
+    """The oracle, single-threaded, on the first M/sample_div edges of the same edge list."""
+    import kernel0
+    import oracle
+
+    N = 1 << scale
+    Ms = (16 * N) // sample_div
+    u, v = kernel0.edges_host(scale, seed, M=Ms)
+    r0 = kernel0.r0_host(N, seed)
+    O = oracle.default()
+    t0 = time.perf_counter()
+    us, vs = O.k1_sort(u, v)
+    t1 = time.perf_counter()
+    R = O.k2_filter(us, vs, N)
+    t2 = time.perf_counter()
+    O.k3_pagerank(R, r0, ITERS, DAMPING)
+    t3 = time.perf_counter()
+    return {"value": Ms / (t3 - t0), "unit": "edges/s", "cores": 1, "kind": "oracle",
+            "sample": "first %d of the %d scale-%d edges (1/%d), N=2^%d, K1+K2+K3 (20 iterations, binary64)"
+                      % (Ms, 16 * N, scale, sample_div, scale),
+            "seconds": t3 - t0, "host_cores": os.cpu_count(),
+            "kernels": {"k1_edges_per_s": Ms / (t1 - t0), "k2_edges_per_s": Ms / (t2 - t1),
+                        "k3_edges_per_s": ITERS * Ms / (t3 - t2)}}
+
+
+def run_reference(args):
+    """The CPU oracle as the reference arm: each step is the oracle pipeline on a sample."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import kernel0
+    import oracle
+
+    scale = args.scale
+    N = 1 << scale
+    sample_div = 64
+    Ms = (16 * N) // sample_div
+    u, v = kernel0.edges_host(scale, SEED, M=Ms)
+    r0 = kernel0.r0_host(N, SEED)
+    O = oracle.default()
+
+    def step():
+        us, vs = O.k1_sort(u, v)
+        R = O.k2_filter(us, vs, N)
+        O.k3_pagerank(R, r0, ITERS, DAMPING)
+
+    for _ in range(args.warmup):
+        step()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        step()
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    val = Ms / (ms * 1e-3)
+    sample = "first %d of the %d scale-%d edges (1/%d), N=2^%d, K1+K2+K3 binary64" % (Ms, 16 * N, scale, sample_div,
+                                                                                      scale)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "edges/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "scale": scale, "sample": sample},
+        "cpu_baseline": {"value": val, "unit": "edges/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--scale", type=int, default=SCALE)
+    ap.add_argument("--dtype", choices=["fp32", "fp64", "bf16"], default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

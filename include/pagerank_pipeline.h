@@ -1,0 +1,193 @@
+/*
+ * libpp — GB300 (sm_103a) CUDA implementation of the data-parallel hot path
+ * of the PageRank Pipeline Benchmark (Dreher et al., arXiv:1603.01876):
+ *
+ *   Kernel 1 (Sec. IV-B)  sort the edge list by start vertex,
+ *   Kernel 2 (Sec. IV-C)  build the count matrix A = sparse(u,v,1,N,N), take
+ *                         the in-degree, zero the supernode and leaf columns,
+ *                         take the out-degree and normalise the rows,
+ *   Kernel 3 (Sec. IV-D)  run damped PageRank iterations
+ *                         r = ((c.*r)*A) + ((1-c)/N).*sum(r).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Vertex ids are 0-based uint32 in [0, N), N = 2^scale, 1 <= scale <= 27.
+ *    (The paper's Matlab statements are 1-based.)  Edge counts M <= 2^31.
+ *  - Every array argument is DEVICE memory owned by the caller unless its
+ *    name ends in _host.  The library never allocates device memory: scratch
+ *    space ("workspace") is passed in, its size given by the matching
+ *    *_workspace query.  Workspace must be 256-byte aligned.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *    asynchronous: they enqueue kernels and return.  Argument errors found on
+ *    the host are returned at once and nothing is enqueued.  Errors found on
+ *    the device (an out-of-range vertex id, an expired bounded wait) are
+ *    recorded in a device error word that pp_last_device_error() returns.
+ *  - Calls on one stream are ordered; two calls may run concurrently on
+ *    different streams only if they share no output and no workspace.
+ *  - No call launches anything that waits without bound: every cross-block
+ *    wait gives up after a fixed number of polls and records PP_DEV_TIMEOUT.
+ */
+#ifndef PAGERANK_PIPELINE_H
+#define PAGERANK_PIPELINE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PP_OK = 0,
+    PP_ERR_INVALID_ARG = 1, /* a size, pointer or enum is out of range */
+    PP_ERR_WORKSPACE = 2,   /* workspace missing, too small or misaligned */
+    PP_ERR_CUDA = 3,        /* a CUDA runtime call or launch failed */
+    PP_ERR_DEVICE = 4       /* pp_last_device_error: the device recorded an error */
+} pp_status;
+
+/* Arithmetic of Kernel 3's rank vector. */
+typedef enum {
+    PP_FP64 = 0,          /* stored and accumulated in binary64 */
+    PP_FP32 = 1,          /* stored and accumulated in binary32 */
+    PP_BF16_FP32ACC = 2   /* the gathered vector stored in bfloat16, sums in binary32 */
+} pp_dtype;
+
+/* Which columns the supernode statement A(:, d_in == max(d_in)) = 0 zeroes. */
+typedef enum {
+    PP_SUPERNODE_LOWEST = 0,  /* only the lowest-numbered column attaining the maximum */
+    PP_SUPERNODE_ALL_TIES = 1 /* every column attaining the maximum (the literal statement) */
+} pp_supernode_rule;
+
+/* Device error word bits (pp_last_device_error). */
+#define PP_DEV_RANGE 1u   /* an input vertex id was >= N */
+#define PP_DEV_TIMEOUT 2u /* a bounded cross-block wait expired; outputs are invalid */
+
+/* Slots of pp_graph.info (device uint64[PP_INFO_LEN]), written by Kernel 2. */
+#define PP_INFO_NNZ0 0       /* nonzeros of A before the column filters */
+#define PP_INFO_NNZ 1        /* nonzeros of A after them */
+#define PP_INFO_DMAX 2       /* max(d_in) */
+#define PP_INFO_VMAX 3       /* lowest column attaining max(d_in) */
+#define PP_INFO_TIES 4       /* number of columns attaining max(d_in) */
+#define PP_INFO_NOVF 5       /* entries whose count does not fit inline (see rowc) */
+#define PP_INFO_SUPERNODES 6 /* supernode columns zeroed under the chosen rule */
+#define PP_INFO_LEN 8
+
+/*
+ * Kernel 2's output: the filtered matrix A in compressed-column form (the
+ * layout Kernel 3's pull iteration reads), plus the degree vectors.  All
+ * pointers are device arrays allocated by the caller with the lengths that
+ * pp_graph_lengths() returns.  Kernel 3 only reads it.
+ *
+ *   colptr[N+1]  column v holds entries colptr[v] .. colptr[v+1]-1;
+ *                colptr[N] = nnz.
+ *   rowc[M]      entry e (e < nnz) packs the row u (= start vertex) in its low
+ *                `scale` bits and the count A(u,v) in the high 32-scale bits;
+ *                within a column the rows ascend.  A count >= 2^(32-scale)-1
+ *                is stored as the all-ones field and found in the overflow
+ *                table.
+ *   ovf_key[n], ovf_cnt[n]  the overflow table: key (u << 32 | v) ascending,
+ *                count; n = info[PP_INFO_NOVF] <= pp_graph_lengths()[2].
+ *   d_in[N]      sum(A,1) before the column filters (Sec. IV-C step 2).
+ *   d_out[N]     sum(A,2) after them (step 4).
+ *   inv_dout32[N], inv_dout64[N]  1/d_out (IEEE round-to-nearest division),
+ *                0 where d_out = 0; A(u,v) = count * inv_dout[u] (step 4).
+ *   info[PP_INFO_LEN]  the scalars listed above.
+ */
+typedef struct {
+    uint32_t scale;
+    uint32_t reserved;
+    uint64_t M; /* number of edges the graph was built from */
+    uint32_t *colptr;
+    uint32_t *rowc;
+    uint64_t *ovf_key;
+    uint32_t *ovf_cnt;
+    uint32_t *d_in;
+    uint32_t *d_out;
+    float *inv_dout32;
+    double *inv_dout64;
+    uint64_t *info;
+} pp_graph;
+
+/* Element counts of the pp_graph arrays for M edges at this scale, in the
+ * order colptr, rowc, ovf_key, ovf_cnt, d_in, d_out, inv_dout32, inv_dout64,
+ * info.  out[] must hold 9 values. */
+pp_status pp_graph_lengths(uint64_t M, uint32_t scale, uint64_t out[9]);
+
+/*
+ * Kernel 1 (Sec. IV-B): sort the edges so that u_out is nondecreasing,
+ * u(i-1) <= u(i) <= u(i+1); edges with equal start vertex are ordered by end
+ * vertex, which makes the result unique.  u, v: M input ids; u_out, v_out:
+ * M outputs, which must not overlap the inputs.  The sort is an LSD radix
+ * sort over the key (u << scale | v), ceil(2*scale/8) passes of 8 bits.
+ * An id >= N sets PP_DEV_RANGE and leaves the output unspecified.
+ */
+pp_status pp_sort_edges_workspace(uint64_t M, uint32_t scale, size_t *bytes);
+pp_status pp_sort_edges(const uint32_t *u, const uint32_t *v, uint64_t M, uint32_t scale,
+                        uint32_t *u_out, uint32_t *v_out, void *workspace, size_t workspace_bytes,
+                        void *stream);
+
+/*
+ * Kernel 2 (Sec. IV-C), from Kernel 1's output (u_sorted, v_sorted; M edges
+ * sorted by (u, v)):
+ *   step 1  A = sparse(u,v,1,N,N)           duplicate edges become counts
+ *   step 2  d_in = sum(A,1)
+ *   step 3  A(:, d_in == max(d_in)) = 0     per `rule`
+ *           A(:, d_in == 1) = 0             (same d_in as the line above)
+ *   step 4  d_out = sum(A,2); A(i,:) = A(i,:) ./ d_out(i) for d_out(i) > 0
+ * Rows with d_out = 0 stay zero: no dangling-node correction (Sec. IV-C).
+ * g->scale and g->M must equal scale and M; g's arrays are overwritten.
+ */
+pp_status pp_build_filter_normalize_workspace(uint64_t M, uint32_t scale, size_t *bytes);
+pp_status pp_build_filter_normalize(const uint32_t *u_sorted, const uint32_t *v_sorted, uint64_t M,
+                                    uint32_t scale, pp_supernode_rule rule, const pp_graph *g,
+                                    void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * Kernel 3 (Sec. IV-D and the appendix): from the start vector r0 (device
+ * binary64[N], any positive values; the call divides by norm(r0,1) first),
+ * run `iters` iterations of
+ *     r(v) = c * sum_u r(u) A(u,v) + ((1-c)/N) * sum(r)
+ * with A from Kernel 2.  sum(r) is reduced in binary64 for every dtype.
+ * r_out receives the final r: double[N] for PP_FP64, float[N] otherwise.
+ * r_l1 (nullable, double[N]) receives r / norm(r,1) in binary64.
+ * The result is deterministic: the same inputs give the same bits.
+ */
+pp_status pp_pagerank_workspace(uint64_t M, uint32_t scale, uint32_t iters, pp_dtype dtype,
+                                size_t *bytes);
+pp_status pp_pagerank(const pp_graph *g, const double *r0, uint32_t iters, double c, pp_dtype dtype,
+                      void *r_out, double *r_l1, void *workspace, size_t workspace_bytes,
+                      void *stream);
+
+/*
+ * Kernels 1-3 back to back from HOST buffers: copies u_host, v_host (M ids
+ * each) and r0_host (N values) to the device, runs the three kernels, each
+ * complete before the next starts, and copies the final r into r_out_host
+ * (double[N] for PP_FP64, float[N] otherwise) and, if info_host is not NULL,
+ * Kernel 2's scalars into info_host[PP_INFO_LEN].  Every device buffer is
+ * carved from `workspace` (size from pp_pipeline_workspace).  Host buffers
+ * should be page-locked for the copies to be asynchronous; the results are
+ * valid after the stream has been synchronised.
+ */
+pp_status pp_pipeline_workspace(uint64_t M, uint32_t scale, uint32_t iters, pp_dtype dtype,
+                                size_t *bytes);
+pp_status pp_pipeline_host(const uint32_t *u_host, const uint32_t *v_host, uint64_t M, uint32_t scale,
+                           const double *r0_host, uint32_t iters, double c, pp_dtype dtype,
+                           pp_supernode_rule rule, void *r_out_host, uint64_t *info_host,
+                           void *workspace, size_t workspace_bytes, void *stream);
+
+/* Synchronise `stream`, then return and clear the device error word (a
+ * PP_DEV_* bit set) of the current device in *code.  Returns PP_ERR_DEVICE if
+ * the word was non-zero, PP_ERR_CUDA if synchronisation failed, else PP_OK. */
+pp_status pp_last_device_error(void *stream, uint32_t *code);
+
+/* A short English description of a status code (static storage). */
+const char *pp_status_string(pp_status status);
+
+/* Number of kernels this library has enqueued in this process so far. */
+uint64_t pp_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PAGERANK_PIPELINE_H */

@@ -1,0 +1,222 @@
+"""Python binding of libpp: the GB300 CUDA path of the PageRank pipeline.
+
+Argument marshalling only.  Every step of Kernels 1-3 runs in the CUDA
+kernels behind include/pagerank_pipeline.h; this module passes device
+pointers (from torch tensors) and sizes through ctypes, and raises if the
+library is missing: there is no CPU fallback.
+
+    sort_edges(u, v, scale)                      Kernel 1 (Sec. IV-B)
+    build_filter_normalize(us, vs, scale, rule)  Kernel 2 (Sec. IV-C) -> Graph
+    pagerank(graph, r0, iters, c, dtype)         Kernel 3 (Sec. IV-D)
+    pipeline_host(u, v, scale, r0, ...)          Kernels 1-3 from host buffers
+
+Vertex ids travel as torch.int32 tensors holding uint32 bit patterns.
+"""
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpp.so")
+
+PP_OK, PP_ERR_INVALID_ARG, PP_ERR_WORKSPACE, PP_ERR_CUDA, PP_ERR_DEVICE = range(5)
+DTYPES = {"fp64": 0, "fp32": 1, "bf16": 2}
+RULES = {"lowest": 0, "all_ties": 1}
+INFO = {"nnz0": 0, "nnz": 1, "dmax": 2, "vmax": 3, "ties": 4, "novf": 5, "supernodes": 6}
+INFO_LEN = 8
+DEV_RANGE, DEV_TIMEOUT = 1, 2
+
+
+class PPError(RuntimeError):
+    def __init__(self, fn, status, detail=""):
+        msg = "%s failed: %s" % (fn, _lib().pp_status_string(status).decode())
+        super().__init__(msg + (" " + detail if detail else ""))
+        self.status = status
+
+
+class CGraph(ctypes.Structure):
+    _fields_ = [
+        ("scale", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("M", ctypes.c_uint64),
+        ("colptr", ctypes.c_void_p), ("rowc", ctypes.c_void_p), ("ovf_key", ctypes.c_void_p),
+        ("ovf_cnt", ctypes.c_void_p), ("d_in", ctypes.c_void_p), ("d_out", ctypes.c_void_p),
+        ("inv_dout32", ctypes.c_void_p), ("inv_dout64", ctypes.c_void_p), ("info", ctypes.c_void_p),
+    ]
+
+
+_L = None
+
+
+def _lib():
+    global _L
+    if _L is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libpp.so is not built (run __graft_entry__.build()); there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, u32, u64, sz = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.POINTER(ctypes.c_size_t)
+        i32, dbl = ctypes.c_int, ctypes.c_double
+        sig = {
+            "pp_graph_lengths": [u64, u32, vp],
+            "pp_sort_edges_workspace": [u64, u32, sz],
+            "pp_sort_edges": [vp, vp, u64, u32, vp, vp, vp, ctypes.c_size_t, vp],
+            "pp_build_filter_normalize_workspace": [u64, u32, sz],
+            "pp_build_filter_normalize": [vp, vp, u64, u32, i32, ctypes.POINTER(CGraph), vp, ctypes.c_size_t, vp],
+            "pp_pagerank_workspace": [u64, u32, u32, i32, sz],
+            "pp_pagerank": [ctypes.POINTER(CGraph), vp, u32, dbl, i32, vp, vp, vp, ctypes.c_size_t, vp],
+            "pp_pipeline_workspace": [u64, u32, u32, i32, sz],
+            "pp_pipeline_host": [vp, vp, u64, u32, vp, u32, dbl, i32, i32, vp, vp, vp, ctypes.c_size_t, vp],
+            "pp_last_device_error": [vp, ctypes.POINTER(ctypes.c_uint32)],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.pp_status_string.argtypes = [ctypes.c_int]
+        L.pp_status_string.restype = ctypes.c_char_p
+        L.pp_launch_count.argtypes = []
+        L.pp_launch_count.restype = ctypes.c_uint64
+        _L = L
+    return _L
+
+
+def lib():
+    return _lib()
+
+
+def _check(fn, st):
+    if st != PP_OK:
+        raise PPError(fn, st)
+
+
+def _stream(stream, device=None):
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _workspace(nbytes, device):
+    # torch's caching allocator returns 512-byte aligned blocks
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+def launch_count():
+    return int(_lib().pp_launch_count())
+
+
+def last_device_error(stream=None):
+    """Synchronise and return (and clear) the device error bits (0 = none)."""
+    code = ctypes.c_uint32(0)
+    st = _lib().pp_last_device_error(_stream(stream), ctypes.byref(code))
+    if st not in (PP_OK, PP_ERR_DEVICE):
+        raise PPError("pp_last_device_error", st)
+    return int(code.value)
+
+
+def graph_lengths(M, scale):
+    out = (ctypes.c_uint64 * 9)()
+    _check("pp_graph_lengths", _lib().pp_graph_lengths(M, scale, out))
+    return list(out)
+
+
+def workspace_bytes(kind, M, scale, iters=20, dtype="fp32"):
+    n = ctypes.c_size_t(0)
+    L = _lib()
+    if kind == "sort":
+        st = L.pp_sort_edges_workspace(M, scale, ctypes.byref(n))
+    elif kind == "build":
+        st = L.pp_build_filter_normalize_workspace(M, scale, ctypes.byref(n))
+    elif kind == "pagerank":
+        st = L.pp_pagerank_workspace(M, scale, iters, DTYPES[dtype], ctypes.byref(n))
+    elif kind == "pipeline":
+        st = L.pp_pipeline_workspace(M, scale, iters, DTYPES[dtype], ctypes.byref(n))
+    else:
+        raise ValueError(kind)
+    _check("workspace query", st)
+    return int(n.value)
+
+
+class Graph:
+    """Kernel 2's output (device tensors) and the C struct that points at them."""
+
+    def __init__(self, M, scale, device):
+        lens = graph_lengths(M, scale)
+        i32, i64 = torch.int32, torch.int64
+        self.M, self.scale, self.N = M, scale, 1 << scale
+        self.colptr = torch.empty(lens[0], dtype=i32, device=device)
+        self.rowc = torch.empty(lens[1], dtype=i32, device=device)
+        self.ovf_key = torch.empty(lens[2], dtype=i64, device=device)
+        self.ovf_cnt = torch.empty(lens[3], dtype=i32, device=device)
+        self.d_in = torch.empty(lens[4], dtype=i32, device=device)
+        self.d_out = torch.empty(lens[5], dtype=i32, device=device)
+        self.inv_dout32 = torch.empty(lens[6], dtype=torch.float32, device=device)
+        self.inv_dout64 = torch.empty(lens[7], dtype=torch.float64, device=device)
+        self.info = torch.zeros(lens[8], dtype=i64, device=device)
+        self.c = CGraph(scale, 0, M, self.colptr.data_ptr(), self.rowc.data_ptr(), self.ovf_key.data_ptr(),
+                        self.ovf_cnt.data_ptr(), self.d_in.data_ptr(), self.d_out.data_ptr(),
+                        self.inv_dout32.data_ptr(), self.inv_dout64.data_ptr(), self.info.data_ptr())
+
+    def info_dict(self):
+        v = self.info.cpu().tolist()
+        return {k: int(v[i]) for k, i in INFO.items()}
+
+
+def sort_edges(u, v, scale, out=None, workspace=None, stream=None):
+    """Kernel 1: (u_out, v_out) sorted by (u, v)."""
+    M = u.numel()
+    dev = u.device
+    if out is None:
+        out = (torch.empty_like(u), torch.empty_like(v))
+    need = workspace_bytes("sort", M, scale)
+    ws = workspace if workspace is not None and workspace.numel() >= need else _workspace(need, dev)
+    st = _lib().pp_sort_edges(_ptr(u), _ptr(v), M, scale, _ptr(out[0]), _ptr(out[1]), _ptr(ws), ws.numel(),
+                              _stream(stream, dev))
+    _check("pp_sort_edges", st)
+    return out
+
+
+def build_filter_normalize(us, vs, scale, rule="lowest", graph=None, workspace=None, stream=None):
+    """Kernel 2: the filtered, normalised matrix as a Graph."""
+    M = us.numel()
+    dev = us.device
+    g = graph if graph is not None else Graph(M, scale, dev)
+    need = workspace_bytes("build", M, scale)
+    ws = workspace if workspace is not None and workspace.numel() >= need else _workspace(need, dev)
+    st = _lib().pp_build_filter_normalize(_ptr(us), _ptr(vs), M, scale, RULES[rule], ctypes.byref(g.c), _ptr(ws),
+                                          ws.numel(), _stream(stream, dev))
+    _check("pp_build_filter_normalize", st)
+    return g
+
+
+def pagerank(graph, r0, iters=20, c=0.85, dtype="fp32", out=None, want_l1=False, workspace=None, stream=None):
+    """Kernel 3: r after `iters` iterations (float64 for fp64, float32 otherwise)."""
+    dev = r0.device
+    if out is None:
+        out = torch.empty(graph.N, dtype=torch.float64 if dtype == "fp64" else torch.float32, device=dev)
+    l1 = torch.empty(graph.N, dtype=torch.float64, device=dev) if want_l1 else None
+    need = workspace_bytes("pagerank", graph.M, graph.scale, iters, dtype)
+    ws = workspace if workspace is not None and workspace.numel() >= need else _workspace(need, dev)
+    st = _lib().pp_pagerank(ctypes.byref(graph.c), _ptr(r0), iters, c, DTYPES[dtype], _ptr(out), _ptr(l1), _ptr(ws),
+                            ws.numel(), _stream(stream, dev))
+    _check("pp_pagerank", st)
+    return (out, l1) if want_l1 else out
+
+
+def pipeline_host(u, v, scale, r0, iters=20, c=0.85, dtype="fp32", rule="lowest", out=None, info=None,
+                  workspace=None, stream=None, device="cuda"):
+    """Kernels 1-3 from host tensors (pin them for asynchronous copies); returns (r, info)."""
+    M = u.numel()
+    N = 1 << scale
+    if out is None:
+        out = torch.empty(N, dtype=torch.float64 if dtype == "fp64" else torch.float32).pin_memory()
+    if info is None:
+        info = torch.zeros(INFO_LEN, dtype=torch.int64).pin_memory()
+    need = workspace_bytes("pipeline", M, scale, iters, dtype)
+    ws = workspace if workspace is not None and workspace.numel() >= need else _workspace(need, device)
+    st = _lib().pp_pipeline_host(_ptr(u), _ptr(v), M, scale, _ptr(r0), iters, c, DTYPES[dtype], RULES[rule],
+                                 _ptr(out), _ptr(info), _ptr(ws), ws.numel(), _stream(stream, ws.device))
+    _check("pp_pipeline_host", st)
+    return out, info

@@ -1,0 +1,135 @@
+// Kernel 1 (Sec. IV-B): sort the edge list by start vertex.
+//
+// Each edge becomes the key (u << scale | v) (32-bit when 2*scale <= 32,
+// 64-bit otherwise); an LSD radix sort over its 2*scale bits, 8 bits per
+// pass, orders the edges by u and, within equal u, by v.  The pack into keys
+// happens while the first pass loads, and the unpack into (u_out, v_out) while
+// the last pass stores, so the edge list is read and written once per pass.
+#include <algorithm>
+
+#include "onesweep.cuh"
+
+PP_DEFINE_ERROR_WORD(k1_fetch_error)
+
+namespace pp {
+namespace k1 {
+
+template <typename KeyT, bool CHECK>
+struct PackSrc {
+    const uint32_t *u, *v;
+    uint32_t scale;
+    __device__ __forceinline__ bool load(uint64_t i, KeyT &k, uint32_t &) const {
+        const uint32_t a = __ldg(u + i), b = __ldg(v + i);
+        if (CHECK && ((a | b) >> scale)) pp_set_error(PP_DEV_RANGE);
+        k = ((KeyT)a << scale) | (KeyT)b;
+        return true;
+    }
+};
+
+template <typename KeyT>
+struct KeySrc {
+    const KeyT *keys;
+    __device__ __forceinline__ bool load(uint64_t i, KeyT &k, uint32_t &) const {
+        k = keys[i];
+        return true;
+    }
+};
+
+template <typename KeyT>
+struct KeyDst {
+    KeyT *keys;
+    __device__ __forceinline__ void store(uint64_t pos, KeyT k, uint32_t) const { keys[pos] = k; }
+};
+
+template <typename KeyT>
+struct UnpackDst {
+    uint32_t *u, *v;
+    uint32_t scale;
+    __device__ __forceinline__ void store(uint64_t pos, KeyT k, uint32_t) const {
+        u[pos] = (uint32_t)(k >> scale);
+        v[pos] = (uint32_t)(k & (((KeyT)1 << scale) - 1));
+    }
+};
+
+struct Layout {
+    void *keys[2];
+    os::SortWs sort;
+    size_t bytes;
+};
+
+inline int num_passes(uint32_t scale) { return (int)ceil_div(2u * scale, 8u); }
+
+inline Layout layout(void *ws, uint64_t M, uint32_t scale) {
+    Carver c(ws);
+    Layout L;
+    const int P = num_passes(scale);
+    const size_t kb = (2 * scale <= 32) ? 4 : 8;
+    L.keys[0] = P >= 2 ? c.take<char>(M * kb) : nullptr;
+    L.keys[1] = P >= 3 ? c.take<char>(M * kb) : nullptr;
+    L.sort = os::carve_sort_ws(c, M);
+    L.bytes = c.size();
+    return L;
+}
+
+template <typename KeyT>
+void run(const uint32_t *u, const uint32_t *v, uint64_t M, uint32_t scale, uint32_t *u_out,
+         uint32_t *v_out, const Layout &L, cudaStream_t s) {
+    const int P = num_passes(scale);
+    const size_t word = L.sort.wide ? 8 : 4;
+    const uint64_t ntiles = ceil_div(M, os::TILE);
+    cudaMemsetAsync(L.sort.hist, 0, os::kCtlBytes, s);
+    const unsigned hgrid = (unsigned)std::min<uint64_t>(ceil_div(M, 256 * 8), (uint64_t)sm_count() * 8);
+    os::hist_kernel<KeyT, PackSrc<KeyT, true>><<<hgrid ? hgrid : 1, 256, 0, s>>>(
+        PackSrc<KeyT, true>{u, v, scale}, nullptr, M, P, L.sort.hist,
+        static_cast<uint32_t *>(L.sort.status[0]), ntiles * os::RADIX * word / 4);
+    count_launch();
+    KeyT *A = static_cast<KeyT *>(L.keys[0]);
+    KeyT *B = static_cast<KeyT *>(L.keys[1]);
+    const PackSrc<KeyT, false> pack{u, v, scale};
+    const UnpackDst<KeyT> unpack{u_out, v_out, scale};
+    if (P == 1) {
+        os::launch_pass<KeyT, false>(L.sort, 0, P, pack, unpack, nullptr, M, s);
+        return;
+    }
+    os::launch_pass<KeyT, false>(L.sort, 0, P, pack, KeyDst<KeyT>{A}, nullptr, M, s);
+    for (int p = 1; p < P - 1; ++p) {
+        KeyT *in = (p & 1) ? A : B;
+        KeyT *out = (p & 1) ? B : A;
+        os::launch_pass<KeyT, false>(L.sort, p, P, KeySrc<KeyT>{in}, KeyDst<KeyT>{out}, nullptr, M, s);
+    }
+    KeyT *last_in = ((P - 1) & 1) ? A : B;
+    os::launch_pass<KeyT, false>(L.sort, P - 1, P, KeySrc<KeyT>{last_in}, unpack, nullptr, M, s);
+}
+
+}  // namespace k1
+}  // namespace pp
+
+using namespace pp;
+
+static bool k1_args_ok(uint64_t M, uint32_t scale) {
+    return scale >= 1 && scale <= 27 && M <= (1ull << 31);
+}
+
+extern "C" pp_status pp_sort_edges_workspace(uint64_t M, uint32_t scale, size_t *bytes) {
+    if (!bytes || !k1_args_ok(M, scale)) return PP_ERR_INVALID_ARG;
+    *bytes = k1::layout(nullptr, M, scale).bytes;
+    return PP_OK;
+}
+
+extern "C" pp_status pp_sort_edges(const uint32_t *u, const uint32_t *v, uint64_t M, uint32_t scale,
+                                   uint32_t *u_out, uint32_t *v_out, void *ws, size_t ws_bytes,
+                                   void *stream) {
+    if (!k1_args_ok(M, scale)) return PP_ERR_INVALID_ARG;
+    if (M == 0) return PP_OK;
+    if (!u || !v || !u_out || !v_out) return PP_ERR_INVALID_ARG;
+    const k1::Layout need = k1::layout(nullptr, M, scale);
+    pp_status st = check_ws(ws, ws_bytes, need.bytes);
+    if (st != PP_OK) return st;
+    const k1::Layout L = k1::layout(ws, M, scale);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (2 * scale <= 32)
+        k1::run<uint32_t>(u, v, M, scale, u_out, v_out, L, s);
+    else
+        k1::run<uint64_t>(u, v, M, scale, u_out, v_out, L, s);
+    return launch_status();
+}

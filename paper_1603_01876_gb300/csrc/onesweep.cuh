@@ -1,0 +1,253 @@
+// Stable LSD radix sort, one scatter pass per 8-bit digit.
+//
+// The scheme follows the published Onesweep method (Adinets & Merrill,
+// "Onesweep: A Faster Least Significant Digit Radix Sort for GPUs", 2022):
+// an up-front pass counts the digits of every pass at once; each scatter pass
+// then takes tiles in the order blocks start, ranks the tile's keys with a
+// warp-level multisplit (match.any + popc) into warp-private shared-memory
+// counters, publishes the tile's per-digit counts, and finds its global
+// offset per digit by a decoupled look-back over earlier tiles' published
+// counts.  Keys are staged in shared memory in sorted order, so each digit's
+// run is written to global memory with consecutive addresses.
+//
+// Look-back waits poll with a bound (kSpinLimit): a wait that expires records
+// PP_DEV_TIMEOUT in the device error word and the kernel carries on, so no
+// launch can hang.  A tile only ever waits for tiles that earlier-started
+// blocks already own, so the bound is never reached in a correct run.
+//
+// Sources and sinks are small functors so that the same pass kernel packs
+// (u, v) into a key on the first pass of Kernel 1, unpacks on its last pass,
+// and filters columns on the first pass of Kernel 2's transpose.
+#pragma once
+
+#include "pp_common.cuh"
+
+namespace pp {
+namespace os {
+
+constexpr int THREADS = 256;
+constexpr int WARPS = THREADS / 32;
+constexpr int ITEMS = 16;
+constexpr int TILE = THREADS * ITEMS;
+constexpr int RADIX = 256;
+constexpr int MAX_PASSES = 8;
+static_assert(THREADS == RADIX, "one thread per digit in the per-digit phases");
+
+template <typename S>
+struct Flags;
+template <>
+struct Flags<uint32_t> {
+    static constexpr uint32_t AGG = 1u << 30, INC = 2u << 30, ANY = 3u << 30, VAL = (1u << 30) - 1;
+};
+template <>
+struct Flags<uint64_t> {
+    static constexpr uint64_t AGG = 1ull << 62, INC = 2ull << 62, ANY = 3ull << 62, VAL = (1ull << 62) - 1;
+};
+
+__device__ __forceinline__ uint32_t ld_status(const uint32_t *p) { return ld_relaxed_u32(p); }
+__device__ __forceinline__ uint64_t ld_status(const uint64_t *p) { return ld_relaxed_u64(p); }
+__device__ __forceinline__ void st_status(uint32_t *p, uint32_t v) { st_relaxed_u32(p, v); }
+__device__ __forceinline__ void st_status(uint64_t *p, uint64_t v) { st_relaxed_u64(p, v); }
+
+// Per-pass control block.
+struct PassCtl {
+    uint32_t shift;         // digit = (key >> shift) & 255
+    const uint32_t *hist;   // [256] number of valid keys per digit in this pass
+    void *status;           // [ntiles * 256] look-back words, zero on entry
+    void *status_next;      // words the next pass uses, zeroed here (nullptr: none)
+    uint32_t *tile_ctr;     // zero on entry
+    const uint64_t *n_dev;  // element count on the device (nullptr: use n_host)
+    uint64_t n_host;
+};
+
+// Status words are 32-bit while every count fits in 30 bits.
+inline bool wide_status(uint64_t n_max) { return n_max >= (1ull << 30); }
+
+template <typename KeyT, typename StatT, bool HAS_VAL, class Src, class Dst>
+__global__ void __launch_bounds__(THREADS, 2) pass_kernel(Src src, Dst dst, PassCtl ctl) {
+    using F = Flags<StatT>;
+    __shared__ KeyT s_keys[TILE];
+    __shared__ uint32_t s_vals[HAS_VAL ? TILE : 1];
+    __shared__ uint32_t s_whist[WARPS][RADIX];
+    __shared__ uint32_t s_binstart[RADIX];
+    __shared__ long long s_gbase[RADIX];
+    __shared__ uint32_t s_scan[40];
+    __shared__ uint32_t s_tile;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_tile = atomicAdd(ctl.tile_ctr, 1u);
+    for (int i = tid; i < WARPS * RADIX; i += THREADS) (&s_whist[0][0])[i] = 0;
+
+    // Global start of each digit: exclusive scan of the pass histogram.
+    uint32_t htotal;
+    const uint32_t hexcl = block_exclusive_sum<uint32_t, THREADS>(ctl.hist[tid], s_scan, &htotal);
+
+    const uint64_t n = ctl.n_dev ? *ctl.n_dev : ctl.n_host;
+    const uint32_t tile = s_tile;
+    const uint64_t ntiles = (n + TILE - 1) / TILE;
+    if (tile >= ntiles) return;
+    if (ctl.status_next) static_cast<StatT *>(ctl.status_next)[(uint64_t)tile * RADIX + tid] = 0;
+
+    // Warp-striped load: warp w owns elements [w*ITEMS*32, (w+1)*ITEMS*32) of
+    // the tile; item i of a lane is element i*32 + lane of that range, so the
+    // order (warp, item, lane) is the input order.
+    const uint64_t base = (uint64_t)tile * TILE + (uint64_t)warp * (ITEMS * 32);
+    KeyT keys[ITEMS];
+    uint32_t vals[ITEMS];
+    uint32_t dig[ITEMS];  // digit, or RADIX for an absent / filtered element
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const uint64_t idx = base + (uint64_t)i * 32 + lane;
+        bool ok = false;
+        keys[i] = 0;
+        vals[i] = 0;
+        if (idx < n) ok = src.load(idx, keys[i], vals[i]);
+        dig[i] = ok ? (uint32_t)(keys[i] >> ctl.shift) & (RADIX - 1) : RADIX;
+    }
+
+    // Warp-level multisplit: rank of each key among equal digits of its warp.
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const uint32_t d = dig[i];
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t before = d < RADIX ? s_whist[warp][d] : 0u;
+        __syncwarp();
+        if (d < RADIX && (peers >> lane) == 1u) s_whist[warp][d] = before + __popc(peers);
+        __syncwarp();
+        dig[i] = d | ((before + __popc(peers & lanemask_lt())) << 16);
+    }
+    __syncthreads();
+
+    // Per digit (thread tid): offsets of the warps within the tile's digit run.
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < WARPS; ++w) {
+        const uint32_t c = s_whist[w][tid];
+        s_whist[w][tid] = run;
+        run += c;
+    }
+    const uint32_t tcount = run;
+    StatT *st = static_cast<StatT *>(ctl.status);
+    StatT *mine = st + (uint64_t)tile * RADIX + tid;
+    st_status(mine, (tile == 0 ? F::INC : F::AGG) | (StatT)tcount);
+
+    uint32_t nvalid;
+    const uint32_t bstart = block_exclusive_sum<uint32_t, THREADS>(tcount, s_scan, &nvalid);
+    s_binstart[tid] = bstart;
+
+    // Decoupled look-back for this digit.
+    StatT excl = 0;
+    if (tile > 0) {
+        uint64_t p = tile - 1;
+        uint32_t spins = 0;
+        while (true) {
+            const StatT s = ld_status(st + p * RADIX + tid);
+            if ((s & F::ANY) == 0) {
+                if (++spins > kSpinLimit) {
+                    pp_set_error(PP_DEV_TIMEOUT);
+                    break;
+                }
+                backoff(spins);
+                continue;
+            }
+            excl += s & F::VAL;
+            if (s & F::INC) break;
+            --p;  // tile 0 always publishes an inclusive word, so p stays >= 0
+        }
+        st_status(mine, F::INC | (excl + (StatT)tcount));
+    }
+    s_gbase[tid] = (long long)hexcl + (long long)excl - (long long)bstart;
+    __syncthreads();
+
+    // Stage the tile in digit order in shared memory.
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const uint32_t d = dig[i] & 0xffffu;
+        if (d < RADIX) {
+            const uint32_t pos = s_binstart[d] + s_whist[warp][d] + (dig[i] >> 16);
+            s_keys[pos] = keys[i];
+            if (HAS_VAL) s_vals[pos] = vals[i];
+        }
+    }
+    __syncthreads();
+
+    // Write each digit run to its global position.
+    for (uint32_t j = tid; j < nvalid; j += THREADS) {
+        const KeyT k = s_keys[j];
+        const uint32_t d = (uint32_t)(k >> ctl.shift) & (RADIX - 1);
+        dst.store((uint64_t)(s_gbase[d] + (long long)j), k, HAS_VAL ? s_vals[j] : 0u);
+    }
+}
+
+// Up-front digit histogram of every pass, plus zeroing of pass 0's look-back
+// words.  hist[p * 256 + d] must be zero on entry.
+template <typename KeyT, class Src>
+__global__ void __launch_bounds__(256) hist_kernel(Src src, const uint64_t *n_dev, uint64_t n_host,
+                                                   int npasses, uint32_t *hist, uint32_t *status0,
+                                                   uint64_t status0_words) {
+    __shared__ uint32_t sh[MAX_PASSES][RADIX];
+    for (int i = threadIdx.x; i < MAX_PASSES * RADIX; i += blockDim.x) (&sh[0][0])[i] = 0;
+    __syncthreads();
+    const uint64_t n = n_dev ? *n_dev : n_host;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        KeyT k;
+        uint32_t val;
+        if (!src.load(i, k, val)) continue;
+        for (int p = 0; p < npasses; ++p) atomicAdd(&sh[p][(uint32_t)(k >> (8 * p)) & (RADIX - 1)], 1u);
+    }
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < status0_words; i += stride)
+        status0[i] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < npasses * RADIX; i += blockDim.x) {
+        const uint32_t c = (&sh[0][0])[i];
+        if (c) atomicAdd(&hist[i], c);
+    }
+}
+
+// Workspace of a sort of at most n_max elements in `npasses` passes.
+struct SortWs {
+    uint32_t *hist;      // [MAX_PASSES * 256]
+    uint32_t *tile_ctr;  // [MAX_PASSES]
+    void *status[2];     // look-back words, alternating between passes
+    uint64_t ntiles_max;
+    bool wide;
+};
+
+inline SortWs carve_sort_ws(Carver &c, uint64_t n_max) {
+    SortWs w;
+    w.hist = c.take<uint32_t>(MAX_PASSES * RADIX + MAX_PASSES);
+    w.tile_ctr = w.hist ? w.hist + MAX_PASSES * RADIX : nullptr;
+    w.ntiles_max = ceil_div(n_max ? n_max : 1, TILE);
+    w.wide = wide_status(n_max);
+    const size_t word = w.wide ? 8 : 4;
+    for (int i = 0; i < 2; ++i) w.status[i] = c.take<char>(w.ntiles_max * RADIX * word);
+    return w;
+}
+
+// Bytes of the control block (hist + tile counters) that must be zeroed
+// before the histogram pass.
+constexpr size_t kCtlBytes = (MAX_PASSES * RADIX + MAX_PASSES) * sizeof(uint32_t);
+
+// Launches pass `p` (of npasses) of a sort prepared in `w`.
+template <typename KeyT, bool HAS_VAL, class Src, class Dst>
+inline void launch_pass(const SortWs &w, int p, int npasses, Src src, Dst dst, const uint64_t *n_dev,
+                        uint64_t n_max, cudaStream_t s) {
+    PassCtl ctl;
+    ctl.shift = 8u * (uint32_t)p;
+    ctl.hist = w.hist + p * RADIX;
+    ctl.status = w.status[p & 1];
+    ctl.status_next = (p + 1 < npasses) ? w.status[(p + 1) & 1] : nullptr;
+    ctl.tile_ctr = w.tile_ctr + p;
+    ctl.n_dev = n_dev;
+    ctl.n_host = n_max;
+    const unsigned grid = (unsigned)ceil_div(n_max ? n_max : 1, TILE);
+    if (w.wide)
+        pass_kernel<KeyT, uint64_t, HAS_VAL, Src, Dst><<<grid, THREADS, 0, s>>>(src, dst, ctl);
+    else
+        pass_kernel<KeyT, uint32_t, HAS_VAL, Src, Dst><<<grid, THREADS, 0, s>>>(src, dst, ctl);
+    count_launch();
+}
+
+}  // namespace os
+}  // namespace pp

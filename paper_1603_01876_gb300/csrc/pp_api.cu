@@ -1,0 +1,128 @@
+// Library-wide entry points: status strings, the device error word, the
+// launch counter, and the host-buffer pipeline (Kernels 1-3 back to back).
+#include <algorithm>
+
+#include "pp_common.cuh"
+
+namespace pp {
+std::atomic<uint64_t> g_launches{0};
+uint32_t k1_fetch_error(cudaStream_t s);
+uint32_t k2_fetch_error(cudaStream_t s);
+uint32_t k3_fetch_error(cudaStream_t s);
+}  // namespace pp
+
+using namespace pp;
+
+extern "C" uint64_t pp_launch_count(void) { return g_launches.load(); }
+
+extern "C" const char *pp_status_string(pp_status st) {
+    switch (st) {
+        case PP_OK: return "ok";
+        case PP_ERR_INVALID_ARG: return "invalid argument";
+        case PP_ERR_WORKSPACE: return "workspace missing, too small or not 256-byte aligned";
+        case PP_ERR_CUDA: return "CUDA runtime error";
+        case PP_ERR_DEVICE: return "the device recorded an error (see pp_last_device_error)";
+    }
+    return "unknown status";
+}
+
+extern "C" pp_status pp_last_device_error(void *stream, uint32_t *code) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return PP_ERR_CUDA;
+    uint32_t w = 0;
+    const uint32_t parts[3] = {k1_fetch_error(s), k2_fetch_error(s), k3_fetch_error(s)};
+    for (uint32_t p : parts) {
+        if (p == 0xffffffffu) return PP_ERR_CUDA;
+        w |= p;
+    }
+    if (code) *code = w;
+    return w ? PP_ERR_DEVICE : PP_OK;
+}
+
+namespace {
+
+struct PipeLayout {
+    uint32_t *u, *v, *us, *vs;
+    pp_graph g;
+    double *r0;
+    void *r_out;
+    void *scratch;
+    size_t scratch_bytes;
+    size_t bytes;
+};
+
+PipeLayout pipe_layout(void *ws, uint64_t M, uint32_t scale, uint32_t iters, pp_dtype dt) {
+    Carver c(ws);
+    PipeLayout L;
+    const uint64_t N = 1ull << scale;
+    const uint64_t cap = M ? M : 1;
+    uint64_t len[9];
+    pp_graph_lengths(M, scale, len);
+    L.u = c.take<uint32_t>(cap);
+    L.v = c.take<uint32_t>(cap);
+    L.us = c.take<uint32_t>(cap);
+    L.vs = c.take<uint32_t>(cap);
+    L.g.scale = scale;
+    L.g.reserved = 0;
+    L.g.M = M;
+    L.g.colptr = c.take<uint32_t>(len[0]);
+    L.g.rowc = c.take<uint32_t>(len[1]);
+    L.g.ovf_key = c.take<uint64_t>(len[2]);
+    L.g.ovf_cnt = c.take<uint32_t>(len[3]);
+    L.g.d_in = c.take<uint32_t>(len[4]);
+    L.g.d_out = c.take<uint32_t>(len[5]);
+    L.g.inv_dout32 = c.take<float>(len[6]);
+    L.g.inv_dout64 = c.take<double>(len[7]);
+    L.g.info = c.take<uint64_t>(len[8]);
+    L.r0 = c.take<double>(N);
+    L.r_out = c.take<char>(N * (dt == PP_FP64 ? 8 : 4));
+    size_t b1 = 0, b2 = 0, b3 = 0;
+    pp_sort_edges_workspace(M, scale, &b1);
+    pp_build_filter_normalize_workspace(M, scale, &b2);
+    pp_pagerank_workspace(M, scale, iters, dt, &b3);
+    L.scratch_bytes = std::max(b1, std::max(b2, b3));
+    L.scratch = c.take<char>(L.scratch_bytes);
+    L.bytes = c.size();
+    return L;
+}
+
+}  // namespace
+
+extern "C" pp_status pp_pipeline_workspace(uint64_t M, uint32_t scale, uint32_t iters, pp_dtype dt,
+                                           size_t *bytes) {
+    if (!bytes || scale < 1 || scale > 27 || M > (1ull << 31) || (int)dt < 0 || (int)dt > 2)
+        return PP_ERR_INVALID_ARG;
+    *bytes = pipe_layout(nullptr, M, scale, iters, dt).bytes;
+    return PP_OK;
+}
+
+extern "C" pp_status pp_pipeline_host(const uint32_t *u_host, const uint32_t *v_host, uint64_t M,
+                                      uint32_t scale, const double *r0_host, uint32_t iters, double c,
+                                      pp_dtype dt, pp_supernode_rule rule, void *r_out_host,
+                                      uint64_t *info_host, void *ws, size_t ws_bytes, void *stream) {
+    if (scale < 1 || scale > 27 || M > (1ull << 31) || (int)dt < 0 || (int)dt > 2) return PP_ERR_INVALID_ARG;
+    if ((M && (!u_host || !v_host)) || !r0_host || !r_out_host) return PP_ERR_INVALID_ARG;
+    const PipeLayout need = pipe_layout(nullptr, M, scale, iters, dt);
+    pp_status st = check_ws(ws, ws_bytes, need.bytes);
+    if (st != PP_OK) return st;
+    const PipeLayout L = pipe_layout(ws, M, scale, iters, dt);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const uint64_t N = 1ull << scale;
+    if (M) {
+        if (cudaMemcpyAsync(L.u, u_host, M * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) return PP_ERR_CUDA;
+        if (cudaMemcpyAsync(L.v, v_host, M * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) return PP_ERR_CUDA;
+    }
+    if (cudaMemcpyAsync(L.r0, r0_host, N * 8, cudaMemcpyHostToDevice, s) != cudaSuccess) return PP_ERR_CUDA;
+    st = pp_sort_edges(L.u, L.v, M, scale, L.us, L.vs, L.scratch, L.scratch_bytes, stream);
+    if (st != PP_OK) return st;
+    st = pp_build_filter_normalize(L.us, L.vs, M, scale, rule, &L.g, L.scratch, L.scratch_bytes, stream);
+    if (st != PP_OK) return st;
+    st = pp_pagerank(&L.g, L.r0, iters, c, dt, L.r_out, nullptr, L.scratch, L.scratch_bytes, stream);
+    if (st != PP_OK) return st;
+    if (cudaMemcpyAsync(r_out_host, L.r_out, N * (dt == PP_FP64 ? 8 : 4), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return PP_ERR_CUDA;
+    if (info_host &&
+        cudaMemcpyAsync(info_host, L.g.info, PP_INFO_LEN * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return PP_ERR_CUDA;
+    return PP_OK;
+}

@@ -1,0 +1,170 @@
+// Shared device/host helpers of libpp (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "../../include/pagerank_pipeline.h"
+
+// One device error word per translation unit (each .cu file gets its own
+// copy); pp_last_device_error() reads and clears all of them.
+static __device__ uint32_t pp_err_word;
+static __device__ __forceinline__ void pp_set_error(uint32_t bits) { atomicOr(&pp_err_word, bits); }
+
+namespace pp {
+
+// ------------------------------------------------------------------ host side
+
+// Number of kernels enqueued by the library (pp_launch_count).
+extern std::atomic<uint64_t> g_launches;
+
+inline void count_launch(uint64_t n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+inline int sm_count() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+inline uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+
+// Carves 256-byte aligned sub-buffers out of one workspace.  With base ==
+// nullptr it only measures, so the size query and the carve share one layout.
+struct Carver {
+    char *base;
+    size_t off = 0;
+    explicit Carver(void *b) : base(static_cast<char *>(b)) {}
+    template <typename T>
+    T *take(uint64_t count) {
+        off = (off + 255) & ~size_t(255);
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += size_t(count) * sizeof(T);
+        return p;
+    }
+    size_t size() const { return (off + 255) & ~size_t(255); }
+};
+
+inline pp_status check_ws(void *ws, size_t have, size_t need) {
+    if (need == 0) return PP_OK;
+    if (!ws || have < need || (reinterpret_cast<uintptr_t>(ws) & 255)) return PP_ERR_WORKSPACE;
+    return PP_OK;
+}
+
+inline pp_status launch_status() {
+    return cudaGetLastError() == cudaSuccess ? PP_OK : PP_ERR_CUDA;
+}
+
+// Longest poll of a cross-block wait before the kernel gives up and records
+// PP_DEV_TIMEOUT (about a second at 2 GHz with the back-off below).
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+// ---------------------------------------------------------------- device side
+
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u32(uint32_t *p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed_u64(uint64_t *p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ void backoff(uint32_t spin) {
+    if (spin > 64) __nanosleep(spin > 4096 ? 256 : 32);
+}
+
+// Inclusive warp scan (sum).
+template <typename T>
+__device__ __forceinline__ T warp_inclusive_sum(T x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+// Exclusive block scan (sum) of one value per thread; returns the exclusive
+// prefix and writes the block total to *total.  `scratch` holds >= 32 T.
+template <typename T, int THREADS>
+__device__ __forceinline__ T block_exclusive_sum(T x, T *scratch, T *total) {
+    constexpr int W = THREADS / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T inc = warp_inclusive_sum(x);
+    if (lane == 31) scratch[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        T w = lane < W ? scratch[lane] : T(0);
+        T wi = warp_inclusive_sum(w);
+        if (lane < W) scratch[lane] = wi - w;
+        if (lane == W - 1) scratch[W] = wi;
+    }
+    __syncthreads();
+    T r = scratch[warp] + inc - x;
+    *total = scratch[W];
+    __syncthreads();
+    return r;
+}
+
+// Block-wide sum with a fixed reduction tree (deterministic for floats).
+template <typename T, int THREADS>
+__device__ __forceinline__ T block_sum(T x, T *scratch) {
+    constexpr int W = THREADS / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) scratch[warp] = x;
+    __syncthreads();
+    T r = T(0);
+    if (warp == 0) {
+        r = lane < W ? scratch[lane] : T(0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    }
+    __syncthreads();
+    return r;  // valid in thread 0
+}
+
+}  // namespace pp
+
+// Host accessor of this translation unit's device error word.
+#define PP_DEFINE_ERROR_WORD(fetch_fn)                                                  \
+    namespace pp {                                                                      \
+    uint32_t fetch_fn(cudaStream_t s) {                                                 \
+        uint32_t v = 0, z = 0;                                                          \
+        if (cudaMemcpyFromSymbolAsync(&v, pp_err_word, sizeof v, 0,                     \
+                                      cudaMemcpyDeviceToHost, s) != cudaSuccess)        \
+            return 0xffffffffu;                                                         \
+        if (cudaMemcpyToSymbolAsync(pp_err_word, &z, sizeof z, 0,                       \
+                                    cudaMemcpyHostToDevice, s) != cudaSuccess)          \
+            return 0xffffffffu;                                                         \
+        if (cudaStreamSynchronize(s) != cudaSuccess) return 0xffffffffu;                \
+        return v;                                                                       \
+    }                                                                                   \
+    }

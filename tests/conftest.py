@@ -13,6 +13,18 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "slow: long-running; still part of its marker's suite")
 
 
+@pytest.fixture(scope="session", autouse=True)
+def built_libraries():
+    """Build (or confirm up to date) the input generator, the oracle and libpp."""
+    import kernel0.build
+    import oracle.build
+    import paper_1603_01876_gb300.build
+
+    kernel0.build.build()
+    oracle.build.build()
+    paper_1603_01876_gb300.build.build()
+
+
 @pytest.fixture(scope="session")
 def oracle_mod():
     import oracle
