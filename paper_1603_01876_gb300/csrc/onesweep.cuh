@@ -64,7 +64,7 @@ struct PassCtl {
 inline bool wide_status(uint64_t n_max) { return n_max >= (1ull << 30); }
 
 template <typename KeyT, typename StatT, bool HAS_VAL, class Src, class Dst>
-__global__ void __launch_bounds__(THREADS, 2) pass_kernel(Src src, Dst dst, PassCtl ctl) {
+__global__ void __launch_bounds__(THREADS, 3) pass_kernel(Src src, Dst dst, PassCtl ctl) {
     using F = Flags<StatT>;
     __shared__ KeyT s_keys[TILE];
     __shared__ uint32_t s_vals[HAS_VAL ? TILE : 1];
@@ -135,24 +135,33 @@ __global__ void __launch_bounds__(THREADS, 2) pass_kernel(Src src, Dst dst, Pass
     const uint32_t bstart = block_exclusive_sum<uint32_t, THREADS>(tcount, s_scan, &nvalid);
     s_binstart[tid] = bstart;
 
-    // Decoupled look-back for this digit.
+    // Decoupled look-back for this digit, four predecessors per round trip.
     StatT excl = 0;
     if (tile > 0) {
-        uint64_t p = tile - 1;
+        long long p = (long long)tile - 1;
         uint32_t spins = 0;
         while (true) {
-            const StatT s = ld_status(st + p * RADIX + tid);
-            if ((s & F::ANY) == 0) {
+            StatT s4[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) s4[q] = p - q >= 0 ? ld_status(st + (uint64_t)(p - q) * RADIX + tid) : StatT(0);
+            int used = 0;
+            bool done = false;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (done || used != q || (s4[q] & F::ANY) == 0) continue;
+                excl += s4[q] & F::VAL;
+                ++used;
+                if (s4[q] & F::INC) done = true;
+            }
+            if (done) break;
+            p -= used;  // tile 0 always publishes an inclusive word, so p stays >= 0
+            if (used == 0) {
                 if (++spins > kSpinLimit) {
                     pp_set_error(PP_DEV_TIMEOUT);
                     break;
                 }
                 backoff(spins);
-                continue;
             }
-            excl += s & F::VAL;
-            if (s & F::INC) break;
-            --p;  // tile 0 always publishes an inclusive word, so p stays >= 0
         }
         st_status(mine, F::INC | (excl + (StatT)tcount));
     }
@@ -229,6 +238,13 @@ inline SortWs carve_sort_ws(Carver &c, uint64_t n_max) {
 // before the histogram pass.
 constexpr size_t kCtlBytes = (MAX_PASSES * RADIX + MAX_PASSES) * sizeof(uint32_t);
 
+// Ask for the largest shared-memory carveout so that several 44 KB blocks fit per SM.
+template <typename K>
+inline bool prefer_shared(K kernel) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    return true;
+}
+
 // Launches pass `p` (of npasses) of a sort prepared in `w`.
 template <typename KeyT, bool HAS_VAL, class Src, class Dst>
 inline void launch_pass(const SortWs &w, int p, int npasses, Src src, Dst dst, const uint64_t *n_dev,
@@ -242,10 +258,15 @@ inline void launch_pass(const SortWs &w, int p, int npasses, Src src, Dst dst, c
     ctl.n_dev = n_dev;
     ctl.n_host = n_max;
     const unsigned grid = (unsigned)ceil_div(n_max ? n_max : 1, TILE);
-    if (w.wide)
+    if (w.wide) {
+        static const bool once = prefer_shared(pass_kernel<KeyT, uint64_t, HAS_VAL, Src, Dst>);
+        (void)once;
         pass_kernel<KeyT, uint64_t, HAS_VAL, Src, Dst><<<grid, THREADS, 0, s>>>(src, dst, ctl);
-    else
+    } else {
+        static const bool once = prefer_shared(pass_kernel<KeyT, uint32_t, HAS_VAL, Src, Dst>);
+        (void)once;
         pass_kernel<KeyT, uint32_t, HAS_VAL, Src, Dst><<<grid, THREADS, 0, s>>>(src, dst, ctl);
+    }
     count_launch();
 }
 

@@ -48,4 +48,6 @@ def oracle_triples(R):
 def rank_errors(got, want):
     got = np.asarray(got, dtype=np.float64)
     d = np.abs(got - want)
-    return {"l1": float(d.sum() / np.abs(want).sum()), "max_rel": float((d / np.abs(want)).max())}
+    nz = want != 0
+    mr = float((d[nz] / np.abs(want[nz])).max()) if nz.any() else 0.0
+    return {"l1": float(d.sum() / np.abs(want).sum()), "max_rel": mr, "zero_mismatch": float(d[~nz].max(initial=0))}
