@@ -327,6 +327,45 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_k3_only(args):
+    """Kernel 3 alone on a graph built by Kernels 1-2, with everything else freed
+    (about 1.6 GB resident at scale 24): for per-kernel timing and profiling."""
+    import torch
+
+    import kernel0
+    import paper_1603_01876_gb300 as pp
+
+    dev = torch.device("cuda", 0)
+    scale, iters = args.scale, ITERS
+    N = 1 << scale
+    M = 16 * N
+    u, v = kernel0.edges_device(scale, SEED, device=dev)
+    us, vs = pp.sort_edges(u, v, scale)
+    del u, v
+    g = pp.build_filter_normalize(us, vs, scale, "lowest")
+    info = g.info_dict()
+    del us, vs
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    r0 = torch.from_numpy(kernel0.r0_host(N, SEED)).to(dev)
+    ws = torch.empty(pp.workspace_bytes("pagerank", M, scale, iters, args.dtype), dtype=torch.uint8, device=dev)
+    out = torch.empty(N, dtype=torch.float64 if args.dtype == "fp64" else torch.float32, device=dev)
+    for _ in range(args.warmup):
+        pp.pagerank(g, r0, iters, DAMPING, args.dtype, out=out, workspace=ws)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e[0].record()
+    for _ in range(args.steps):
+        pp.pagerank(g, r0, iters, DAMPING, args.dtype, out=out, workspace=ws)
+    e[1].record()
+    torch.cuda.synchronize()
+    ms = e[0].elapsed_time(e[1]) / args.steps
+    b = k3_bytes_per_iter(info["nnz"], N, args.dtype) * iters
+    print(json.dumps({"stage": "k3", "scale": scale, "dtype": args.dtype, "tune": args.tune, "ms": ms, "nnz": info["nnz"],
+                      "edges_per_s": iters * M / (ms * 1e-3), "gbs": b / ms / 1e6,
+                      "device_error": pp.last_device_error()}))
+
+
 def cpu_baseline(scale, seed, max_seconds=20.0, sample_div=16):
     """The oracle, single-threaded, on the first M/sample_div edges of the same edge list."""
     import kernel0
@@ -404,8 +443,20 @@ def main():
     ap.add_argument("--dtype", choices=["fp32", "fp64", "bf16"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--tune", action="append", default=[], metavar="KEY=VALUE",
+                    help="set a library tuning knob before running (repeatable)")
+    ap.add_argument("--stage", choices=["all", "k3"], default="all",
+                    help="k3: time Kernel 3 alone (profiling aid); the default times the whole pipeline")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.tune:
+        import paper_1603_01876_gb300 as pp
+
+        for kv in args.tune:
+            k, v = kv.split("=")
+            pp.set_tuning(k, int(v))
+    if args.stage == "k3":
+        run_k3_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

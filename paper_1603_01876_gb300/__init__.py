@@ -73,6 +73,10 @@ def _lib():
             f.restype = ctypes.c_int
         L.pp_status_string.argtypes = [ctypes.c_int]
         L.pp_status_string.restype = ctypes.c_char_p
+        L.pp_set_tuning.argtypes = [ctypes.c_char_p, ctypes.c_int64]
+        L.pp_set_tuning.restype = ctypes.c_int
+        L.pp_get_tuning.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_int64)]
+        L.pp_get_tuning.restype = ctypes.c_int
         L.pp_launch_count.argtypes = []
         L.pp_launch_count.restype = ctypes.c_uint64
         _L = L
@@ -101,6 +105,17 @@ def _ptr(t):
 def _workspace(nbytes, device):
     # torch's caching allocator returns 512-byte aligned blocks
     return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+def set_tuning(key, value):
+    """Set a library tuning knob (see pp_set_tuning in include/pagerank_pipeline.h)."""
+    _check("pp_set_tuning(%s=%r)" % (key, value), _lib().pp_set_tuning(key.encode(), int(value)))
+
+
+def get_tuning(key):
+    v = ctypes.c_int64(0)
+    _check("pp_get_tuning(%s)" % key, _lib().pp_get_tuning(key.encode(), ctypes.byref(v)))
+    return int(v.value)
 
 
 def launch_count():

@@ -4,21 +4,25 @@
 //
 // as a pull over Kernel 2's compressed columns.  With A(u,v) = count(u,v) /
 // d_out(u), the sum over a column is sum_e count_e * x(u_e) for the vector
-// x = r .* (1/d_out), which each iteration writes for the next one; so the
-// row normalisation is folded into the gathered vector and the matrix is
-// read as packed (row, count) words only.
+// x = r .* (1/d_out), which each iteration writes for the next one: the row
+// normalisation is folded into the gathered vector and the matrix is read as
+// packed (row, count) words only.
 //
-// Work split: a merge path over the sequence of column ends and entries
-// (Merrill & Garland, "Merge-based parallel sparse matrix-vector
-// multiplication", SC'16) cuts the columns + entries into equal tiles, so
-// empty, short and very long columns all cost the same per item.  A tile
-// stages its column ends in shared memory, gathers count * x(u) for its
-// entries with coalesced index loads, reduces each column by a segmented
-// scan, and finishes the columns that end inside it: r = c*y + teleport and
-// x' = r / d_out(v).  A column that started in earlier tiles adds their
-// published partial sums in a fixed order.  sum(r) for the next iteration is
-// accumulated exactly in 128-bit fixed point, so it does not depend on which
-// block took which tile and results are bitwise reproducible.
+// Work split by column length (a degree-bucketed pull SpMV), one warp per
+// work item and no block-wide barriers, so each warp's gathers overlap other
+// warps' arithmetic:
+//   - a column longer than SHORTMAX entries is cut into chunks of CHUNK
+//     entries; a warp sums a chunk with coalesced index loads and a group of
+//     gathers in flight per lane, reduces it in a fixed shuffle tree, and the
+//     warp that finishes a column's last chunk adds the chunk sums in order;
+//   - the other columns form tiles of at most 32 consecutive columns and
+//     2*SHORTMAX entries; a warp gathers count * x(u) for the tile's entries
+//     into its shared-memory slab, then each lane sums one short column in
+//     order, and the whole warp takes each medium column (lanes stride, fixed
+//     shuffle tree).
+// Items are dealt to warps round-robin.  Every column sum has a fixed order
+// and sum(r) is accumulated exactly in 128-bit fixed point, so results are
+// bitwise reproducible whichever warp takes which item.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -31,16 +35,17 @@ namespace pp {
 namespace k3 {
 
 constexpr int THREADS = 256;
-constexpr int ITEMS_F32 = 12;       // merge items per thread: binary32 / bfloat16 ranks
-constexpr int ITEMS_F64 = 8;        // binary64 ranks (twice the shared memory per item)
-constexpr int D_MIN = THREADS * ITEMS_F64;
-constexpr int SETUP_BLOCKS = 512;   // fixed, so the start-vector reduction is reproducible
-
-struct Carry {
-    double val;
-    uint32_t col;
-    uint32_t epoch;
-};
+constexpr int WARPS = THREADS / 32;
+constexpr int TILE_COLS = 32;      // one lane per column in a tile
+constexpr int SHORTMAX = 256;      // columns longer than this are cut into chunks
+constexpr int TILE_ENTRIES = 2 * SHORTMAX;
+constexpr int CHUNK = 2048;        // entries of a long column per work item
+constexpr int LANE_SHORT = 16;     // columns up to this long are summed by one lane
+constexpr uint32_t LONG_FLAG = 0x80000000u;
+constexpr int SETUP_BLOCKS = 512;  // fixed, so the start-vector reduction is reproducible
+constexpr int PLAN_THREADS = 256;
+constexpr int PLAN_ITEMS = 16;
+constexpr int PLAN_TILE = PLAN_THREADS * PLAN_ITEMS;
 
 __device__ __forceinline__ float to_acc(float x) { return x; }
 __device__ __forceinline__ float to_acc(__nv_bfloat16 x) { return __bfloat162float(x); }
@@ -56,25 +61,28 @@ __device__ __forceinline__ TS from_acc(double x) { return x; }
 
 // Control words in the workspace.
 struct Ctl {
-    uint32_t ntiles;
-    uint32_t pad[3];
+    uint32_t n_items;  // work items (tiles and long-column chunks)
+    uint32_t n_bound;  // columns that start a tile or a long column
+    uint32_t pad[2];
 };
 
 struct Args {
     uint32_t N, scale, cmax, iters;
-    uint32_t D;         // merge items per tile
     const uint32_t *colptr, *rowc;
     const uint64_t *ovf_key;
     const uint32_t *ovf_cnt;
     const uint64_t *info;
-    uint2 *coord;       // [max_tiles + 1] (column, entry) at each tile's start
-    Carry *carry;       // [max_tiles]
-    unsigned long long *acc;  // [2 * (iters + 1)]: sum(r) before each iteration (and of
-                              // the result) in 128-bit fixed point, hi then lo
-    int *fx_exp;              // [iters + 1]: the scale exponent E of each accumulator
-    double *ipart;      // [SETUP_BLOCKS]
+    uint32_t *bound;          // [N] boundary columns, ascending (plan)
+    uint32_t *bound_item;     // [N] index of each boundary's first work item
+    uint4 *item;              // [N + M/CHUNK + 1] work items, see plan_items_kernel
+    double *chunk_sum;        // [same] partial sums of long-column chunks
+    uint32_t *ticket;         // [same] finished-chunk counters, at a column's first item
+    uint64_t *plan_status;    // [N / PLAN_TILE + 1] look-back words of the plan scan
+    unsigned long long *acc;  // [2 * (iters + 1)] sum(r) per iterate, 128-bit fixed point
+    int *fx_exp;              // [iters + 1] scale exponent of each accumulator
+    double *ipart;            // [SETUP_BLOCKS]
     Ctl *ctl;
-    uint32_t *tile_ctr; // [iters]
+    uint32_t *ctr;            // [1] plan tile counter
     double c;
 };
 
@@ -91,32 +99,137 @@ __device__ __forceinline__ uint32_t ovf_lookup(const uint64_t *keys, const uint3
     return (lo < n && __ldg(keys + lo) == key) ? __ldg(cnts + lo) : 0u;
 }
 
-// Plan the tiles, reset the per-call counters and sum |r0|.
+// ------------------------------------------------------------------- planning
+
+constexpr uint64_t F_AGG = 1ull << 62, F_INC = 2ull << 62, F_ANY = 3ull << 62;
+
+// Column v starts a work item if it is long, follows a long column, starts in
+// a new SHORTMAX-entry chunk of the entry array, or is a multiple of
+// TILE_COLS.  So a tile holds at most TILE_COLS columns, all starting in one
+// chunk, and its last column ends at most SHORTMAX entries past that chunk:
+// at most 2*SHORTMAX entries.
+__device__ __forceinline__ void classify(const uint32_t *colptr, uint32_t v, bool &bound, uint32_t &nitems) {
+    const uint32_t s = __ldg(colptr + v), e = __ldg(colptr + v + 1);
+    const bool is_long = e - s > (uint32_t)SHORTMAX;
+    nitems = is_long ? (e - s + CHUNK - 1) / CHUNK : 1u;
+    bound = true;
+    if (v == 0 || is_long || v % TILE_COLS == 0) return;
+    const uint32_t ps = __ldg(colptr + v - 1);
+    if (s - ps > (uint32_t)SHORTMAX) return;  // the previous column is long
+    bound = (s / SHORTMAX) != (ps / SHORTMAX);
+}
+
+// Compacts the boundary columns in order and numbers their work items (one
+// look-back scan of two packed counters: boundaries, items).
+__global__ void __launch_bounds__(PLAN_THREADS) plan_kernel(Args a) {
+    __shared__ uint32_t s_tile;
+    __shared__ uint64_t s_scan[40];
+    __shared__ uint64_t s_excl;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_tile = atomicAdd(a.ctr, 1u);
+    __syncthreads();
+    const uint64_t tile = s_tile;
+    const uint64_t ntiles = (a.N + PLAN_TILE - 1) / PLAN_TILE;
+    if (tile >= ntiles) return;
+    const uint64_t v0 = tile * PLAN_TILE + (uint64_t)tid * PLAN_ITEMS;
+    uint32_t bmask = 0, nitems = 0;
+#pragma unroll
+    for (int j = 0; j < PLAN_ITEMS; ++j) {
+        const uint64_t v = v0 + j;
+        if (v < a.N) {
+            bool b;
+            uint32_t ni;
+            classify(a.colptr, (uint32_t)v, b, ni);
+            if (b) {
+                bmask |= 1u << j;
+                nitems += ni;
+            }
+        }
+    }
+    // bits 30:0 count boundaries, bits 61:31 work items
+    const uint64_t mine = (uint64_t)__popc(bmask) | ((uint64_t)nitems << 31);
+    uint64_t total;
+    const uint64_t texcl = block_exclusive_sum<uint64_t, PLAN_THREADS>(mine, s_scan, &total);
+    if (tid == 0) {
+        uint64_t *st = a.plan_status + tile;
+        uint64_t ex = 0;
+        if (tile == 0) {
+            st_relaxed_u64(st, F_INC | total);
+        } else {
+            st_relaxed_u64(st, F_AGG | total);
+            uint64_t p = tile - 1;
+            uint32_t spins = 0;
+            while (true) {
+                const uint64_t sv = ld_relaxed_u64(a.plan_status + p);
+                if ((sv & F_ANY) == 0) {
+                    if (++spins > kSpinLimit) {
+                        pp_set_error(PP_DEV_TIMEOUT);
+                        break;
+                    }
+                    backoff(spins);
+                    continue;
+                }
+                ex += sv & ~F_ANY;
+                if (sv & F_INC) break;
+                --p;  // tile 0 always publishes an inclusive word
+            }
+            st_relaxed_u64(st, F_INC | (ex + total));
+        }
+        s_excl = ex;
+        if (tile == ntiles - 1) {
+            const uint64_t inc = ex + total;
+            a.ctl->n_bound = (uint32_t)(inc & 0x7fffffffull);
+            a.ctl->n_items = (uint32_t)(inc >> 31);
+        }
+    }
+    __syncthreads();
+    const uint64_t g = s_excl + texcl;
+    uint32_t bi = (uint32_t)(g & 0x7fffffffull), ii = (uint32_t)(g >> 31);
+#pragma unroll
+    for (int j = 0; j < PLAN_ITEMS; ++j) {
+        if (!(bmask >> j & 1u)) continue;
+        const uint32_t v = (uint32_t)(v0 + j);
+        a.bound[bi] = v;
+        a.bound_item[bi] = ii;
+        const uint32_t s = __ldg(a.colptr + v), e = __ldg(a.colptr + v + 1);
+        ii += e - s > (uint32_t)SHORTMAX ? (e - s + CHUNK - 1) / CHUNK : 1u;
+        ++bi;
+    }
+}
+
+// Writes the work items of each boundary, so that a warp can start loading
+// entries without reading the column pointers first:
+//   tile:        (first column, number of columns, first entry, entries)
+//   long chunk:  (column | LONG_FLAG, first item of the column, first entry,
+//                 entries | chunks of the column << 12)
+// A tile runs to the next boundary; a long column gets one item per chunk.
+__global__ void __launch_bounds__(256) plan_items_kernel(Args a) {
+    const uint32_t nb = a.ctl->n_bound;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x) {
+        const uint32_t v = a.bound[i], o = a.bound_item[i];
+        const uint32_t s = __ldg(a.colptr + v), e = __ldg(a.colptr + v + 1);
+        if (e - s > (uint32_t)SHORTMAX) {
+            const uint32_t nc = (e - s + CHUNK - 1) / CHUNK;
+            for (uint32_t k = 0; k < nc; ++k) {
+                const uint32_t cs = s + k * CHUNK;
+                a.item[o + k] = make_uint4(v | LONG_FLAG, o, cs, min((uint32_t)CHUNK, e - cs) | (nc << 12));
+                a.ticket[o + k] = 0;
+            }
+        } else {
+            const uint32_t c1 = i + 1 < nb ? a.bound[i + 1] : a.N;
+            a.item[o] = make_uint4(v, c1 - v, s, __ldg(a.colptr + c1) - s);
+        }
+    }
+}
+
+// Reset the per-call counters and sum |r0|.
 __global__ void __launch_bounds__(256) setup_kernel(Args a, const double *r0) {
     __shared__ double s_red[32];
-    const uint64_t nnz = a.info[PP_INFO_NNZ];
-    const uint64_t total = (uint64_t)a.N + nnz;
-    const uint64_t D = a.D;
-    const uint32_t ntiles = (uint32_t)((total + D - 1) / D);
     const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    if (gtid == 0) a.ctl->ntiles = ntiles;
-    for (uint64_t t = gtid; t <= ntiles; t += stride) {
-        const uint64_t diag = std::min<uint64_t>(t * D, total);
-        // merge path: column end i (= colptr[i+1]) comes before entry j iff colptr[i+1] <= j
-        uint64_t lo = diag > nnz ? diag - nnz : 0, hi = std::min<uint64_t>(diag, a.N);
-        while (lo < hi) {
-            const uint64_t pivot = (lo + hi) >> 1;
-            if ((uint64_t)__ldg(a.colptr + pivot + 1) + pivot + 1 <= diag)
-                lo = pivot + 1;
-            else
-                hi = pivot;
-        }
-        a.coord[t] = make_uint2((uint32_t)lo, (uint32_t)(diag - lo));
-    }
-    for (uint64_t t = gtid; t < ntiles; t += stride) a.carry[t].epoch = 0;
-    for (uint64_t i = gtid; i < a.iters; i += stride) a.tile_ctr[i] = 0;
+    if (gtid == 0) a.ctr[0] = 0;
     for (uint64_t i = gtid; i < 2ull * (a.iters + 1); i += stride) a.acc[i] = 0;
+    for (uint64_t i = gtid; i < (a.N + PLAN_TILE - 1) / PLAN_TILE; i += stride) a.plan_status[i] = 0;
     if (gtid == 0) a.fx_exp[0] = 1;  // the normalised start vector has every entry <= 1 < 2^1
     double acc = 0.0;
     for (uint64_t i = gtid; i < a.N; i += stride) acc += fabs(r0[i]);
@@ -124,12 +237,14 @@ __global__ void __launch_bounds__(256) setup_kernel(Args a, const double *r0) {
     if (threadIdx.x == 0) a.ipart[blockIdx.x] = bs;
 }
 
+// ----------------------------------------------------------- exact sum(r)
+
 // Exact, order-independent accumulation of non-negative doubles in 128-bit
 // fixed point whose last bit is worth 2^(E-100), where 2^E bounds every term
 // (E is derived from the previous sum(r), which bounds every new rank because
 // the update never increases the total).  Any grouping of the same terms
 // gives the same bits, so sum(r) does not depend on which block took which
-// tile, and terms below 2^(E-100) are the only ones truncated.
+// item, and only terms below 2^(E-100) lose bits.
 struct Fx128 {
     uint64_t hi, lo;
 };
@@ -139,12 +254,9 @@ __device__ __forceinline__ void fx_add(Fx128 &a, uint64_t h, uint64_t l) {
     a.hi += h + (a.lo < l ? 1ull : 0ull);
 }
 
-__device__ __forceinline__ void fx_add(Fx128 &a, double x, int E) {
-    if (!(x > 0.0)) return;
-    const uint64_t bits = (uint64_t)__double_as_longlong(x);
-    const int e = (int)((bits >> 52) & 0x7ff);
-    const uint64_t m = (bits & ((1ull << 52) - 1)) | (e ? (1ull << 52) : 0ull);
-    const int sh = (e ? e : 1) - 1075 + 100 - E;  // x = m * 2^(sh + E - 100)
+// m * 2^sh as a 128-bit integer (m < 2^53; the caller's bound on E keeps
+// sh + 53 <= 128), integer instructions only.
+__device__ __forceinline__ void fx_add_shifted(Fx128 &a, uint64_t m, int sh) {
     uint64_t h = 0, l = 0;
     if (sh <= -64) {
         return;
@@ -155,12 +267,29 @@ __device__ __forceinline__ void fx_add(Fx128 &a, double x, int E) {
     } else if (sh < 64) {
         l = m << sh;
         h = m >> (64 - sh);
-    } else if (sh < 75) {
-        h = m << (sh - 64);
     } else {
-        h = ~0ull;  // cannot happen for terms below 2^(E+11); saturate rather than wrap
+        h = m << (sh - 64);
     }
     fx_add(a, h, l);
+}
+
+// x * 2^(100-E) from the bits of x (x >= 0; 0, negative and NaN add nothing).
+__device__ __forceinline__ void fx_add(Fx128 &a, double x, int E) {
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    if ((long long)b <= 0) return;
+    const int e = (int)(b >> 52);
+    if (e == 0x7ff) return;
+    const uint64_t m = (b & ((1ull << 52) - 1)) | (e ? (1ull << 52) : 0ull);
+    fx_add_shifted(a, m, (e ? e : 1) - 1075 + 100 - E);  // x = m * 2^((e?e:1) - 1075)
+}
+
+__device__ __forceinline__ void fx_add(Fx128 &a, float x, int E) {
+    const uint32_t b = __float_as_uint(x);
+    if ((int)b <= 0) return;
+    const int e = (int)(b >> 23);
+    if (e == 0xff) return;
+    const uint64_t m = (b & 0x7fffffu) | (e ? 0x800000u : 0u);
+    fx_add_shifted(a, m, (e ? e : 1) - 150 + 100 - E);  // x = m * 2^((e?e:1) - 150)
 }
 
 __device__ __forceinline__ double fx_value(uint64_t hi, uint64_t lo, int E) {
@@ -201,9 +330,6 @@ __device__ __forceinline__ void fx_atomic_add(unsigned long long *acc /* [hi, lo
     if (v.hi + carry) atomicAdd(acc, (unsigned long long)(v.hi + carry));
 }
 
-template <typename TS>
-__device__ __forceinline__ TS ldg_x(const TS *p) { return __ldg(p); }
-
 // r = r0 / norm(r0,1) rounded to the working precision; x = r / d_out; and
 // sum(r) of that vector.  With iters == 0 the normalised r is the result.
 template <typename TS, typename TA, typename TO>
@@ -222,7 +348,7 @@ __global__ void __launch_bounds__(256) normalize_kernel(Args a, const double *r0
     Fx128 acc{0, 0};
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += stride) {
         const TA r = (TA)(r0[i] / norm);
-        fx_add(acc, (double)r, 1);
+        fx_add(acc, r, 1);
         x0[i] = from_acc<TS>(r * inv[i]);
         if (a.iters == 0) r_out[i] = (TO)r;
     }
@@ -230,204 +356,211 @@ __global__ void __launch_bounds__(256) normalize_kernel(Args a, const double *r0
     if (threadIdx.x == 0 && (bt.hi | bt.lo)) fx_atomic_add(a.acc, bt);
 }
 
-// One iteration.  Persistent: each block claims tiles in order from a counter
-// (the next claim is issued while the current tile is processed).
-template <typename TS, typename TA, typename TO, bool LAST, int ITEMS>
+// ------------------------------------------------------------- the iteration
+
+// Gathered-vector loads and stores, kept in L2 (evict-last).
+__device__ __forceinline__ float ld_x(const float *p, uint64_t pol) { return ld_hint(p, pol); }
+__device__ __forceinline__ double ld_x(const double *p, uint64_t pol) { return ld_hint(p, pol); }
+__device__ __forceinline__ __nv_bfloat16 ld_x(const __nv_bfloat16 *p, uint64_t pol) {
+    return __ushort_as_bfloat16(ld_hint_b16(p, pol));
+}
+__device__ __forceinline__ void st_x(float *p, float v, uint64_t pol) { st_hint(p, v, pol); }
+__device__ __forceinline__ void st_x(double *p, double v, uint64_t pol) { st_hint(p, v, pol); }
+__device__ __forceinline__ void st_x(__nv_bfloat16 *p, __nv_bfloat16 v, uint64_t pol) {
+    st_hint_b16(p, __bfloat16_as_ushort(v), pol);
+}
+__device__ __forceinline__ float ld_inv(const float *p, uint64_t pol) { return ld_hint(p, pol); }
+__device__ __forceinline__ double ld_inv(const double *p, uint64_t pol) { return ld_hint(p, pol); }
+
+// Finishes column `col` from its sum y: r = c*y + teleport, x' = r / d_out.
+template <typename TS, typename TA, typename TO, bool LAST>
+struct Epilogue {
+    const TA *inv;
+    TS *x_out;
+    TO *r_out;
+    TA cc, tele;
+    uint64_t keep, stream;
+    int E;
+    __device__ __forceinline__ void operator()(uint32_t col, TA y, TA inv_col, Fx128 &acc) const {
+        const TA r = cc * y + tele;
+        if (LAST) r_out[col] = (TO)r;
+        st_x(x_out + col, from_acc<TS>(r * inv_col), keep);
+        fx_add(acc, r, E);
+    }
+};
+
+// count * x(u) of one packed entry of column `col` (the column is only needed,
+// and only valid, when the count did not fit inline).
+template <typename TA>
+__device__ __forceinline__ TA entry_product(uint32_t w, TA xv, uint32_t col, const Args &a) {
+    uint32_t cf = w >> a.scale;
+    if (cf == a.cmax) {
+        const uint32_t u = w & ((1u << a.scale) - 1u);
+        cf = ovf_lookup(a.ovf_key, a.ovf_cnt, a.info[PP_INFO_NOVF], ((uint64_t)u << 32) | col);
+    }
+    return (TA)cf * xv;
+}
+
+template <typename TA>
+__device__ __forceinline__ TA warp_sum(TA y) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) y += __shfl_down_sync(0xffffffffu, y, o);
+    return y;  // in lane 0
+}
+
+template <typename TS, typename TA, typename TO, bool LAST, int UNROLL>
 __global__ void __launch_bounds__(THREADS) iterate_kernel(Args a, const TA *inv, const TS *__restrict__ x_in,
                                                           TS *__restrict__ x_out, TO *r_out, uint32_t iter) {
-    constexpr int DT = THREADS * ITEMS;
-    constexpr int W = THREADS / 32;
-    __shared__ uint32_t s_colend[DT];
-    __shared__ TA s_prod[DT];
-    __shared__ TA s_y[DT];
-    __shared__ TA s_wv[W];
-    __shared__ int s_wf[W];
-    __shared__ uint64_t s_fx[2 * W];
-    __shared__ TA s_tcin;
-    __shared__ uint32_t s_next;
+    static_assert(TILE_ENTRIES % (32 * UNROLL) == 0 && CHUNK % (32 * UNROLL) == 0, "unroll must divide the work");
+    __shared__ TA s_prod[WARPS][TILE_ENTRIES];
+    __shared__ uint32_t s_cp[WARPS][TILE_COLS + 1];
+    __shared__ uint64_t s_fx[2 * WARPS];
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t ntiles = a.ctl->ntiles;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t n_items = a.ctl->n_items;
     const double S = fx_value(a.acc[2 * iter], a.acc[2 * iter + 1], a.fx_exp[iter]);
     const int E = fx_exponent(S);
     if (blockIdx.x == 0 && threadIdx.x == 0) a.fx_exp[iter + 1] = E;
-    const TA tele = (TA)(((1.0 - a.c) / (double)a.N) * S);
-    const TA cc = (TA)a.c;
     const uint32_t umask = (1u << a.scale) - 1u;
-    const uint32_t epoch = iter + 1;
-    uint32_t *ctr = a.tile_ctr + iter;
+    const uint64_t keep = policy_evict_last(), stream = policy_evict_first();
+    const Epilogue<TS, TA, TO, LAST> epi{inv, x_out, r_out, (TA)a.c, (TA)(((1.0 - a.c) / (double)a.N) * S),
+                                         keep, stream, E};
+    TA *prod = s_prod[warp];
+    uint32_t *cp = s_cp[warp];
     Fx128 acc{0, 0};
+    const uint32_t nwarps = gridDim.x * WARPS;
 
-    if (tid == 0) s_next = atomicAdd(ctr, 1u);
-    __syncthreads();
-    while (true) {
-        const uint32_t t = s_next;
-        if (t >= ntiles) break;
-        uint32_t nxt = 0;
-        if (tid == 0) nxt = atomicAdd(ctr, 1u);
-        const uint2 c0 = a.coord[t], c1 = a.coord[t + 1];
-        const uint32_t i0 = c0.x, j0 = c0.y;
-        const int ncol = (int)(c1.x - c0.x), nent = (int)(c1.y - c0.y);
-
-        for (int k = tid; k < ncol; k += THREADS) s_colend[k] = __ldg(a.colptr + i0 + 1 + k);
-
-        // Gather count * x(u): all index loads first, then all gathers.
-        uint32_t w[ITEMS];
+    uint32_t item = blockIdx.x * WARPS + warp;
+    uint4 it = item < n_items ? __ldg(a.item + item) : make_uint4(0, 0, 0, 0);
+    while (item < n_items) {
+        // the next item's descriptor is fetched while this one is processed
+        const uint32_t next = item + nwarps;
+        const uint4 nit = next < n_items ? __ldg(a.item + next) : make_uint4(0, 0, 0, 0);
+        const uint32_t e0 = it.z;
+        if (it.x & LONG_FLAG) {
+            // ---- one chunk of a long column
+            const uint32_t col = it.x & ~LONG_FLAG, first = it.y;
+            const uint32_t nent = it.w & 0xfffu, nchunks = it.w >> 12;
+            TA part = TA(0);
+            for (uint32_t base = 0; base < nent; base += 32 * UNROLL) {
+                uint32_t w[UNROLL];
+                TA xv[UNROLL];
 #pragma unroll
-        for (int m = 0; m < ITEMS; ++m) {
-            const int k = tid + m * THREADS;
-            w[m] = k < nent ? __ldg(a.rowc + j0 + k) : 0u;
-        }
-        TA xv[ITEMS];
+                for (int m = 0; m < UNROLL; ++m) {
+                    const uint32_t k = base + (uint32_t)(m * 32 + lane);
+                    w[m] = k < nent ? ld_stream_u32(a.rowc + e0 + k, stream) : 0u;
+                }
 #pragma unroll
-        for (int m = 0; m < ITEMS; ++m) {
-            const int k = tid + m * THREADS;
-            xv[m] = k < nent ? to_acc(ldg_x(x_in + (w[m] & umask))) : TA(0);
-        }
-        int esc = 0;
+                for (int m = 0; m < UNROLL; ++m) {
+                    const uint32_t k = base + (uint32_t)(m * 32 + lane);
+                    xv[m] = k < nent ? to_acc(ld_x(x_in + (w[m] & umask), keep)) : TA(0);
+                }
 #pragma unroll
-        for (int m = 0; m < ITEMS; ++m) {
-            const int k = tid + m * THREADS;
-            if (k < nent) {
-                const uint32_t cf = w[m] >> a.scale;
-                esc |= cf == a.cmax;
-                s_prod[k] = (TA)cf * xv[m];
-            }
-        }
-        if (__syncthreads_or(esc)) {
-            // a count that did not fit inline: find its column, then the overflow entry
-#pragma unroll
-            for (int m = 0; m < ITEMS; ++m) {
-                const int k = tid + m * THREADS;
-                if (k < nent && (w[m] >> a.scale) == a.cmax) {
-                    int lo = 0, hi = ncol;
-                    while (lo < hi) {
-                        const int mid = (lo + hi) >> 1;
-                        if (s_colend[mid] <= j0 + (uint32_t)k)
-                            lo = mid + 1;
-                        else
-                            hi = mid;
-                    }
-                    const uint32_t u = w[m] & umask, v = i0 + (uint32_t)lo;
-                    s_prod[k] = (TA)ovf_lookup(a.ovf_key, a.ovf_cnt, a.info[PP_INFO_NOVF], ((uint64_t)u << 32) | v) * xv[m];
+                for (int m = 0; m < UNROLL; ++m) {
+                    const uint32_t k = base + (uint32_t)(m * 32 + lane);
+                    if (k < nent) part += entry_product<TA>(w[m], xv[m], col, a);
                 }
             }
-            __syncthreads();
-        }
-
-        // This thread's stretch of the merge path: first walk finds where its
-        // first column ends and its open partial sum.
-        const int total = ncol + nent;
-        const int d0 = min(tid * ITEMS, total), d1 = min(d0 + ITEMS, total);
-        int lo = max(d0 - nent, 0), hi = min(d0, ncol);
-        while (lo < hi) {
-            const int pivot = (lo + hi) >> 1;
-            if ((int)(s_colend[pivot] - j0) <= d0 - pivot - 1)
-                lo = pivot + 1;
-            else
-                hi = pivot;
-        }
-        const int ci0 = lo, ej0 = d0 - lo;
-        TA running = TA(0);
-        int f = 0;
-        {
-            int ci = ci0, ej = ej0;
-            for (int it = d0; it < d1; ++it) {
-                if (ci < ncol && (int)(s_colend[ci] - j0) <= ej) {
-                    f = 1;
-                    running = TA(0);
-                    ++ci;
+            const TA y = warp_sum(part);
+            if (lane == 0) {
+                if (nchunks == 1) {
+                    epi(col, y, ld_inv(inv + col, stream), acc);
                 } else {
-                    running += s_prod[ej];
-                    ++ej;
+                    // the warp finishing the column's last chunk adds the chunk sums in order
+                    a.chunk_sum[item] = (double)y;
+                    __threadfence();
+                    const uint32_t t = atomicAdd(a.ticket + first, 1u);
+                    if ((t + 1) % nchunks == 0) {
+                        __threadfence();
+                        TA tot = TA(0);
+                        for (uint32_t q = 0; q < nchunks; ++q) tot += (TA)__ldcg(a.chunk_sum + first + q);
+                        epi(col, tot, ld_inv(inv + col, stream), acc);
+                    }
                 }
             }
-        }
-        // Segmented scan of the open partial sums in thread order.
-        TA v = running;
-        int fl = f;
+        } else {
+            // ---- a tile of up to 32 short columns
+            const uint32_t c0 = it.x, ncol = it.y, nent = it.w;
+            // column starts and 1/d_out of lane's column, in flight with the entries
+            const uint32_t mycp = lane < (int)ncol ? ld_stream_u32(a.colptr + c0 + lane, stream) : 0u;
+            const TA myinv = lane < (int)ncol ? ld_inv(inv + c0 + lane, stream) : TA(0);
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const TA vu = __shfl_up_sync(0xffffffffu, v, o);
-            const int fu = __shfl_up_sync(0xffffffffu, fl, o);
-            if (lane >= o) {
-                if (!fl) v = vu + v;
-                fl |= fu;
-            }
-        }
-        if (lane == 31) {
-            s_wv[warp] = v;
-            s_wf[warp] = fl;
-        }
-        TA ev = __shfl_up_sync(0xffffffffu, v, 1);
-        int ef = __shfl_up_sync(0xffffffffu, fl, 1);
-        if (lane == 0) {
-            ev = TA(0);
-            ef = 0;
-        }
-        if (tid == 0) s_tcin = TA(0);
-        __syncthreads();
-        TA wc = TA(0);
-        for (int q = 0; q < warp; ++q) wc = s_wf[q] ? s_wv[q] : wc + s_wv[q];
-        const TA cin = ef ? ev : wc + ev;
-        if (tid == THREADS - 1) {
-            // this tile's own partial sum of column c1.x, which ends in a later tile
-            a.carry[t].val = (double)(fl ? v : wc + v);
-            a.carry[t].col = c1.x;
-            st_release_u32(&a.carry[t].epoch, epoch);
-        }
-        if (tid == 0 && ncol > 0) {
-            // the first column began in earlier tiles: add their partials, nearest first
-            const uint32_t start = __ldg(a.colptr + i0);
-            if (start < j0) {
-                TA tacc = TA(0);
-                uint32_t p = t - 1;
-                while (true) {
-                    uint32_t spins = 0;
-                    while (ld_acquire_u32(&a.carry[p].epoch) != epoch) {
-                        if (++spins > kSpinLimit) {
-                            pp_set_error(PP_DEV_TIMEOUT);
-                            break;
+            for (int g = 0; g < TILE_ENTRIES / 32; g += UNROLL) {
+                if ((uint32_t)(g * 32) >= nent) break;
+                uint32_t w[UNROLL];
+                TA xv[UNROLL];
+#pragma unroll
+                for (int m = 0; m < UNROLL; ++m) {
+                    const uint32_t k = (uint32_t)((g + m) * 32 + lane);
+                    w[m] = k < nent ? ld_stream_u32(a.rowc + e0 + k, stream) : 0u;
+                }
+#pragma unroll
+                for (int m = 0; m < UNROLL; ++m) {
+                    const uint32_t k = (uint32_t)((g + m) * 32 + lane);
+                    xv[m] = k < nent ? to_acc(ld_x(x_in + (w[m] & umask), keep)) : TA(0);
+                }
+                if (g == 0) {
+                    if (lane < (int)ncol) cp[lane] = mycp - e0;
+                    if (lane == 0) cp[ncol] = nent;
+                    __syncwarp();
+                }
+#pragma unroll
+                for (int m = 0; m < UNROLL; ++m) {
+                    const uint32_t k = (uint32_t)((g + m) * 32 + lane);
+                    if (k < nent) {
+                        uint32_t col = 0;
+                        if ((w[m] >> a.scale) == a.cmax) {
+                            // the count did not fit inline: find this entry's column
+                            uint32_t lo = 0, hi = ncol;
+                            while (lo < hi) {
+                                const uint32_t mid = (lo + hi) >> 1;
+                                if (cp[mid + 1] <= k)
+                                    lo = mid + 1;
+                                else
+                                    hi = mid;
+                            }
+                            col = c0 + lo;
                         }
-                        backoff(spins);
+                        prod[k] = entry_product<TA>(w[m], xv[m], col, a);
                     }
-                    tacc += (TA)__ldcg(&a.carry[p].val);
-                    if (a.coord[p].y <= start || p == 0) break;
-                    --p;
                 }
-                s_tcin = tacc;
             }
-        }
-        // Second walk: the sums of the columns that end here, carry-in first.
-        {
-            int ci = ci0, ej = ej0;
-            TA run = cin;
-            for (int it = d0; it < d1; ++it) {
-                if (ci < ncol && (int)(s_colend[ci] - j0) <= ej) {
-                    s_y[ci] = run;
-                    run = TA(0);
-                    ++ci;
+            if (nent == 0) {
+                if (lane < (int)ncol) cp[lane] = mycp - e0;
+                if (lane == 0) cp[ncol] = nent;
+            }
+            __syncwarp();
+            // short columns: one lane each, entries in order
+            uint32_t medium = 0;
+            if (lane < (int)ncol) {
+                const uint32_t s = cp[lane], e = cp[lane + 1];
+                if (e - s <= (uint32_t)LANE_SHORT) {
+                    TA y = TA(0);
+                    for (uint32_t k = s; k < e; ++k) y += prod[k];
+                    epi(c0 + lane, y, myinv, acc);
                 } else {
-                    run += s_prod[ej];
-                    ++ej;
+                    medium = 1;
                 }
             }
+            // medium columns: the whole warp, lanes stride, fixed shuffle tree
+            uint32_t mm = __ballot_sync(0xffffffffu, medium);
+            while (mm) {
+                const int j = __ffs(mm) - 1;
+                mm &= mm - 1;
+                const uint32_t s = cp[j], e = cp[j + 1];
+                TA y = TA(0);
+                for (uint32_t k = s + lane; k < e; k += 32) y += prod[k];
+                y = warp_sum(y);
+                const TA invj = __shfl_sync(0xffffffffu, myinv, j);
+                if (lane == 0) epi(c0 + j, y, invj, acc);
+            }
+            __syncwarp();
         }
-        if (tid == 0) s_next = nxt;
-        __syncthreads();
-
-        // Finish the columns that end in this tile.
-        for (int k = tid; k < ncol; k += THREADS) {
-            const uint32_t col = i0 + (uint32_t)k;
-            const TA y = k == 0 ? s_y[0] + s_tcin : s_y[k];
-            const TA r = cc * y + tele;
-            if (LAST) r_out[col] = (TO)r;
-            x_out[col] = from_acc<TS>(r * inv[col]);
-            fx_add(acc, (double)r, E);
-        }
+        item = next;
+        it = nit;
     }
     const Fx128 bt = fx_block_sum<THREADS>(acc, s_fx);
-    if (tid == 0 && (bt.hi | bt.lo)) fx_atomic_add(a.acc + 2 * (iter + 1), bt);
+    if (threadIdx.x == 0 && (bt.hi | bt.lo)) fx_atomic_add(a.acc + 2 * (iter + 1), bt);
 }
 
 // r_l1 = r / norm(r,1) in binary64: sum, then scale.
@@ -457,14 +590,16 @@ __global__ void __launch_bounds__(256) l1_scale_kernel(const TO *r, uint32_t N, 
 
 struct Layout {
     void *x[2];
-    uint2 *coord;
-    Carry *carry;
+    uint32_t *bound, *bound_item;
+    uint4 *item;
+    double *chunk_sum;
+    uint32_t *ticket;
+    uint64_t *plan_status;
     unsigned long long *acc;
     int *fx_exp;
     double *ipart;
     Ctl *ctl;
-    uint32_t *tile_ctr;
-    uint32_t max_tiles;
+    uint32_t *ctr;
     size_t bytes;
 };
 
@@ -472,17 +607,21 @@ inline Layout layout(void *ws, uint64_t M, uint32_t scale, uint32_t iters, pp_dt
     Carver c(ws);
     Layout L;
     const uint64_t N = 1ull << scale;
+    const uint64_t max_items = N + M / CHUNK + 1;
     const size_t xs = dt == PP_FP64 ? 8 : (dt == PP_FP32 ? 4 : 2);
-    L.max_tiles = (uint32_t)ceil_div(N + M, D_MIN) + 1;
     L.x[0] = c.take<char>(N * xs);
     L.x[1] = c.take<char>(N * xs);
-    L.coord = c.take<uint2>((uint64_t)L.max_tiles + 1);
-    L.carry = c.take<Carry>(L.max_tiles);
+    L.bound = c.take<uint32_t>(N);
+    L.bound_item = c.take<uint32_t>(N);
+    L.item = c.take<uint4>(max_items);
+    L.chunk_sum = c.take<double>(max_items);
+    L.ticket = c.take<uint32_t>(max_items);
+    L.plan_status = c.take<uint64_t>(ceil_div(N, PLAN_TILE));
     L.acc = c.take<unsigned long long>(2ull * (iters + 1));
     L.fx_exp = c.take<int>((uint64_t)iters + 1);
     L.ipart = c.take<double>(SETUP_BLOCKS);
     L.ctl = c.take<Ctl>(1);
-    L.tile_ctr = c.take<uint32_t>(iters ? iters : 1);
+    L.ctr = c.take<uint32_t>(1);
     L.bytes = c.size();
     return L;
 }
@@ -494,28 +633,31 @@ inline int occupancy(K kernel) {
     return o > 0 ? o : 1;
 }
 
-template <typename TS, typename TA, typename TO, int ITEMS>
-pp_status run(const pp_graph *g, const double *r0, uint32_t iters, double c, pp_dtype dt, TO *r_out,
-              double *r_l1, const Layout &L, cudaStream_t s) {
+template <typename TS, typename TA, typename TO, int UNROLL>
+pp_status run_unroll(const pp_graph *g, const double *r0, uint32_t iters, double c, pp_dtype dt, TO *r_out,
+                     double *r_l1, const Layout &L, cudaStream_t s) {
     const uint32_t N = 1u << g->scale;
     Args a;
     a.N = N;
     a.scale = g->scale;
     a.cmax = (uint32_t)((1ull << (32 - g->scale)) - 1);
     a.iters = iters;
-    a.D = THREADS * ITEMS;
     a.colptr = g->colptr;
     a.rowc = g->rowc;
     a.ovf_key = g->ovf_key;
     a.ovf_cnt = g->ovf_cnt;
     a.info = g->info;
-    a.coord = L.coord;
-    a.carry = L.carry;
+    a.bound = L.bound;
+    a.bound_item = L.bound_item;
+    a.item = L.item;
+    a.chunk_sum = L.chunk_sum;
+    a.ticket = L.ticket;
+    a.plan_status = L.plan_status;
     a.acc = L.acc;
     a.fx_exp = L.fx_exp;
     a.ipart = L.ipart;
     a.ctl = L.ctl;
-    a.tile_ctr = L.tile_ctr;
+    a.ctr = L.ctr;
     a.c = c;
     const TA *inv = dt == PP_FP64 ? reinterpret_cast<const TA *>(g->inv_dout64)
                                   : reinterpret_cast<const TA *>(g->inv_dout32);
@@ -523,19 +665,21 @@ pp_status run(const pp_graph *g, const double *r0, uint32_t iters, double c, pp_
     TS *x0 = static_cast<TS *>(L.x[0]);
     TS *x1 = static_cast<TS *>(L.x[1]);
     setup_kernel<<<SETUP_BLOCKS, 256, 0, s>>>(a, r0);
+    plan_kernel<<<(unsigned)ceil_div(N, PLAN_TILE), PLAN_THREADS, 0, s>>>(a);
+    plan_items_kernel<<<(unsigned)std::min<uint64_t>(ceil_div(N, 256), 4096), 256, 0, s>>>(a);
     normalize_kernel<TS, TA, TO><<<SETUP_BLOCKS, 256, 0, s>>>(a, r0, inv, x0, r_out);
-    count_launch(2);
+    count_launch(4);
 
-    static const int o_mid = occupancy(iterate_kernel<TS, TA, TO, false, ITEMS>);
-    static const int o_last = occupancy(iterate_kernel<TS, TA, TO, true, ITEMS>);
+    static const int o_mid = occupancy(iterate_kernel<TS, TA, TO, false, UNROLL>);
+    static const int o_last = occupancy(iterate_kernel<TS, TA, TO, true, UNROLL>);
     const int sms = sm_count();
     for (uint32_t it = 0; it < iters; ++it) {
         const TS *xin = (it & 1) ? x1 : x0;
         TS *xout = (it & 1) ? x0 : x1;
         if (it + 1 == iters)
-            iterate_kernel<TS, TA, TO, true, ITEMS><<<sms * o_last, THREADS, 0, s>>>(a, inv, xin, xout, r_out, it);
+            iterate_kernel<TS, TA, TO, true, UNROLL><<<sms * o_last, THREADS, 0, s>>>(a, inv, xin, xout, r_out, it);
         else
-            iterate_kernel<TS, TA, TO, false, ITEMS><<<sms * o_mid, THREADS, 0, s>>>(a, inv, xin, xout, r_out, it);
+            iterate_kernel<TS, TA, TO, false, UNROLL><<<sms * o_mid, THREADS, 0, s>>>(a, inv, xin, xout, r_out, it);
         count_launch();
     }
     if (r_l1) {
@@ -544,6 +688,16 @@ pp_status run(const pp_graph *g, const double *r0, uint32_t iters, double c, pp_
         count_launch(2);
     }
     return launch_status();
+}
+
+template <typename TS, typename TA, typename TO>
+pp_status run(const pp_graph *g, const double *r0, uint32_t iters, double c, pp_dtype dt, TO *r_out,
+              double *r_l1, const Layout &L, cudaStream_t s) {
+    switch (tuning(sizeof(TA) == 8 ? "k3_unroll_f64" : "k3_unroll_f32")) {
+        case 4: return run_unroll<TS, TA, TO, 4>(g, r0, iters, c, dt, r_out, r_l1, L, s);
+        case 16: return run_unroll<TS, TA, TO, 16>(g, r0, iters, c, dt, r_out, r_l1, L, s);
+        default: return run_unroll<TS, TA, TO, 8>(g, r0, iters, c, dt, r_out, r_l1, L, s);
+    }
 }
 
 }  // namespace k3
@@ -571,13 +725,11 @@ extern "C" pp_status pp_pagerank(const pp_graph *g, const double *r0, uint32_t i
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     switch (dt) {
         case PP_FP64:
-            return k3::run<double, double, double, k3::ITEMS_F64>(g, r0, iters, c, dt, static_cast<double *>(r_out),
-                                                                  r_l1, L, s);
+            return k3::run<double, double, double>(g, r0, iters, c, dt, static_cast<double *>(r_out), r_l1, L, s);
         case PP_FP32:
-            return k3::run<float, float, float, k3::ITEMS_F32>(g, r0, iters, c, dt, static_cast<float *>(r_out), r_l1,
-                                                               L, s);
+            return k3::run<float, float, float>(g, r0, iters, c, dt, static_cast<float *>(r_out), r_l1, L, s);
         default:
-            return k3::run<__nv_bfloat16, float, float, k3::ITEMS_F32>(g, r0, iters, c, dt, static_cast<float *>(r_out),
-                                                                       r_l1, L, s);
+            return k3::run<__nv_bfloat16, float, float>(g, r0, iters, c, dt, static_cast<float *>(r_out), r_l1, L,
+                                                        s);
     }
 }

@@ -1,6 +1,7 @@
 // Library-wide entry points: status strings, the device error word, the
 // launch counter, and the host-buffer pipeline (Kernels 1-3 back to back).
 #include <algorithm>
+#include <cstring>
 
 #include "pp_common.cuh"
 
@@ -11,7 +12,50 @@ uint32_t k2_fetch_error(cudaStream_t s);
 uint32_t k3_fetch_error(cudaStream_t s);
 }  // namespace pp
 
+namespace pp {
+namespace {
+struct Knob {
+    const char *key;
+    std::atomic<int64_t> value;
+    int64_t allowed[4];
+};
+Knob g_knobs[] = {
+    {"k3_unroll_f32", {8}, {4, 8, 16, 0}},
+    {"k3_unroll_f64", {8}, {4, 8, 16, 0}},
+};
+Knob *find_knob(const char *key) {
+    if (!key) return nullptr;
+    for (Knob &k : g_knobs)
+        if (std::strcmp(k.key, key) == 0) return &k;
+    return nullptr;
+}
+}  // namespace
+
+int64_t tuning(const char *key) {
+    Knob *k = find_knob(key);
+    return k ? k->value.load() : 0;
+}
+}  // namespace pp
+
 using namespace pp;
+
+extern "C" pp_status pp_set_tuning(const char *key, int64_t value) {
+    Knob *k = find_knob(key);
+    if (!k) return PP_ERR_INVALID_ARG;
+    for (int64_t a : k->allowed)
+        if (a && a == value) {
+            k->value.store(value);
+            return PP_OK;
+        }
+    return PP_ERR_INVALID_ARG;
+}
+
+extern "C" pp_status pp_get_tuning(const char *key, int64_t *value) {
+    Knob *k = find_knob(key);
+    if (!k || !value) return PP_ERR_INVALID_ARG;
+    *value = k->value.load();
+    return PP_OK;
+}
 
 extern "C" uint64_t pp_launch_count(void) { return g_launches.load(); }
 

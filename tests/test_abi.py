@@ -81,3 +81,19 @@ def test_binding_fails_loudly_without_library(monkeypatch):
     monkeypatch.setattr(pp, "_L", None)
     with pytest.raises(ImportError):
         pp.lib()
+
+
+def test_tuning_knobs():
+    import paper_1603_01876_gb300 as pp
+
+    old = pp.get_tuning("k3_unroll_f32")
+    try:
+        for v in (4, 8, 16):
+            pp.set_tuning("k3_unroll_f32", v)
+            assert pp.get_tuning("k3_unroll_f32") == v
+        with pytest.raises(pp.PPError):
+            pp.set_tuning("k3_unroll_f32", 7)
+        with pytest.raises(pp.PPError):
+            pp.set_tuning("no_such_knob", 1)
+    finally:
+        pp.set_tuning("k3_unroll_f32", old)
