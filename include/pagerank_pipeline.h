@@ -127,6 +127,26 @@ pp_status pp_sort_edges(const uint32_t *u, const uint32_t *v, uint64_t M, uint32
                         void *stream);
 
 /*
+ * Kernel 1 for callers that cannot allocate device memory (the paper has no
+ * counterpart; this is a deployment variant of pp_sort_edges).  Callers whose
+ * GPU memory is owned by another allocator, or who must not trigger
+ * cudaMalloc's implicit device synchronisation, pass only inputs and
+ * outputs; the scratch space is a fixed array in device memory
+ * (about 17 MiB, held by every GPU that loads the library until the process
+ * exits).  M must not exceed PP_SORT_STATIC_MAX_EDGES, otherwise
+ * PP_ERR_INVALID_ARG is returned and nothing is enqueued.  The call
+ * allocates nothing (no cudaMalloc or cudaFree).  Its first call on a device
+ * looks up the array's device address with that device current; make that
+ * first call outside any stream capture.  Calls share the array, which keeps
+ * the last call's contents: each call clears what it needs zeroed, and calls
+ * that overlap on the GPU (other streams, other host threads) race on it.
+ * Results are identical to pp_sort_edges.
+ */
+#define PP_SORT_STATIC_MAX_EDGES (1u << 20)
+pp_status pp_sort_edges_static(const uint32_t *u, const uint32_t *v, uint64_t M, uint32_t scale,
+                               uint32_t *u_out, uint32_t *v_out, void *stream);
+
+/*
  * Kernel 2 (Sec. IV-C), from Kernel 1's output (u_sorted, v_sorted; M edges
  * sorted by (u, v)):
  *   step 1  A = sparse(u,v,1,N,N)           duplicate edges become counts

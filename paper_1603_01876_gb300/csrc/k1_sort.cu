@@ -133,3 +133,58 @@ extern "C" pp_status pp_sort_edges(const uint32_t *u, const uint32_t *v, uint64_
         k1::run<uint64_t>(u, v, M, scale, u_out, v_out, L, s);
     return launch_status();
 }
+
+// ---------------------------------------------------------------------------
+// Kernel 1 without allocation (pp_sort_edges_static).  Some callers cannot
+// allocate device memory at all: their GPU memory belongs to another
+// allocator (a framework's caching pool, a fixed real-time budget) or
+// cudaMalloc's implicit device synchronisation would stall their other
+// streams.  For them this entry point keeps its scratch space in a
+// fixed-size array in device memory, which every GPU that loads the library
+// holds until the process exits.  Its device address is looked up once per
+// device (cudaGetSymbolAddress) on the first call made with that device
+// current; do that first call outside any stream capture.  All calls share
+// the array and it keeps the last call's contents: the sort clears its
+// counters and look-back words itself, and calls whose work overlaps on the
+// GPU (concurrent streams, several host threads) race on it.
+
+#include <mutex>
+
+namespace {
+constexpr uint64_t kStaticMaxEdges = PP_SORT_STATIC_MAX_EDGES;
+// Largest layout the sort needs for kStaticMaxEdges edges: two 64-bit key
+// buffers, the digit histograms and two sets of 32-bit look-back words.
+constexpr size_t kStaticBytes = (size_t)17 << 20;
+static __device__ __align__(256) unsigned char k1_static_scratch[kStaticBytes];
+
+std::mutex g_static_mutex;
+void *g_static_addr[64] = {};
+}  // namespace
+
+extern "C" pp_status pp_sort_edges_static(const uint32_t *u, const uint32_t *v, uint64_t M, uint32_t scale,
+                                          uint32_t *u_out, uint32_t *v_out, void *stream) {
+    if (!k1_args_ok(M, scale) || M > kStaticMaxEdges) return PP_ERR_INVALID_ARG;
+    if (M == 0) return PP_OK;
+    if (!u || !v || !u_out || !v_out) return PP_ERR_INVALID_ARG;
+    const k1::Layout need = k1::layout(nullptr, M, scale);
+    if (need.bytes > kStaticBytes) return PP_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return PP_ERR_CUDA;
+    void *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_static_mutex);
+        if (!g_static_addr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, k1_static_scratch) != cudaSuccess || !p) return PP_ERR_CUDA;
+            g_static_addr[dev] = p;
+        }
+        base = g_static_addr[dev];
+    }
+    const k1::Layout L = k1::layout(base, M, scale);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (2 * scale <= 32)
+        k1::run<uint32_t>(u, v, M, scale, u_out, v_out, L, s);
+    else
+        k1::run<uint64_t>(u, v, M, scale, u_out, v_out, L, s);
+    return launch_status();
+}
