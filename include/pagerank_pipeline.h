@@ -210,8 +210,10 @@ uint64_t pp_launch_count(void);
  * Tuning knobs (process-wide, read when a call is made; they change speed,
  * never results):
  *   "k3_unroll_f32"  gathers each Kernel 3 thread issues before using any,
- *                    binary32 and bfloat16 ranks: 4, 8 or 16 (default 8)
- *   "k3_unroll_f64"  the same for binary64 ranks: 4, 8 or 16 (default 8)
+ *                    binary32 and bfloat16 ranks: 4 or 8 (default 8)
+ *   "k3_unroll_f64"  the same for binary64 ranks: 4 or 8 (default 8)
+ *   "k3_minblocks"   Kernel 3 blocks per SM the registers are budgeted for:
+ *                    4, 5 or 6 (default 4)
  * pp_set_tuning returns PP_ERR_INVALID_ARG for an unknown key or value.
  * The autotuner (paper_1603_01876_gb300/tune.py) measures the choices and
  * stores the fastest per device and scale.

@@ -408,8 +408,8 @@ __device__ __forceinline__ TA warp_sum(TA y) {
     return y;  // in lane 0
 }
 
-template <typename TS, typename TA, typename TO, bool LAST, int UNROLL>
-__global__ void __launch_bounds__(THREADS) iterate_kernel(Args a, const TA *inv, const TS *__restrict__ x_in,
+template <typename TS, typename TA, typename TO, bool LAST, int UNROLL, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) iterate_kernel(Args a, const TA *inv, const TS *__restrict__ x_in,
                                                           TS *__restrict__ x_out, TO *r_out, uint32_t iter) {
     static_assert(TILE_ENTRIES % (32 * UNROLL) == 0 && CHUNK % (32 * UNROLL) == 0, "unroll must divide the work");
     __shared__ TA s_prod[WARPS][TILE_ENTRIES];
@@ -633,7 +633,7 @@ inline int occupancy(K kernel) {
     return o > 0 ? o : 1;
 }
 
-template <typename TS, typename TA, typename TO, int UNROLL>
+template <typename TS, typename TA, typename TO, int UNROLL, int MINB>
 pp_status run_unroll(const pp_graph *g, const double *r0, uint32_t iters, double c, pp_dtype dt, TO *r_out,
                      double *r_l1, const Layout &L, cudaStream_t s) {
     const uint32_t N = 1u << g->scale;
@@ -670,16 +670,18 @@ pp_status run_unroll(const pp_graph *g, const double *r0, uint32_t iters, double
     normalize_kernel<TS, TA, TO><<<SETUP_BLOCKS, 256, 0, s>>>(a, r0, inv, x0, r_out);
     count_launch(4);
 
-    static const int o_mid = occupancy(iterate_kernel<TS, TA, TO, false, UNROLL>);
-    static const int o_last = occupancy(iterate_kernel<TS, TA, TO, true, UNROLL>);
+    static const int o_mid = occupancy(iterate_kernel<TS, TA, TO, false, UNROLL, MINB>);
+    static const int o_last = occupancy(iterate_kernel<TS, TA, TO, true, UNROLL, MINB>);
     const int sms = sm_count();
     for (uint32_t it = 0; it < iters; ++it) {
         const TS *xin = (it & 1) ? x1 : x0;
         TS *xout = (it & 1) ? x0 : x1;
         if (it + 1 == iters)
-            iterate_kernel<TS, TA, TO, true, UNROLL><<<sms * o_last, THREADS, 0, s>>>(a, inv, xin, xout, r_out, it);
+            iterate_kernel<TS, TA, TO, true, UNROLL, MINB><<<sms * o_last, THREADS, 0, s>>>(a, inv, xin, xout, r_out,
+                                                                                         it);
         else
-            iterate_kernel<TS, TA, TO, false, UNROLL><<<sms * o_mid, THREADS, 0, s>>>(a, inv, xin, xout, r_out, it);
+            iterate_kernel<TS, TA, TO, false, UNROLL, MINB><<<sms * o_mid, THREADS, 0, s>>>(a, inv, xin, xout, r_out,
+                                                                                          it);
         count_launch();
     }
     if (r_l1) {
@@ -693,10 +695,17 @@ pp_status run_unroll(const pp_graph *g, const double *r0, uint32_t iters, double
 template <typename TS, typename TA, typename TO>
 pp_status run(const pp_graph *g, const double *r0, uint32_t iters, double c, pp_dtype dt, TO *r_out,
               double *r_l1, const Layout &L, cudaStream_t s) {
-    switch (tuning(sizeof(TA) == 8 ? "k3_unroll_f64" : "k3_unroll_f32")) {
-        case 4: return run_unroll<TS, TA, TO, 4>(g, r0, iters, c, dt, r_out, r_l1, L, s);
-        case 16: return run_unroll<TS, TA, TO, 16>(g, r0, iters, c, dt, r_out, r_l1, L, s);
-        default: return run_unroll<TS, TA, TO, 8>(g, r0, iters, c, dt, r_out, r_l1, L, s);
+    const bool u4 = tuning(sizeof(TA) == 8 ? "k3_unroll_f64" : "k3_unroll_f32") == 4;
+    switch (tuning("k3_minblocks")) {
+        case 5:
+            return u4 ? run_unroll<TS, TA, TO, 4, 5>(g, r0, iters, c, dt, r_out, r_l1, L, s)
+                      : run_unroll<TS, TA, TO, 8, 5>(g, r0, iters, c, dt, r_out, r_l1, L, s);
+        case 6:
+            return u4 ? run_unroll<TS, TA, TO, 4, 6>(g, r0, iters, c, dt, r_out, r_l1, L, s)
+                      : run_unroll<TS, TA, TO, 8, 6>(g, r0, iters, c, dt, r_out, r_l1, L, s);
+        default:
+            return u4 ? run_unroll<TS, TA, TO, 4, 4>(g, r0, iters, c, dt, r_out, r_l1, L, s)
+                      : run_unroll<TS, TA, TO, 8, 4>(g, r0, iters, c, dt, r_out, r_l1, L, s);
     }
 }
 

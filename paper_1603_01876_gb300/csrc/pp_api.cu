@@ -20,8 +20,9 @@ struct Knob {
     int64_t allowed[4];
 };
 Knob g_knobs[] = {
-    {"k3_unroll_f32", {8}, {4, 8, 16, 0}},
-    {"k3_unroll_f64", {8}, {4, 8, 16, 0}},
+    {"k3_unroll_f32", {8}, {4, 8, 0, 0}},
+    {"k3_unroll_f64", {8}, {4, 8, 0, 0}},
+    {"k3_minblocks", {4}, {4, 5, 6, 0}},
 };
 Knob *find_knob(const char *key) {
     if (!key) return nullptr;
