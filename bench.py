@@ -274,7 +274,7 @@ def run_ours(args):
     dom = max(stages, key=lambda s: stages[s][0])
     dom_ms, dom_bytes = stages[dom]
     if dom == "k3_pagerank":
-        kname, launches_per_stage = "k3 iterate_kernel (merge-path pull SpMV)", iters
+        kname, launches_per_stage = "k3 iterate_kernel (warp-tiled, degree-bucketed pull SpMV)", iters
     elif dom == "k1_sort":
         kname, launches_per_stage = "k1 onesweep pass_kernel (8-bit LSD pass)", P
     else:
@@ -319,6 +319,10 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clocks.summary(),
     }
+    if not args.no_batched:
+        del pws
+        torch.cuda.empty_cache()
+        out["batched"] = run_batched(dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(scale, seed, max_seconds=args.cpu_seconds)
     if rank == 0:
@@ -364,6 +368,63 @@ def run_k3_only(args):
     print(json.dumps({"stage": "k3", "scale": scale, "dtype": args.dtype, "tune": args.tune, "ms": ms, "nnz": info["nnz"],
                       "edges_per_s": iters * M / (ms * 1e-3), "gbs": b / ms / 1e6,
                       "device_error": pp.last_device_error()}))
+
+
+def run_batched(dev, steps=3, warmup=1, nrhs=32, n_graphs=64, lo=12, hi=18):
+    """Batched Kernel 3: 64 Kronecker graphs of scales drawn from 12..18, 32
+    start vectors each, one SpMM kernel per iteration (binary32), against the
+    2048 single-vector binary64 runs of the plain path on the same GPU."""
+    import numpy as np
+    import torch
+
+    import kernel0
+    import paper_1603_01876_gb300 as pp
+
+    scales = kernel0.batch_scales(n_graphs, lo, hi, seed=SEED)
+    graphs = []
+    for g, s in enumerate(scales):
+        u, v = kernel0.edges_device(s, SEED, graph=g, device=dev)
+        us, vs = pp.sort_edges(u, v, s)
+        graphs.append(pp.build_filter_normalize(us, vs, s))
+    r0 = np.concatenate([np.stack([kernel0.r0_host(1 << s, SEED, graph=g, rhs=j) for j in range(nrhs)], axis=1)
+                         for g, s in enumerate(scales)])
+    r0d = torch.from_numpy(r0).to(dev)
+    out = pp.pagerank_batched(graphs, r0d, nrhs, ITERS, DAMPING)
+    for _ in range(warmup):
+        pp.pagerank_batched(graphs, r0d, nrhs, ITERS, DAMPING, out=out)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e[0].record()
+    for _ in range(steps):
+        pp.pagerank_batched(graphs, r0d, nrhs, ITERS, DAMPING, out=out)
+    e[1].record()
+    torch.cuda.synchronize()
+    ms_b = e[0].elapsed_time(e[1]) / steps
+    # the same 2048 runs one after another, binary64, single-vector path
+    row = np.cumsum([0] + [1 << s for s in scales])
+    cols = [[r0d[row[g]:row[g + 1], j].contiguous() for j in range(nrhs)] for g in range(n_graphs)]
+    ref = torch.empty(int(row[-1]), nrhs, dtype=torch.float64, device=dev)
+    ws = torch.empty(max(pp.workspace_bytes("pagerank", gr.M, gr.scale, ITERS, "fp64") for gr in graphs),
+                     dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+    e[0].record()
+    for g in range(n_graphs):
+        for j in range(nrhs):
+            ref[row[g]:row[g + 1], j] = pp.pagerank(graphs[g], cols[g][j], ITERS, DAMPING, "fp64", workspace=ws)
+    e[1].record()
+    torch.cuda.synchronize()
+    ms_s = e[0].elapsed_time(e[1])
+    d = (out.double() - ref).abs()
+    l1 = max(float((d[row[g]:row[g + 1], j].sum() / ref[row[g]:row[g + 1], j].abs().sum()))
+             for g in range(n_graphs) for j in range(nrhs))
+    nz = ref != 0
+    edges = int(sum(gr.M for gr in graphs))
+    return {"graphs": n_graphs, "scales": "%d..%d" % (lo, hi), "start_vectors": nrhs, "edges": edges,
+            "ms": ms_b, "edges_per_s": ITERS * edges * nrhs / (ms_b * 1e-3),
+            "sequential_fp64_ms": ms_s, "sequential_fp64_edges_per_s": ITERS * edges * nrhs / (ms_s * 1e-3),
+            "speedup_vs_sequential_fp64": ms_s / ms_b, "max_l1_err_vs_fp64": l1,
+            "max_rel_err_vs_fp64": float((d[nz] / ref[nz].abs()).max()),
+            "device_error": pp.last_device_error()}
 
 
 def cpu_baseline(scale, seed, max_seconds=20.0, sample_div=16):
@@ -443,9 +504,10 @@ def main():
     ap.add_argument("--dtype", choices=["fp32", "fp64", "bf16"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched Kernel 3 section")
     ap.add_argument("--tune", action="append", default=[], metavar="KEY=VALUE",
                     help="set a library tuning knob before running (repeatable)")
-    ap.add_argument("--stage", choices=["all", "k3"], default="all",
+    ap.add_argument("--stage", choices=["all", "k3", "batched"], default="all",
                     help="k3: time Kernel 3 alone (profiling aid); the default times the whole pipeline")
     args = ap.parse_args()
     if args.tune:
@@ -456,6 +518,10 @@ def main():
             pp.set_tuning(k, int(v))
     if args.stage == "k3":
         run_k3_only(args)
+    elif args.stage == "batched":
+        import torch
+
+        print(json.dumps({"stage": "batched", **run_batched(torch.device("cuda", 0), args.steps, args.warmup)}))
     elif args.impl == "reference":
         run_reference(args)
     else:

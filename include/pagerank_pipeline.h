@@ -179,6 +179,27 @@ pp_status pp_pagerank(const pp_graph *g, const double *r0, uint32_t iters, doubl
                       void *stream);
 
 /*
+ * Kernel 3 for a batch of graphs with several start vectors each (a sparse
+ * matrix times dense matrix product; every (graph, vector) pair is one run of
+ * the iteration above, in binary32 with sum(r) reduced exactly).
+ *   gs[n_graphs]   host array of Kernel 2 outputs (device arrays inside);
+ *                  1 <= n_graphs <= PP_BATCH_MAX_GRAPHS, scales 1..24.
+ *   nrhs           start vectors per graph, 1 <= nrhs <= PP_BATCH_MAX_RHS.
+ *   r0             device binary64, the start vectors of all graphs as one
+ *                  row-major (sum of N_g) x nrhs matrix: graph g's rows come
+ *                  after graph g-1's, row i holds the nrhs values of vertex i.
+ *   r_out          device binary32, the final ranks in the same layout.
+ * Deterministic; one persistent kernel per iteration covers every graph.
+ */
+#define PP_BATCH_MAX_GRAPHS 128
+#define PP_BATCH_MAX_RHS 32
+pp_status pp_pagerank_batched_workspace(const pp_graph *gs, uint32_t n_graphs, uint32_t nrhs, uint32_t iters,
+                                        size_t *bytes);
+pp_status pp_pagerank_batched(const pp_graph *gs, uint32_t n_graphs, const double *r0, uint32_t nrhs,
+                              uint32_t iters, double c, float *r_out, void *workspace, size_t workspace_bytes,
+                              void *stream);
+
+/*
  * Kernels 1-3 back to back from HOST buffers: copies u_host, v_host (M ids
  * each) and r0_host (N values) to the device, runs the three kernels, each
  * complete before the next starts, and copies the final r into r_out_host

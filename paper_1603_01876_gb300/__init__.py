@@ -66,6 +66,8 @@ def _lib():
             "pp_pipeline_workspace": [u64, u32, u32, i32, sz],
             "pp_pipeline_host": [vp, vp, u64, u32, vp, u32, dbl, i32, i32, vp, vp, vp, ctypes.c_size_t, vp],
             "pp_last_device_error": [vp, ctypes.POINTER(ctypes.c_uint32)],
+            "pp_pagerank_batched_workspace": [ctypes.POINTER(CGraph), u32, u32, u32, sz],
+            "pp_pagerank_batched": [ctypes.POINTER(CGraph), u32, vp, u32, u32, dbl, vp, vp, ctypes.c_size_t, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -218,6 +220,31 @@ def pagerank(graph, r0, iters=20, c=0.85, dtype="fp32", out=None, want_l1=False,
                             ws.numel(), _stream(stream, dev))
     _check("pp_pagerank", st)
     return (out, l1) if want_l1 else out
+
+
+BATCH_MAX_GRAPHS, BATCH_MAX_RHS = 128, 32
+
+
+def pagerank_batched(graphs, r0, nrhs, iters=20, c=0.85, out=None, workspace=None, stream=None):
+    """Kernel 3 for several graphs and nrhs start vectors each (binary32 ranks).
+
+    r0: device float64 tensor of shape (sum of N_g, nrhs), the graphs' rows
+    one after another; returns a float32 tensor of the same shape."""
+    n = len(graphs)
+    arr = (CGraph * n)(*[g.c for g in graphs])
+    rows = sum(g.N for g in graphs)
+    assert r0.shape == (rows, nrhs) and r0.dtype == torch.float64 and r0.is_contiguous()
+    dev = r0.device
+    if out is None:
+        out = torch.empty(rows, nrhs, dtype=torch.float32, device=dev)
+    need = ctypes.c_size_t(0)
+    _check("pp_pagerank_batched_workspace", _lib().pp_pagerank_batched_workspace(arr, n, nrhs, iters,
+                                                                               ctypes.byref(need)))
+    ws = workspace if workspace is not None and workspace.numel() >= need.value else _workspace(need.value, dev)
+    st = _lib().pp_pagerank_batched(arr, n, _ptr(r0), nrhs, iters, c, _ptr(out), _ptr(ws), ws.numel(),
+                                    _stream(stream, dev))
+    _check("pp_pagerank_batched", st)
+    return out
 
 
 def pipeline_host(u, v, scale, r0, iters=20, c=0.85, dtype="fp32", rule="lowest", out=None, info=None,
