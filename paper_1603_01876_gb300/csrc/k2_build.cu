@@ -1,18 +1,28 @@
 // Kernel 2 (Sec. IV-C): build, filter and normalise the adjacency matrix.
 //
 //   unique_kernel    step 1: run-lengths of equal (u, v) in Kernel 1's sorted
-//                    output are the counts A(u,v); one thread block per tile,
-//                    output offsets by decoupled look-back; each entry adds
-//                    (1, count) to a packed per-column (entries, d_in) word.
-//   dmax_kernel      step 2 done: d_in out; max(d_in) and its lowest column.
-//   mask_scan_kernel step 3: the supernode and leaf columns; the CSC column
-//                    pointer of what survives by a look-back scan over N.
-//   prepass_kernel   step 4: d_out = row sums of the kept counts (entries are
-//                    in row order, so a warp aggregates a row before its
-//                    atomic); digit histograms for the transpose.
-//   onesweep passes  stable sort of the kept entries by column: rows stay
-//                    ascending inside every column (the CSC layout).
+//                    output are the counts A(u,v); output offsets by a
+//                    decoupled look-back over tiles.  Each entry is written
+//                    as one 64-bit word (column << 32 | row | count << scale);
+//                    each row's counts (entries arrive in row order) go to
+//                    the row's out-degree before filtering, and the column
+//                    digits to the transpose's histograms.
+//   transpose        stable LSD radix sort of the entry words by column (rows
+//                    stay ascending inside a column).
+//   colscan_kernel   step 2: with the entries grouped by column, the entry
+//                    count and d_in = sum(A,1) of each column, one atomic per
+//                    run of a column inside a thread's stretch.
+//   dmax_kernel      d_in out; max(d_in) and its lowest column.
+//   mask_scan_kernel step 3: the supernode and leaf columns; two look-back
+//                    scans over the columns give the kept-entry column
+//                    pointer and the removed entries before each column.
+//   compact_kernel   step 4: kept entries move to their compacted place;
+//                    a removed entry's count comes off its row's out-degree
+//                    (d_out = sum(A,2) after the filter).
 //   finalize_kernel  1/d_out in binary32 and binary64.
+// Every pass after the unique pass streams the entries in column order, so
+// the per-column lookups are nearly sequential and no atomic is issued per
+// entry.
 #include <algorithm>
 
 #include "onesweep.cuh"
@@ -29,34 +39,12 @@ constexpr int SC_THREADS = 256;
 constexpr int SC_ITEMS = 16;
 constexpr int SC_TILE = SC_THREADS * SC_ITEMS;
 
-constexpr uint64_t F_AGG = 1ull << 62, F_INC = 2ull << 62, F_ANY = 3ull << 62, F_VAL = F_AGG - 1;
+constexpr uint64_t F_AGG = 1ull << 62, F_INC = 2ull << 62;
 
 __device__ __forceinline__ uint64_t uq_tiles(uint64_t M) { return (M + UQ_TILE - 1) / UQ_TILE; }
 
 __device__ __forceinline__ uint64_t edge_key(const uint32_t *us, const uint32_t *vs, uint64_t i) {
     return ((uint64_t)__ldg(us + i) << 32) | (uint64_t)__ldg(vs + i);
-}
-
-// Exclusive prefix of the tiles before `tile` in a chained scan whose status
-// words carry flags in bits 63:62 and a sum in bits 61:0.
-__device__ __forceinline__ uint64_t lookback(uint64_t *status, uint64_t tile) {
-    uint64_t excl = 0;
-    uint64_t p = tile - 1;
-    uint32_t spins = 0;
-    while (true) {
-        const uint64_t s = ld_relaxed_u64(status + p);
-        if ((s & F_ANY) == 0) {
-            if (++spins > kSpinLimit) {
-                pp_set_error(PP_DEV_TIMEOUT);
-                return excl;
-            }
-            backoff(spins);
-            continue;
-        }
-        excl += s & F_VAL;
-        if (s & F_INC) return excl;
-        --p;
-    }
 }
 
 // Exclusive block max-scan of one int64 per thread (identity -1).
@@ -91,143 +79,229 @@ __device__ __forceinline__ uint32_t ovf_lookup(const uint64_t *keys, const uint3
     return (lo < n && keys[lo] == key) ? cnts[lo] : 0u;
 }
 
+// Run by one whole warp: publishes a tile's aggregate, looks back over the
+// earlier tiles and publishes the inclusive prefix; lane 0 stores the tile's
+// exclusive prefix in *s_excl.
+__device__ __forceinline__ void warp_tile_prefix(uint64_t *status, uint64_t tile, uint64_t total,
+                                                 uint64_t *s_excl) {
+    const int lane = threadIdx.x & 31;
+    if (tile == 0) {
+        if (lane == 0) {
+            st_relaxed_u64(status, F_INC | total);
+            *s_excl = 0;
+        }
+        return;
+    }
+    if (lane == 0) st_relaxed_u64(status + tile, F_AGG | total);
+    const uint64_t ex = warp_lookback(status, tile);
+    if (lane == 0) {
+        st_relaxed_u64(status + tile, F_INC | (ex + total));
+        *s_excl = ex;
+    }
+}
+
 struct UniqueArgs {
     const uint32_t *us, *vs;
     uint64_t M;
     uint32_t scale, cmax;
-    uint32_t *out_v, *out_rowc;
+    unsigned long long *ent;  // [nnz0] column << 32 | row | count field << scale
     uint64_t *ovf_key;
     uint32_t *ovf_cnt;
-    unsigned long long *deg;  // [N]: entries << 32 | d_in
+    uint32_t *d_out;          // [N]: row sums before the filter
+    uint32_t *hist;           // [npasses * 256] column digits, for the transpose
+    int npasses;
     uint64_t *status;
     uint32_t *tile_ctr;
     uint64_t *info;
 };
 
+// Persistent: each block claims tiles in order until none is left.
 __global__ void __launch_bounds__(UQ_THREADS) unique_kernel(UniqueArgs a) {
     __shared__ uint32_t s_tile;
     __shared__ uint64_t s_scan[40];
     __shared__ long long s_max[UQ_THREADS / 32];
     __shared__ uint64_t s_excl;
+    __shared__ uint32_t s_hist[os::MAX_PASSES][os::RADIX];
     const int tid = threadIdx.x;
-    if (tid == 0) s_tile = atomicAdd(a.tile_ctr, 1u);
-    __syncthreads();
-    const uint64_t tile = s_tile;
-    if (tile >= uq_tiles(a.M)) return;
-    const uint64_t base = tile * UQ_TILE;
-    const uint64_t my0 = base + (uint64_t)tid * UQ_ITEMS;
+    for (int i = tid; i < os::MAX_PASSES * os::RADIX; i += UQ_THREADS) (&s_hist[0][0])[i] = 0;
+    const uint64_t ntiles = uq_tiles(a.M);
+    const uint32_t umask = (a.scale >= 32) ? 0xffffffffu : ((1u << a.scale) - 1u);
+    while (true) {
+        if (tid == 0) s_tile = atomicAdd(a.tile_ctr, 1u);
+        __syncthreads();
+        const uint64_t tile = s_tile;
+        if (tile >= ntiles) break;
+        const uint64_t base = tile * UQ_TILE;
+        const uint64_t my0 = base + (uint64_t)tid * UQ_ITEMS;
 
-    uint64_t k[UQ_ITEMS];
+        uint64_t k[UQ_ITEMS];
 #pragma unroll
-    for (int j = 0; j < UQ_ITEMS; ++j) k[j] = (my0 + j < a.M) ? edge_key(a.us, a.vs, my0 + j) : ~0ull;
-    const uint64_t knext = (my0 + UQ_ITEMS < a.M) ? edge_key(a.us, a.vs, my0 + UQ_ITEMS) : ~0ull;
+        for (int j = 0; j < UQ_ITEMS; ++j) k[j] = (my0 + j < a.M) ? edge_key(a.us, a.vs, my0 + j) : ~0ull;
+        const uint64_t knext = (my0 + UQ_ITEMS < a.M) ? edge_key(a.us, a.vs, my0 + UQ_ITEMS) : ~0ull;
 
-    // A run ends ("tail") where the next key differs.
-    uint32_t tails = 0;
-    int last_tail = -1;
+        // A run ends ("tail") where the next key differs.
+        uint32_t tails = 0;
+        int last_tail = -1;
 #pragma unroll
-    for (int j = 0; j < UQ_ITEMS; ++j) {
-        const uint64_t nx = j + 1 < UQ_ITEMS ? k[j + 1] : knext;
-        if (my0 + j < a.M && k[j] != nx) {
-            tails |= 1u << j;
-            last_tail = j;
+        for (int j = 0; j < UQ_ITEMS; ++j) {
+            const uint64_t nx = j + 1 < UQ_ITEMS ? k[j + 1] : knext;
+            if (my0 + j < a.M && k[j] != nx) {
+                tails |= 1u << j;
+                last_tail = j;
+            }
         }
-    }
-    const long long prev_tail = block_exclusive_max(last_tail >= 0 ? (long long)(my0 + last_tail) : -1ll, s_max);
+        const long long prev_tail =
+            block_exclusive_max(last_tail >= 0 ? (long long)(my0 + last_tail) : -1ll, s_max);
 
-    // Start of the run of this thread's first tail.
-    uint64_t start = (uint64_t)(prev_tail + 1);
-    if (prev_tail < 0) {
-        start = base;
-        const int first = tails ? __ffs(tails) - 1 : -1;
-        uint64_t K = 0;
+        // Start of the run of this thread's first tail.
+        uint64_t start = (uint64_t)(prev_tail + 1);
+        if (prev_tail < 0) {
+            start = base;
+            const int first = tails ? __ffs(tails) - 1 : -1;
+            uint64_t K = 0;
 #pragma unroll
-        for (int j = 0; j < UQ_ITEMS; ++j)
-            if (j == first) K = k[j];
-        if (first >= 0 && base > 0 && edge_key(a.us, a.vs, base - 1) == K) {
-            // The run began in an earlier tile: gallop back, then bisect.
-            uint64_t hi = base - 1, step = 1;
-            long long lo = -1;
-            while (true) {
-                if (hi < step) break;
-                const uint64_t p = hi - step;
-                if (edge_key(a.us, a.vs, p) != K) {
-                    lo = (long long)p;
-                    break;
+            for (int j = 0; j < UQ_ITEMS; ++j)
+                if (j == first) K = k[j];
+            if (first >= 0 && base > 0 && edge_key(a.us, a.vs, base - 1) == K) {
+                // The run began in an earlier tile: gallop back, then bisect.
+                uint64_t hi = base - 1, step = 1;
+                long long lo = -1;
+                while (true) {
+                    if (hi < step) break;
+                    const uint64_t p = hi - step;
+                    if (edge_key(a.us, a.vs, p) != K) {
+                        lo = (long long)p;
+                        break;
+                    }
+                    hi = p;
+                    step <<= 1;
                 }
-                hi = p;
-                step <<= 1;
+                while ((long long)hi - lo > 1) {
+                    const uint64_t mid = (uint64_t)((lo + (long long)hi) >> 1);
+                    if (edge_key(a.us, a.vs, mid) == K)
+                        hi = mid;
+                    else
+                        lo = (long long)mid;
+                }
+                start = hi;
             }
-            while ((long long)hi - lo > 1) {
-                const uint64_t mid = (uint64_t)((lo + (long long)hi) >> 1);
-                if (edge_key(a.us, a.vs, mid) == K)
-                    hi = mid;
-                else
-                    lo = (long long)mid;
-            }
-            start = hi;
         }
-    }
 
-    uint32_t cnt[UQ_ITEMS];
-    uint32_t nt = 0, ne = 0;
+        uint32_t cnt[UQ_ITEMS];
+        uint32_t nt = 0, ne = 0;
 #pragma unroll
-    for (int j = 0; j < UQ_ITEMS; ++j) {
-        cnt[j] = 0;
-        if (tails >> j & 1u) {
-            cnt[j] = (uint32_t)(my0 + j - start + 1);
-            start = my0 + j + 1;
-            ++nt;
-            ne += cnt[j] >= a.cmax;
+        for (int j = 0; j < UQ_ITEMS; ++j) {
+            cnt[j] = 0;
+            if (tails >> j & 1u) {
+                cnt[j] = (uint32_t)(my0 + j - start + 1);
+                start = my0 + j + 1;
+                ++nt;
+                ne += cnt[j] >= a.cmax;
+            }
         }
-    }
 
-    uint64_t total;
-    const uint64_t mine = ((uint64_t)ne << 32) | nt;
-    const uint64_t texcl = block_exclusive_sum<uint64_t, UQ_THREADS>(mine, s_scan, &total);
-    if (tid == 0) {
-        uint64_t *st = a.status + tile;
-        if (tile == 0) {
-            st_relaxed_u64(st, F_INC | total);
-            s_excl = 0;
-        } else {
-            st_relaxed_u64(st, F_AGG | total);
-            const uint64_t ex = lookback(a.status, tile);
-            st_relaxed_u64(st, F_INC | (ex + total));
-            s_excl = ex;
-        }
-        if (tile == uq_tiles(a.M) - 1) {
+        // bits 61:32 count overflow entries, bits 31:0 entries
+        uint64_t total;
+        const uint64_t mine = ((uint64_t)ne << 32) | nt;
+        const uint64_t texcl = block_exclusive_sum<uint64_t, UQ_THREADS>(mine, s_scan, &total);
+        if (tid < 32) warp_tile_prefix(a.status, tile, total, &s_excl);
+        __syncthreads();
+        if (tid == 0 && tile == ntiles - 1) {
             const uint64_t inc = s_excl + total;
             a.info[PP_INFO_NNZ0] = inc & 0xffffffffull;
             a.info[PP_INFO_NOVF] = (inc >> 32) & 0x3fffffffull;
         }
+        const uint64_t gex = s_excl + texcl;
+        uint64_t pos = gex & 0xffffffffull;
+        uint64_t epos = (gex >> 32) & 0x3fffffffull;
+        uint32_t row = 0xffffffffu, rowsum = 0;
+#pragma unroll
+        for (int j = 0; j < UQ_ITEMS; ++j) {
+            if (!(tails >> j & 1u)) continue;
+            uint32_t u = (uint32_t)(k[j] >> 32), v = (uint32_t)k[j];
+            if ((u | v) & ~umask) {
+                // an id >= N: report it and keep every later access in bounds
+                pp_set_error(PP_DEV_RANGE);
+                u &= umask;
+                v &= umask;
+            }
+            const uint32_t c = cnt[j];
+            const uint32_t field = c >= a.cmax ? a.cmax : c;
+            a.ent[pos] = ((unsigned long long)v << 32) | (u | (field << a.scale));
+            if (c >= a.cmax) {
+                a.ovf_key[epos] = ((uint64_t)u << 32) | v;
+                a.ovf_cnt[epos] = c;
+                ++epos;
+            }
+            for (int p = 0; p < a.npasses; ++p) atomicAdd(&s_hist[p][(v >> (8 * p)) & (os::RADIX - 1)], 1u);
+            // this thread's entries ascend in u: add each row's run once
+            if (u != row) {
+                if (rowsum) atomicAdd(&a.d_out[row], rowsum);
+                row = u;
+                rowsum = 0;
+            }
+            rowsum += c;
+            ++pos;
+        }
+        if (rowsum) atomicAdd(&a.d_out[row], rowsum);
+        __syncthreads();  // shared scratch is reused by the next tile
     }
     __syncthreads();
-    const uint64_t gex = s_excl + texcl;
-    uint64_t pos = gex & 0xffffffffull;
-    uint64_t epos = (gex >> 32) & 0x3fffffffull;
-    const uint32_t umask = (a.scale >= 32) ? 0xffffffffu : ((1u << a.scale) - 1u);
-#pragma unroll
-    for (int j = 0; j < UQ_ITEMS; ++j) {
-        if (!(tails >> j & 1u)) continue;
-        uint32_t u = (uint32_t)(k[j] >> 32), v = (uint32_t)k[j];
-        if ((u | v) & ~umask) {
-            // an id >= N: report it and keep every later access in bounds
-            pp_set_error(PP_DEV_RANGE);
-            u &= umask;
-            v &= umask;
+    for (int i = tid; i < a.npasses * os::RADIX; i += UQ_THREADS) {
+        const uint32_t c = (&s_hist[0][0])[i];
+        if (c) atomicAdd(&a.hist[i], c);
+    }
+}
+
+// In-degree and entry count of each column from the column-sorted entries:
+// each thread sums the runs of equal columns in its stretch and adds each
+// run with one atomic.
+__global__ void __launch_bounds__(256) colscan_kernel(const unsigned long long *ent, const uint64_t *info,
+                                                      uint32_t scale, uint32_t cmax, const uint64_t *ovf_key,
+                                                      const uint32_t *ovf_cnt, unsigned long long *deg) {
+    constexpr int ITEMS = 16;
+    const uint64_t n = info[PP_INFO_NNZ0];
+    const uint64_t novf = info[PP_INFO_NOVF];
+    const uint32_t umask = (1u << scale) - 1u;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * ITEMS;
+    for (uint64_t i0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * ITEMS; i0 < n; i0 += stride) {
+        uint32_t col = 0xffffffffu;
+        unsigned long long acc = 0;
+        for (int j = 0; j < ITEMS && i0 + j < n; ++j) {
+            const unsigned long long e = ent[i0 + j];
+            const uint32_t v = (uint32_t)(e >> 32), w = (uint32_t)e;
+            uint32_t c = w >> scale;
+            if (c == cmax) c = ovf_lookup(ovf_key, ovf_cnt, novf, ((uint64_t)(w & umask) << 32) | v);
+            if (v != col) {
+                if (acc) atomicAdd(&deg[col], acc);
+                col = v;
+                acc = 0;
+            }
+            acc += (1ull << 32) | (unsigned long long)c;
         }
-        const uint32_t c = cnt[j];
-        const uint32_t field = c >= a.cmax ? a.cmax : c;
-        a.out_v[pos] = v;
-        a.out_rowc[pos] = u | (field << a.scale);
-        if (c >= a.cmax) {
-            a.ovf_key[epos] = k[j];
-            a.ovf_cnt[epos] = c;
-            ++epos;
+        if (acc) atomicAdd(&deg[col], acc);
+    }
+}
+
+// Step 4 over the column-sorted entries: kept entries move down by the
+// removed entries before their column; removed entries leave the out-degree.
+__global__ void __launch_bounds__(256) compact_kernel(const unsigned long long *ent, const uint64_t *info,
+                                                      uint32_t scale, uint32_t cmax, const uint64_t *ovf_key,
+                                                      const uint32_t *ovf_cnt, const uint8_t *kill,
+                                                      const uint32_t *shift, uint32_t *rowc, uint32_t *d_out) {
+    const uint64_t n = info[PP_INFO_NNZ0];
+    const uint64_t novf = info[PP_INFO_NOVF];
+    const uint32_t umask = (1u << scale) - 1u;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const unsigned long long e = ent[i];
+        const uint32_t v = (uint32_t)(e >> 32), w = (uint32_t)e;
+        if (kill[v]) {
+            uint32_t c = w >> scale;
+            if (c == cmax) c = ovf_lookup(ovf_key, ovf_cnt, novf, ((uint64_t)(w & umask) << 32) | v);
+            atomicSub(&d_out[w & umask], c);
+        } else {
+            rowc[i - shift[v]] = w;
         }
-        atomicAdd(&a.deg[v], (1ull << 32) | (unsigned long long)c);
-        ++pos;
     }
 }
 
@@ -255,8 +329,8 @@ struct ScanArgs {
     const unsigned long long *dmaxkey;
     uint8_t *kill;
     uint32_t *colptr;
-    uint32_t *d_out;
-    uint64_t *status;
+    uint32_t *shift;  // removed entries in the columns before each column
+    uint64_t *status_kept, *status_gone;
     uint32_t *tile_ctr;
     uint64_t *info;
 };
@@ -264,9 +338,9 @@ struct ScanArgs {
 __global__ void __launch_bounds__(SC_THREADS) mask_scan_kernel(ScanArgs a) {
     __shared__ uint32_t s_tile;
     __shared__ uint64_t s_scan[40];
-    __shared__ uint64_t s_excl;
+    __shared__ uint64_t s_excl[2];
     __shared__ unsigned long long s_red[2][SC_THREADS / 32];
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5;
     if (tid == 0) s_tile = atomicAdd(a.tile_ctr, 1u);
     __syncthreads();
     const uint64_t tile = s_tile;
@@ -276,13 +350,13 @@ __global__ void __launch_bounds__(SC_THREADS) mask_scan_kernel(ScanArgs a) {
     const uint32_t dmax = (uint32_t)(key >> 32);
     const uint32_t vmax = ~(uint32_t)key;
     const uint64_t v0 = tile * SC_TILE + (uint64_t)tid * SC_ITEMS;
-    uint32_t cnt[SC_ITEMS];
-    uint64_t sum = 0;
+    uint32_t kept[SC_ITEMS], gone[SC_ITEMS];
+    uint64_t sk = 0, sg = 0;
     unsigned long long ties = 0, sup = 0;
 #pragma unroll
     for (int j = 0; j < SC_ITEMS; ++j) {
         const uint64_t v = v0 + j;
-        cnt[j] = 0;
+        kept[j] = gone[j] = 0;
         if (v < a.N) {
             const unsigned long long w = a.deg[v];
             const uint32_t din = (uint32_t)w, entries = (uint32_t)(w >> 32);
@@ -291,38 +365,35 @@ __global__ void __launch_bounds__(SC_THREADS) mask_scan_kernel(ScanArgs a) {
             ties += din == dmax;
             sup += is_max;
             a.kill[v] = kill;
-            a.d_out[v] = 0;
-            cnt[j] = kill ? 0u : entries;
-            sum += cnt[j];
+            kept[j] = kill ? 0u : entries;
+            gone[j] = kill ? entries : 0u;
+            sk += kept[j];
+            sg += gone[j];
         }
     }
-    uint64_t total;
-    const uint64_t texcl = block_exclusive_sum<uint64_t, SC_THREADS>(sum, s_scan, &total);
-    if (tid == 0) {
-        uint64_t *st = a.status + tile;
-        if (tile == 0) {
-            st_relaxed_u64(st, F_INC | total);
-            s_excl = 0;
-        } else {
-            st_relaxed_u64(st, F_AGG | total);
-            const uint64_t ex = lookback(a.status, tile);
-            st_relaxed_u64(st, F_INC | (ex + total));
-            s_excl = ex;
-        }
-        if (tile == ntiles - 1) {
-            a.colptr[a.N] = (uint32_t)(s_excl + total);
-            a.info[PP_INFO_NNZ] = s_excl + total;
-            a.info[PP_INFO_DMAX] = dmax;
-            a.info[PP_INFO_VMAX] = vmax;
-        }
-    }
+    uint64_t tk, tg;
+    const uint64_t ek = block_exclusive_sum<uint64_t, SC_THREADS>(sk, s_scan, &tk);
+    const uint64_t eg = block_exclusive_sum<uint64_t, SC_THREADS>(sg, s_scan, &tg);
+    // warp 0 looks back for the kept entries, warp 1 for the removed ones
+    if (warp == 0) warp_tile_prefix(a.status_kept, tile, tk, &s_excl[0]);
+    if (warp == 1) warp_tile_prefix(a.status_gone, tile, tg, &s_excl[1]);
     __syncthreads();
-    uint64_t run = s_excl + texcl;
+    if (tid == 0 && tile == ntiles - 1) {
+        a.colptr[a.N] = (uint32_t)(s_excl[0] + tk);
+        a.info[PP_INFO_NNZ] = s_excl[0] + tk;
+        a.info[PP_INFO_DMAX] = dmax;
+        a.info[PP_INFO_VMAX] = vmax;
+    }
+    uint64_t rk = s_excl[0] + ek, rg = s_excl[1] + eg;
 #pragma unroll
     for (int j = 0; j < SC_ITEMS; ++j) {
         const uint64_t v = v0 + j;
-        if (v < a.N) a.colptr[v] = (uint32_t)run;
-        run += cnt[j];
+        if (v < a.N) {
+            a.colptr[v] = (uint32_t)rk;
+            a.shift[v] = (uint32_t)rg;
+        }
+        rk += kept[j];
+        rg += gone[j];
     }
     // tie and supernode counts
 #pragma unroll
@@ -346,56 +417,6 @@ __global__ void __launch_bounds__(SC_THREADS) mask_scan_kernel(ScanArgs a) {
     }
 }
 
-struct PrepassArgs {
-    const uint32_t *uv_v, *uv_rowc;
-    const uint64_t *info;
-    uint32_t scale, cmax;
-    const uint8_t *kill;
-    const uint64_t *ovf_key;
-    const uint32_t *ovf_cnt;
-    uint32_t *d_out;
-    int npasses;
-    uint32_t *hist;
-    uint32_t *status0;
-    uint64_t status0_words;
-};
-
-__global__ void __launch_bounds__(256) prepass_kernel(PrepassArgs a) {
-    __shared__ uint32_t sh[os::MAX_PASSES][os::RADIX];
-    for (int i = threadIdx.x; i < os::MAX_PASSES * os::RADIX; i += blockDim.x) (&sh[0][0])[i] = 0;
-    __syncthreads();
-    const uint64_t n = a.info[PP_INFO_NNZ0];
-    const uint64_t novf = a.info[PP_INFO_NOVF];
-    const uint32_t umask = (1u << a.scale) - 1u;
-    const int lane = threadIdx.x & 31;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); b < n; b += stride) {
-        const uint64_t i = b + lane;
-        uint32_t u = 0xffffffffu, c = 0;
-        if (i < n) {
-            const uint32_t v = a.uv_v[i];
-            const uint32_t w = a.uv_rowc[i];
-            u = w & umask;
-            if (!a.kill[v]) {
-                for (int p = 0; p < a.npasses; ++p) atomicAdd(&sh[p][(v >> (8 * p)) & (os::RADIX - 1)], 1u);
-                c = w >> a.scale;
-                if (c == a.cmax) c = ovf_lookup(a.ovf_key, a.ovf_cnt, novf, ((uint64_t)u << 32) | v);
-            }
-        }
-        // rows are contiguous: sum each row's kept counts across the warp first
-        const uint32_t peers = __match_any_sync(0xffffffffu, u);
-        const uint32_t rowsum = __reduce_add_sync(peers, c);
-        if (i < n && rowsum && lane == __ffs(peers) - 1) atomicAdd(&a.d_out[u], rowsum);
-    }
-    const uint64_t gs = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.status0_words; i += gs) a.status0[i] = 0;
-    __syncthreads();
-    for (int i = threadIdx.x; i < a.npasses * os::RADIX; i += blockDim.x) {
-        const uint32_t c = (&sh[0][0])[i];
-        if (c) atomicAdd(&a.hist[i], c);
-    }
-}
-
 __global__ void __launch_bounds__(256) finalize_kernel(const uint32_t *d_out, uint32_t N, float *inv32,
                                                        double *inv64) {
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) {
@@ -405,43 +426,27 @@ __global__ void __launch_bounds__(256) finalize_kernel(const uint32_t *d_out, ui
     }
 }
 
-// Sources and sinks of the transpose sort (key = column v, value = packed row/count).
-struct FilterSrc {
-    const uint32_t *v, *rowc;
-    const uint8_t *kill;
-    __device__ __forceinline__ bool load(uint64_t i, uint32_t &k, uint32_t &val) const {
-        k = v[i];
-        val = rowc[i];
-        return !kill[k];
-    }
-};
-struct KVSrc {
-    const uint32_t *k, *val;
-    __device__ __forceinline__ bool load(uint64_t i, uint32_t &kk, uint32_t &vv) const {
-        kk = k[i];
-        vv = val[i];
+// The transpose sorts the 64-bit entry words by their column (bits 63:32).
+struct EntSrc {
+    const unsigned long long *e;
+    __device__ __forceinline__ bool load(uint64_t i, unsigned long long &k, uint32_t &) const {
+        k = e[i];
         return true;
     }
 };
-struct KVDst {
-    uint32_t *k, *val;
-    __device__ __forceinline__ void store(uint64_t pos, uint32_t kk, uint32_t vv) const {
-        k[pos] = kk;
-        val[pos] = vv;
-    }
-};
-struct ValDst {
-    uint32_t *val;
-    __device__ __forceinline__ void store(uint64_t pos, uint32_t, uint32_t vv) const { val[pos] = vv; }
+struct EntDst {
+    unsigned long long *e;
+    __device__ __forceinline__ void store(uint64_t pos, unsigned long long k, uint32_t) const { e[pos] = k; }
 };
 
 struct Layout {
-    uint32_t *uv_v, *uv_rowc, *a_key, *a_val;
+    unsigned long long *ent[2];  // entry words, ping-pong
     unsigned long long *deg;
     uint8_t *kill;
+    uint32_t *shift;
     uint64_t *uq_status, *sc_status;
-    uint32_t *ctr;                 // [0] unique tiles, [1] scan tiles
-    unsigned long long *dmaxkey;   // follows ctr in one control block
+    uint32_t *ctr;                // [0] unique tiles, [1] scan tiles
+    unsigned long long *dmaxkey;  // follows ctr in one control block
     os::SortWs sort;
     size_t bytes;
 };
@@ -453,15 +458,13 @@ inline Layout layout(void *ws, uint64_t M, uint32_t scale) {
     Layout L;
     const uint64_t N = 1ull << scale;
     const uint64_t cap = M ? M : 1;
-    L.uv_v = c.take<uint32_t>(cap);
-    L.uv_rowc = c.take<uint32_t>(cap);
-    const bool two = num_passes(scale) >= 2;
-    L.a_key = two ? c.take<uint32_t>(cap) : nullptr;
-    L.a_val = two ? c.take<uint32_t>(cap) : nullptr;
+    L.ent[0] = c.take<unsigned long long>(cap);
+    L.ent[1] = c.take<unsigned long long>(cap);
     L.deg = c.take<unsigned long long>(N);
     L.kill = c.take<uint8_t>(N);
+    L.shift = c.take<uint32_t>(N);
     L.uq_status = c.take<uint64_t>(ceil_div(cap, UQ_TILE));
-    L.sc_status = c.take<uint64_t>(ceil_div(N, SC_TILE));
+    L.sc_status = c.take<uint64_t>(2 * ceil_div(N, SC_TILE));
     L.ctr = c.take<uint32_t>(4);  // two counters + the 8-byte max key
     L.dmaxkey = L.ctr ? reinterpret_cast<unsigned long long *>(L.ctr + 2) : nullptr;
     L.sort = os::carve_sort_ws(c, cap);
@@ -514,55 +517,52 @@ extern "C" pp_status pp_build_filter_normalize(const uint32_t *us, const uint32_
     const uint32_t cmax = (uint32_t)((1ull << (32 - scale)) - 1);
     const int P = k2::num_passes(scale);
     const int sms = sm_count();
+    const uint64_t sc_tiles = ceil_div(N, k2::SC_TILE);
 
+    const size_t word = L.sort.wide ? 8 : 4;
     cudaMemsetAsync(g->info, 0, PP_INFO_LEN * sizeof(uint64_t), s);
     cudaMemsetAsync(L.ctr, 0, 4 * sizeof(uint32_t), s);
     cudaMemsetAsync(L.deg, 0, (size_t)N * sizeof(unsigned long long), s);
+    cudaMemsetAsync(g->d_out, 0, (size_t)N * sizeof(uint32_t), s);
     cudaMemsetAsync(L.sort.hist, 0, os::kCtlBytes, s);
     cudaMemsetAsync(L.uq_status, 0, ceil_div(M ? M : 1, k2::UQ_TILE) * sizeof(uint64_t), s);
-    cudaMemsetAsync(L.sc_status, 0, ceil_div(N, k2::SC_TILE) * sizeof(uint64_t), s);
+    cudaMemsetAsync(L.sc_status, 0, 2 * sc_tiles * sizeof(uint64_t), s);
+    cudaMemsetAsync(L.sort.status[0], 0, ceil_div(M ? M : 1, os::TILE) * os::RADIX * word, s);
 
+    const unsigned ngrid = (unsigned)std::min<uint64_t>(ceil_div(N, 256), (uint64_t)sms * 8);
+    unsigned long long *sorted = L.ent[0];
     if (M) {
-        k2::UniqueArgs ua{us, vs, M, scale, cmax, L.uv_v, L.uv_rowc, g->ovf_key, g->ovf_cnt, L.deg,
+        static int uq_occ = 0;
+        if (!uq_occ) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&uq_occ, k2::unique_kernel, k2::UQ_THREADS, 0);
+            if (uq_occ < 1) uq_occ = 1;
+        }
+        const unsigned ugrid = (unsigned)std::min<uint64_t>(ceil_div(M, k2::UQ_TILE), (uint64_t)sms * uq_occ);
+        k2::UniqueArgs ua{us, vs, M, scale, cmax, L.ent[0], g->ovf_key, g->ovf_cnt, g->d_out, L.sort.hist, P,
                           L.uq_status, L.ctr, g->info};
-        k2::unique_kernel<<<(unsigned)ceil_div(M, k2::UQ_TILE), k2::UQ_THREADS, 0, s>>>(ua);
+        k2::unique_kernel<<<ugrid, k2::UQ_THREADS, 0, s>>>(ua);
+        count_launch();
+        // transpose: every entry sorted by column, P passes over bits 32 .. 32+scale
+        const uint64_t *n_dev = g->info + PP_INFO_NNZ0;
+        for (int p = 0; p < P; ++p) {
+            os::launch_pass<unsigned long long, false>(L.sort, p, P, k2::EntSrc{L.ent[p & 1]},
+                                                       k2::EntDst{L.ent[(p + 1) & 1]}, n_dev, M, s, 32);
+        }
+        sorted = L.ent[P & 1];
+        const unsigned cgrid = (unsigned)std::min<uint64_t>(ceil_div(M, 256 * 16), (uint64_t)sms * 8);
+        k2::colscan_kernel<<<cgrid, 256, 0, s>>>(sorted, g->info, scale, cmax, g->ovf_key, g->ovf_cnt, L.deg);
         count_launch();
     }
-    const unsigned ngrid = (unsigned)std::min<uint64_t>(ceil_div(N, 256), (uint64_t)sms * 8);
     k2::dmax_kernel<<<ngrid, 256, 0, s>>>(L.deg, N, g->d_in, L.dmaxkey);
-    k2::ScanArgs sa{L.deg, N, rule == PP_SUPERNODE_ALL_TIES, L.dmaxkey, L.kill, g->colptr, g->d_out,
-                    L.sc_status, L.ctr + 1, g->info};
-    k2::mask_scan_kernel<<<(unsigned)ceil_div(N, k2::SC_TILE), k2::SC_THREADS, 0, s>>>(sa);
+    k2::ScanArgs sa{L.deg, N, rule == PP_SUPERNODE_ALL_TIES, L.dmaxkey, L.kill, g->colptr, L.shift,
+                    L.sc_status, L.sc_status + sc_tiles, L.ctr + 1, g->info};
+    k2::mask_scan_kernel<<<(unsigned)sc_tiles, k2::SC_THREADS, 0, s>>>(sa);
     count_launch(2);
     if (M) {
-        const size_t word = L.sort.wide ? 8 : 4;
-        k2::PrepassArgs pa{L.uv_v, L.uv_rowc, g->info, scale, cmax, L.kill, g->ovf_key, g->ovf_cnt, g->d_out, P,
-                           L.sort.hist, static_cast<uint32_t *>(L.sort.status[0]),
-                           ceil_div(M, os::TILE) * os::RADIX * word / 4};
-        const unsigned pgrid = (unsigned)std::min<uint64_t>(ceil_div(M, 256 * 4), (uint64_t)sms * 8);
-        k2::prepass_kernel<<<pgrid, 256, 0, s>>>(pa);
+        const unsigned pgrid = (unsigned)std::min<uint64_t>(ceil_div(M, 256), (uint64_t)sms * 16);
+        k2::compact_kernel<<<pgrid, 256, 0, s>>>(sorted, g->info, scale, cmax, g->ovf_key, g->ovf_cnt, L.kill,
+                                                 L.shift, g->rowc, g->d_out);
         count_launch();
-        // pass 0 reads every unique entry and drops the zeroed columns; later
-        // passes see only the nnz entries that survived
-        const uint64_t *n_dev = g->info + PP_INFO_NNZ0;
-        const uint64_t *n_kept = g->info + PP_INFO_NNZ;
-        const k2::FilterSrc fsrc{L.uv_v, L.uv_rowc, L.kill};
-        const k2::ValDst out{g->rowc};
-        if (P == 1) {
-            os::launch_pass<uint32_t, true>(L.sort, 0, P, fsrc, out, n_dev, M, s);
-        } else {
-            // ping-pong between A and the (by then consumed) unique-pass arrays
-            uint32_t *bk = L.uv_v, *bv = L.uv_rowc;
-            os::launch_pass<uint32_t, true>(L.sort, 0, P, fsrc, k2::KVDst{L.a_key, L.a_val}, n_dev, M, s);
-            for (int p = 1; p < P - 1; ++p) {
-                const bool odd = p & 1;
-                os::launch_pass<uint32_t, true>(L.sort, p, P, k2::KVSrc{odd ? L.a_key : bk, odd ? L.a_val : bv},
-                                                k2::KVDst{odd ? bk : L.a_key, odd ? bv : L.a_val}, n_kept, M, s);
-            }
-            const bool odd = (P - 1) & 1;
-            os::launch_pass<uint32_t, true>(L.sort, P - 1, P, k2::KVSrc{odd ? L.a_key : bk, odd ? L.a_val : bv},
-                                            out, n_kept, M, s);
-        }
     }
     k2::finalize_kernel<<<ngrid, 256, 0, s>>>(g->d_out, N, g->inv_dout32, g->inv_dout64);
     count_launch();

@@ -41,7 +41,7 @@ constexpr uint32_t LONG_FLAG = 0x80000000u;
 constexpr int PLAN_THREADS = 256;
 constexpr int PLAN_ITEMS = 16;
 constexpr int PLAN_TILE = PLAN_THREADS * PLAN_ITEMS;
-constexpr uint64_t F_AGG = 1ull << 62, F_INC = 2ull << 62, F_ANY = 3ull << 62;
+constexpr uint64_t F_AGG = 1ull << 62, F_INC = 2ull << 62;
 
 // One graph of the batch, as the kernels see it.
 struct BG {
@@ -228,36 +228,24 @@ __global__ void __launch_bounds__(PLAN_THREADS) plan_kernel(const __grid_constan
     const uint64_t mine = (uint64_t)__popc(bmask) | ((uint64_t)nitems << 31);
     uint64_t total;
     const uint64_t texcl = block_exclusive_sum<uint64_t, PLAN_THREADS>(mine, s_scan, &total);
-    if (tid == 0) {
+    if (tid < 32) {
+        // warp 0: publish this tile's counts and look back over earlier tiles
         uint64_t *st = w.plan_status + tile;
         uint64_t ex = 0;
         if (tile == 0) {
-            st_relaxed_u64(st, F_INC | total);
+            if (tid == 0) st_relaxed_u64(st, F_INC | total);
         } else {
-            st_relaxed_u64(st, F_AGG | total);
-            uint64_t p = tile - 1;
-            uint32_t spins = 0;
-            while (true) {
-                const uint64_t sv = ld_relaxed_u64(w.plan_status + p);
-                if ((sv & F_ANY) == 0) {
-                    if (++spins > kSpinLimit) {
-                        pp_set_error(PP_DEV_TIMEOUT);
-                        break;
-                    }
-                    backoff(spins);
-                    continue;
-                }
-                ex += sv & ~F_ANY;
-                if (sv & F_INC) break;
-                --p;  // tile 0 always publishes an inclusive word
-            }
-            st_relaxed_u64(st, F_INC | (ex + total));
+            if (tid == 0) st_relaxed_u64(st, F_AGG | total);
+            ex = warp_lookback(w.plan_status, tile);
+            if (tid == 0) st_relaxed_u64(st, F_INC | (ex + total));
         }
-        s_excl = ex;
-        if (tile == ntiles - 1) {
-            const uint64_t inc = ex + total;
-            w.ctl[1] = (uint32_t)(inc & 0x7fffffffull);
-            w.ctl[0] = (uint32_t)(inc >> 31);
+        if (tid == 0) {
+            s_excl = ex;
+            if (tile == ntiles - 1) {
+                const uint64_t inc = ex + total;
+                w.ctl[1] = (uint32_t)(inc & 0x7fffffffull);
+                w.ctl[0] = (uint32_t)(inc >> 31);
+            }
         }
     }
     __syncthreads();

@@ -102,7 +102,7 @@ __device__ __forceinline__ uint32_t ovf_lookup(const uint64_t *keys, const uint3
 
 // ------------------------------------------------------------------- planning
 
-constexpr uint64_t F_AGG = 1ull << 62, F_INC = 2ull << 62, F_ANY = 3ull << 62;
+constexpr uint64_t F_AGG = 1ull << 62, F_INC = 2ull << 62;
 
 // Column v starts a work item if it is long, follows a long column, starts in
 // a new SHORTMAX-entry chunk of the entry array, or is a multiple of
@@ -151,36 +151,24 @@ __global__ void __launch_bounds__(PLAN_THREADS) plan_kernel(Args a) {
     const uint64_t mine = (uint64_t)__popc(bmask) | ((uint64_t)nitems << 31);
     uint64_t total;
     const uint64_t texcl = block_exclusive_sum<uint64_t, PLAN_THREADS>(mine, s_scan, &total);
-    if (tid == 0) {
+    if (tid < 32) {
+        // warp 0: publish this tile's counts and look back over earlier tiles
         uint64_t *st = a.plan_status + tile;
         uint64_t ex = 0;
         if (tile == 0) {
-            st_relaxed_u64(st, F_INC | total);
+            if (tid == 0) st_relaxed_u64(st, F_INC | total);
         } else {
-            st_relaxed_u64(st, F_AGG | total);
-            uint64_t p = tile - 1;
-            uint32_t spins = 0;
-            while (true) {
-                const uint64_t sv = ld_relaxed_u64(a.plan_status + p);
-                if ((sv & F_ANY) == 0) {
-                    if (++spins > kSpinLimit) {
-                        pp_set_error(PP_DEV_TIMEOUT);
-                        break;
-                    }
-                    backoff(spins);
-                    continue;
-                }
-                ex += sv & ~F_ANY;
-                if (sv & F_INC) break;
-                --p;  // tile 0 always publishes an inclusive word
-            }
-            st_relaxed_u64(st, F_INC | (ex + total));
+            if (tid == 0) st_relaxed_u64(st, F_AGG | total);
+            ex = warp_lookback(a.plan_status, tile);
+            if (tid == 0) st_relaxed_u64(st, F_INC | (ex + total));
         }
-        s_excl = ex;
-        if (tile == ntiles - 1) {
-            const uint64_t inc = ex + total;
-            a.ctl->n_bound = (uint32_t)(inc & 0x7fffffffull);
-            a.ctl->n_items = (uint32_t)(inc >> 31);
+        if (tid == 0) {
+            s_excl = ex;
+            if (tile == ntiles - 1) {
+                const uint64_t inc = ex + total;
+                a.ctl->n_bound = (uint32_t)(inc & 0x7fffffffull);
+                a.ctl->n_items = (uint32_t)(inc >> 31);
+            }
         }
     }
     __syncthreads();

@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(THREADS, 3) pass_kernel(Src src, Dst dst, Pass
 template <typename KeyT, class Src>
 __global__ void __launch_bounds__(256) hist_kernel(Src src, const uint64_t *n_dev, uint64_t n_host,
                                                    int npasses, uint32_t *hist, uint32_t *status0,
-                                                   uint64_t status0_words) {
+                                                   uint64_t status0_words, uint32_t shift0 = 0) {
     __shared__ uint32_t sh[MAX_PASSES][RADIX];
     for (int i = threadIdx.x; i < MAX_PASSES * RADIX; i += blockDim.x) (&sh[0][0])[i] = 0;
     __syncthreads();
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(256) hist_kernel(Src src, const uint64_t *n_de
         KeyT k;
         uint32_t val;
         if (!src.load(i, k, val)) continue;
-        for (int p = 0; p < npasses; ++p) atomicAdd(&sh[p][(uint32_t)(k >> (8 * p)) & (RADIX - 1)], 1u);
+        for (int p = 0; p < npasses; ++p) atomicAdd(&sh[p][(uint32_t)(k >> (shift0 + 8 * p)) & (RADIX - 1)], 1u);
     }
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < status0_words; i += stride)
         status0[i] = 0;
@@ -248,9 +248,9 @@ inline bool prefer_shared(K kernel) {
 // Launches pass `p` (of npasses) of a sort prepared in `w`.
 template <typename KeyT, bool HAS_VAL, class Src, class Dst>
 inline void launch_pass(const SortWs &w, int p, int npasses, Src src, Dst dst, const uint64_t *n_dev,
-                        uint64_t n_max, cudaStream_t s) {
+                        uint64_t n_max, cudaStream_t s, uint32_t shift0 = 0) {
     PassCtl ctl;
-    ctl.shift = 8u * (uint32_t)p;
+    ctl.shift = shift0 + 8u * (uint32_t)p;
     ctl.hist = w.hist + p * RADIX;
     ctl.status = w.status[p & 1];
     ctl.status_next = (p + 1 < npasses) ? w.status[(p + 1) & 1] : nullptr;

@@ -197,6 +197,43 @@ __device__ __forceinline__ T block_sum(T x, T *scratch) {
     return r;  // valid in thread 0
 }
 
+// Decoupled look-back by one whole warp over 64-bit status words (flags in
+// bits 63:62: 1 = aggregate of that tile only, 2 = inclusive prefix; the sum
+// in bits 61:0).  Lane k reads the word of tile `tile - 1 - k`, so one round
+// trip covers 32 predecessors; the walk stops at the nearest inclusive word.
+// Returns the exclusive prefix of `tile` in every lane.  Waits are bounded:
+// after kSpinLimit empty polls the device error word gets PP_DEV_TIMEOUT.
+__device__ __forceinline__ uint64_t warp_lookback(const uint64_t *status, uint64_t tile) {
+    constexpr uint64_t INC = 2ull << 62, ANY = 3ull << 62;
+    const int lane = threadIdx.x & 31;
+    uint64_t excl = 0;
+    long long p = (long long)tile - 1;
+    uint32_t spins = 0;
+    while (p >= 0) {
+        const long long q = p - lane;
+        const uint64_t s = q >= 0 ? ld_relaxed_u64(status + q) : INC;  // tile 0 is always inclusive
+        const uint32_t nready = __ballot_sync(0xffffffffu, (s & ANY) == 0);
+        const uint32_t inc = __ballot_sync(0xffffffffu, (s & INC) != 0 && (s & ANY) != 0);
+        const int first_nr = nready ? __ffs(nready) - 1 : 32;
+        const int first_inc = inc ? __ffs(inc) - 1 : 32;
+        const int take = first_inc < first_nr ? first_inc + 1 : first_nr;  // lanes 0 .. take-1
+        uint64_t v = lane < take ? (s & ~ANY) : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        excl += v;
+        if (first_inc < first_nr) break;
+        p -= take;
+        if (take == 0) {
+            if (++spins > kSpinLimit) {
+                if (lane == 0) pp_set_error(PP_DEV_TIMEOUT);
+                break;
+            }
+            backoff(spins);
+        }
+    }
+    return excl;
+}
+
 }  // namespace pp
 
 // Host accessor of this translation unit's device error word.
