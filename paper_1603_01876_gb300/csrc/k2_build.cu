@@ -110,6 +110,7 @@ struct UniqueArgs {
     uint32_t *d_out;          // [N]: row sums before the filter
     uint32_t *hist;           // [npasses * 256] column digits, for the transpose
     int npasses;
+    int vec;                  // us and vs are 16-byte aligned: load 4 ids at a time
     uint64_t *status;
     uint32_t *tile_ctr;
     uint64_t *info;
@@ -122,6 +123,7 @@ __global__ void __launch_bounds__(UQ_THREADS) unique_kernel(UniqueArgs a) {
     __shared__ long long s_max[UQ_THREADS / 32];
     __shared__ uint64_t s_excl;
     __shared__ uint32_t s_hist[os::MAX_PASSES][os::RADIX];
+    __shared__ unsigned long long s_out[UQ_TILE];  // the tile's entries, written out coalesced
     const int tid = threadIdx.x;
     for (int i = tid; i < os::MAX_PASSES * os::RADIX; i += UQ_THREADS) (&s_hist[0][0])[i] = 0;
     const uint64_t ntiles = uq_tiles(a.M);
@@ -135,8 +137,21 @@ __global__ void __launch_bounds__(UQ_THREADS) unique_kernel(UniqueArgs a) {
         const uint64_t my0 = base + (uint64_t)tid * UQ_ITEMS;
 
         uint64_t k[UQ_ITEMS];
+        if (a.vec && my0 + UQ_ITEMS <= a.M) {
+            const uint4 *pu = reinterpret_cast<const uint4 *>(a.us + my0);
+            const uint4 *pv = reinterpret_cast<const uint4 *>(a.vs + my0);
 #pragma unroll
-        for (int j = 0; j < UQ_ITEMS; ++j) k[j] = (my0 + j < a.M) ? edge_key(a.us, a.vs, my0 + j) : ~0ull;
+            for (int q = 0; q < UQ_ITEMS / 4; ++q) {
+                const uint4 x = __ldg(pu + q), y = __ldg(pv + q);
+                k[4 * q + 0] = ((uint64_t)x.x << 32) | y.x;
+                k[4 * q + 1] = ((uint64_t)x.y << 32) | y.y;
+                k[4 * q + 2] = ((uint64_t)x.z << 32) | y.z;
+                k[4 * q + 3] = ((uint64_t)x.w << 32) | y.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < UQ_ITEMS; ++j) k[j] = (my0 + j < a.M) ? edge_key(a.us, a.vs, my0 + j) : ~0ull;
+        }
         const uint64_t knext = (my0 + UQ_ITEMS < a.M) ? edge_key(a.us, a.vs, my0 + UQ_ITEMS) : ~0ull;
 
         // A run ends ("tail") where the next key differs.
@@ -212,7 +227,7 @@ __global__ void __launch_bounds__(UQ_THREADS) unique_kernel(UniqueArgs a) {
             a.info[PP_INFO_NOVF] = (inc >> 32) & 0x3fffffffull;
         }
         const uint64_t gex = s_excl + texcl;
-        uint64_t pos = gex & 0xffffffffull;
+        uint32_t lpos = (uint32_t)texcl;  // place inside the tile's output
         uint64_t epos = (gex >> 32) & 0x3fffffffull;
         uint32_t row = 0xffffffffu, rowsum = 0;
 #pragma unroll
@@ -227,7 +242,7 @@ __global__ void __launch_bounds__(UQ_THREADS) unique_kernel(UniqueArgs a) {
             }
             const uint32_t c = cnt[j];
             const uint32_t field = c >= a.cmax ? a.cmax : c;
-            a.ent[pos] = ((unsigned long long)v << 32) | (u | (field << a.scale));
+            s_out[lpos] = ((unsigned long long)v << 32) | (u | (field << a.scale));
             if (c >= a.cmax) {
                 a.ovf_key[epos] = ((uint64_t)u << 32) | v;
                 a.ovf_cnt[epos] = c;
@@ -241,9 +256,15 @@ __global__ void __launch_bounds__(UQ_THREADS) unique_kernel(UniqueArgs a) {
                 rowsum = 0;
             }
             rowsum += c;
-            ++pos;
+            ++lpos;
         }
         if (rowsum) atomicAdd(&a.d_out[row], rowsum);
+        __syncthreads();
+        {
+            unsigned long long *dst = a.ent + (s_excl & 0xffffffffull);
+            const uint32_t n_out = (uint32_t)total;
+            for (uint32_t i = tid; i < n_out; i += UQ_THREADS) dst[i] = s_out[i];
+        }
         __syncthreads();  // shared scratch is reused by the next tile
     }
     __syncthreads();
@@ -253,54 +274,86 @@ __global__ void __launch_bounds__(UQ_THREADS) unique_kernel(UniqueArgs a) {
     }
 }
 
-// In-degree and entry count of each column from the column-sorted entries:
-// each thread sums the runs of equal columns in its stretch and adds each
-// run with one atomic.
+constexpr int CS_ITEMS = 8;
+constexpr int CS_TILE = 256 * CS_ITEMS;
+
+// In-degree and entry count of each column from the column-sorted entries.
+// A block stages a tile through shared memory (coalesced reads), then each
+// thread sums the runs of equal columns in its CS_ITEMS consecutive entries
+// and adds each run with one atomic.
 __global__ void __launch_bounds__(256) colscan_kernel(const unsigned long long *ent, const uint64_t *info,
                                                       uint32_t scale, uint32_t cmax, const uint64_t *ovf_key,
                                                       const uint32_t *ovf_cnt, unsigned long long *deg) {
-    constexpr int ITEMS = 16;
+    // row stride CS_ITEMS + 1 words: a half-warp's reads of its own rows hit distinct banks
+    __shared__ unsigned long long s[256 * (CS_ITEMS + 1)];
+    const int tid = threadIdx.x;
     const uint64_t n = info[PP_INFO_NNZ0];
     const uint64_t novf = info[PP_INFO_NOVF];
     const uint32_t umask = (1u << scale) - 1u;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * ITEMS;
-    for (uint64_t i0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * ITEMS; i0 < n; i0 += stride) {
+    for (uint64_t t0 = (uint64_t)blockIdx.x * CS_TILE; t0 < n; t0 += (uint64_t)gridDim.x * CS_TILE) {
+#pragma unroll
+        for (int r = 0; r < CS_ITEMS; ++r) {
+            const uint32_t k = tid + 256 * r;
+            if (t0 + k < n) s[(k / CS_ITEMS) * (CS_ITEMS + 1) + k % CS_ITEMS] = ent[t0 + k];
+        }
+        __syncthreads();
         uint32_t col = 0xffffffffu;
         unsigned long long acc = 0;
-        for (int j = 0; j < ITEMS && i0 + j < n; ++j) {
-            const unsigned long long e = ent[i0 + j];
-            const uint32_t v = (uint32_t)(e >> 32), w = (uint32_t)e;
-            uint32_t c = w >> scale;
-            if (c == cmax) c = ovf_lookup(ovf_key, ovf_cnt, novf, ((uint64_t)(w & umask) << 32) | v);
-            if (v != col) {
-                if (acc) atomicAdd(&deg[col], acc);
-                col = v;
-                acc = 0;
+        const uint64_t i0 = t0 + (uint64_t)tid * CS_ITEMS;
+#pragma unroll
+        for (int j = 0; j < CS_ITEMS; ++j) {
+            if (i0 + j < n) {
+                const unsigned long long e = s[tid * (CS_ITEMS + 1) + j];
+                const uint32_t v = (uint32_t)(e >> 32), w = (uint32_t)e;
+                uint32_t c = w >> scale;
+                if (c == cmax) c = ovf_lookup(ovf_key, ovf_cnt, novf, ((uint64_t)(w & umask) << 32) | v);
+                if (v != col) {
+                    if (acc) atomicAdd(&deg[col], acc);
+                    col = v;
+                    acc = 0;
+                }
+                acc += (1ull << 32) | (unsigned long long)c;
             }
-            acc += (1ull << 32) | (unsigned long long)c;
         }
         if (acc) atomicAdd(&deg[col], acc);
+        __syncthreads();
     }
 }
 
+constexpr uint32_t KILL_BIT = 1u << 31;
+constexpr int CP_ITEMS = 4;
+
 // Step 4 over the column-sorted entries: kept entries move down by the
 // removed entries before their column; removed entries leave the out-degree.
+// shift[v] carries the removed-entry count and, in bit 31, the column's
+// removal flag.
 __global__ void __launch_bounds__(256) compact_kernel(const unsigned long long *ent, const uint64_t *info,
                                                       uint32_t scale, uint32_t cmax, const uint64_t *ovf_key,
-                                                      const uint32_t *ovf_cnt, const uint8_t *kill,
-                                                      const uint32_t *shift, uint32_t *rowc, uint32_t *d_out) {
+                                                      const uint32_t *ovf_cnt, const uint32_t *shift, uint32_t *rowc,
+                                                      uint32_t *d_out) {
     const uint64_t n = info[PP_INFO_NNZ0];
     const uint64_t novf = info[PP_INFO_NOVF];
     const uint32_t umask = (1u << scale) - 1u;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        const unsigned long long e = ent[i];
-        const uint32_t v = (uint32_t)(e >> 32), w = (uint32_t)e;
-        if (kill[v]) {
-            uint32_t c = w >> scale;
-            if (c == cmax) c = ovf_lookup(ovf_key, ovf_cnt, novf, ((uint64_t)(w & umask) << 32) | v);
-            atomicSub(&d_out[w & umask], c);
-        } else {
-            rowc[i - shift[v]] = w;
+    const uint64_t step = (uint64_t)gridDim.x * 256 * CP_ITEMS;
+    for (uint64_t b = (uint64_t)blockIdx.x * 256 * CP_ITEMS + threadIdx.x; b < n; b += step) {
+        unsigned long long e[CP_ITEMS];
+        uint32_t sh[CP_ITEMS];
+#pragma unroll
+        for (int q = 0; q < CP_ITEMS; ++q) e[q] = (b + 256 * q < n) ? ent[b + 256 * q] : 0ull;
+#pragma unroll
+        for (int q = 0; q < CP_ITEMS; ++q) sh[q] = (b + 256 * q < n) ? shift[(uint32_t)(e[q] >> 32)] : 0u;
+#pragma unroll
+        for (int q = 0; q < CP_ITEMS; ++q) {
+            const uint64_t i = b + 256 * q;
+            if (i >= n) break;
+            const uint32_t v = (uint32_t)(e[q] >> 32), w = (uint32_t)e[q];
+            if (sh[q] & KILL_BIT) {
+                uint32_t c = w >> scale;
+                if (c == cmax) c = ovf_lookup(ovf_key, ovf_cnt, novf, ((uint64_t)(w & umask) << 32) | v);
+                atomicSub(&d_out[w & umask], c);
+            } else {
+                rowc[i - sh[q]] = w;
+            }
         }
     }
 }
@@ -327,9 +380,8 @@ struct ScanArgs {
     uint32_t N;
     int all_ties;
     const unsigned long long *dmaxkey;
-    uint8_t *kill;
     uint32_t *colptr;
-    uint32_t *shift;  // removed entries in the columns before each column
+    uint32_t *shift;  // removed entries in the columns before each column | KILL_BIT
     uint64_t *status_kept, *status_gone;
     uint32_t *tile_ctr;
     uint64_t *info;
@@ -350,7 +402,7 @@ __global__ void __launch_bounds__(SC_THREADS) mask_scan_kernel(ScanArgs a) {
     const uint32_t dmax = (uint32_t)(key >> 32);
     const uint32_t vmax = ~(uint32_t)key;
     const uint64_t v0 = tile * SC_TILE + (uint64_t)tid * SC_ITEMS;
-    uint32_t kept[SC_ITEMS], gone[SC_ITEMS];
+    uint32_t kept[SC_ITEMS], gone[SC_ITEMS], killed = 0;
     uint64_t sk = 0, sg = 0;
     unsigned long long ties = 0, sup = 0;
 #pragma unroll
@@ -364,7 +416,7 @@ __global__ void __launch_bounds__(SC_THREADS) mask_scan_kernel(ScanArgs a) {
             const bool kill = is_max || din == 1;
             ties += din == dmax;
             sup += is_max;
-            a.kill[v] = kill;
+            killed |= (uint32_t)kill << j;
             kept[j] = kill ? 0u : entries;
             gone[j] = kill ? entries : 0u;
             sk += kept[j];
@@ -390,7 +442,8 @@ __global__ void __launch_bounds__(SC_THREADS) mask_scan_kernel(ScanArgs a) {
         const uint64_t v = v0 + j;
         if (v < a.N) {
             a.colptr[v] = (uint32_t)rk;
-            a.shift[v] = (uint32_t)rg;
+            // a kept column with entries has fewer than 2^31 removed entries before it
+            a.shift[v] = (uint32_t)rg | ((killed >> j & 1u) ? KILL_BIT : 0u);
         }
         rk += kept[j];
         rg += gone[j];
@@ -442,7 +495,6 @@ struct EntDst {
 struct Layout {
     unsigned long long *ent[2];  // entry words, ping-pong
     unsigned long long *deg;
-    uint8_t *kill;
     uint32_t *shift;
     uint64_t *uq_status, *sc_status;
     uint32_t *ctr;                // [0] unique tiles, [1] scan tiles
@@ -461,7 +513,6 @@ inline Layout layout(void *ws, uint64_t M, uint32_t scale) {
     L.ent[0] = c.take<unsigned long long>(cap);
     L.ent[1] = c.take<unsigned long long>(cap);
     L.deg = c.take<unsigned long long>(N);
-    L.kill = c.take<uint8_t>(N);
     L.shift = c.take<uint32_t>(N);
     L.uq_status = c.take<uint64_t>(ceil_div(cap, UQ_TILE));
     L.sc_status = c.take<uint64_t>(2 * ceil_div(N, SC_TILE));
@@ -538,7 +589,8 @@ extern "C" pp_status pp_build_filter_normalize(const uint32_t *us, const uint32_
             if (uq_occ < 1) uq_occ = 1;
         }
         const unsigned ugrid = (unsigned)std::min<uint64_t>(ceil_div(M, k2::UQ_TILE), (uint64_t)sms * uq_occ);
-        k2::UniqueArgs ua{us, vs, M, scale, cmax, L.ent[0], g->ovf_key, g->ovf_cnt, g->d_out, L.sort.hist, P,
+        const int vec = (((uintptr_t)us | (uintptr_t)vs) & 15u) == 0;
+        k2::UniqueArgs ua{us, vs, M, scale, cmax, L.ent[0], g->ovf_key, g->ovf_cnt, g->d_out, L.sort.hist, P, vec,
                           L.uq_status, L.ctr, g->info};
         k2::unique_kernel<<<ugrid, k2::UQ_THREADS, 0, s>>>(ua);
         count_launch();
@@ -549,19 +601,19 @@ extern "C" pp_status pp_build_filter_normalize(const uint32_t *us, const uint32_
                                                        k2::EntDst{L.ent[(p + 1) & 1]}, n_dev, M, s, 32);
         }
         sorted = L.ent[P & 1];
-        const unsigned cgrid = (unsigned)std::min<uint64_t>(ceil_div(M, 256 * 16), (uint64_t)sms * 8);
+        const unsigned cgrid = (unsigned)std::min<uint64_t>(ceil_div(M, k2::CS_TILE), (uint64_t)sms * 8);
         k2::colscan_kernel<<<cgrid, 256, 0, s>>>(sorted, g->info, scale, cmax, g->ovf_key, g->ovf_cnt, L.deg);
         count_launch();
     }
     k2::dmax_kernel<<<ngrid, 256, 0, s>>>(L.deg, N, g->d_in, L.dmaxkey);
-    k2::ScanArgs sa{L.deg, N, rule == PP_SUPERNODE_ALL_TIES, L.dmaxkey, L.kill, g->colptr, L.shift,
+    k2::ScanArgs sa{L.deg, N, rule == PP_SUPERNODE_ALL_TIES, L.dmaxkey, g->colptr, L.shift,
                     L.sc_status, L.sc_status + sc_tiles, L.ctr + 1, g->info};
     k2::mask_scan_kernel<<<(unsigned)sc_tiles, k2::SC_THREADS, 0, s>>>(sa);
     count_launch(2);
     if (M) {
-        const unsigned pgrid = (unsigned)std::min<uint64_t>(ceil_div(M, 256), (uint64_t)sms * 16);
-        k2::compact_kernel<<<pgrid, 256, 0, s>>>(sorted, g->info, scale, cmax, g->ovf_key, g->ovf_cnt, L.kill,
-                                                 L.shift, g->rowc, g->d_out);
+        const unsigned pgrid = (unsigned)std::min<uint64_t>(ceil_div(M, 256 * k2::CP_ITEMS), (uint64_t)sms * 8);
+        k2::compact_kernel<<<pgrid, 256, 0, s>>>(sorted, g->info, scale, cmax, g->ovf_key, g->ovf_cnt, L.shift,
+                                                 g->rowc, g->d_out);
         count_launch();
     }
     k2::finalize_kernel<<<ngrid, 256, 0, s>>>(g->d_out, N, g->inv_dout32, g->inv_dout64);
