@@ -134,16 +134,11 @@ def k1_bytes(M, scale):
 
 
 def k2_bytes(M, N, nnz0, nnz, scale):
-    P2 = -(-scale // 8)
-    b = 8 * M + 8 * nnz0 + 16 * N          # unique pass: read edges, write entries, degree words
-    b += 12 * N + 17 * N                   # max reduction; mask + column pointers + d_out reset
-    b += 8 * nnz0 + N + 8 * N              # pre-pass: entries, mask, d_out
-    if P2 == 1:
-        b += 8 * nnz0 + 4 * nnz
-    else:
-        b += 8 * nnz0 + 8 * nnz + 16 * nnz * (P2 - 2) + 12 * nnz
-    b += 16 * N                            # 1/d_out in two precisions
-    return b
+    """Algorithmic bytes of Kernel 2 as a design-independent count: read the
+    sorted edges, write and re-read (u, v, count) triples, write the filtered
+    matrix, transpose it (read + write), and about 25 bytes of per-vertex
+    vectors (d_in, mask, d_out, column pointers, 1/d_out)."""
+    return 8 * M + 12 * nnz0 + 12 * nnz0 + 12 * nnz + 24 * nnz + 25 * N
 
 
 def run_ours(args):
@@ -225,20 +220,34 @@ def run_ours(args):
         raise RuntimeError("device error word %#x in the timed region" % err)
     ms_step = total_ms / args.steps
 
-    # Kernel 3 in binary64 on the same graph, and the binary32 error against it
+    def time_k3(dtype, out, n_iters, reps=3):
+        pp.pagerank(g, r0, n_iters, DAMPING, dtype, out=out, workspace=ws)
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record(stream)
+        for _ in range(reps):
+            pp.pagerank(g, r0, n_iters, DAMPING, dtype, out=out, workspace=ws)
+        e[1].record(stream)
+        torch.cuda.synchronize()
+        return e[0].elapsed_time(e[1]) / reps
+
+    # Kernel 3 in binary64 and with the gathered vector in bfloat16 on the same
+    # graph; errors of the binary32 and bfloat16 ranks against binary64
     r64 = torch.empty(N, dtype=torch.float64, device=dev)
-    pp.pagerank(g, r0, iters, DAMPING, "fp64", out=r64, workspace=ws)
-    torch.cuda.synchronize()
-    ev64 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    ev64[0].record(stream)
-    for _ in range(3):
-        pp.pagerank(g, r0, iters, DAMPING, "fp64", out=r64, workspace=ws)
-    ev64[1].record(stream)
-    torch.cuda.synchronize()
-    k3_64 = ev64[0].elapsed_time(ev64[1]) / 3
-    d = (r_out.double() - r64).abs()
-    l1_fp32 = float(d.sum() / r64.abs().sum())
-    maxrel_fp32 = float((d / r64.abs()).max())
+    k3_64 = time_k3("fp64", r64, iters)
+    r_bf = torch.empty(N, dtype=torch.float32, device=dev)
+    k3_bf = time_k3("bf16", r_bf, iters)
+    # the iteration kernel alone: the stage minus its set-up (the same call with 0 iterations)
+    r_tmp = torch.empty(N, dtype=torch.float64 if args.dtype == "fp64" else torch.float32, device=dev)
+    k3_setup = time_k3(args.dtype, r_tmp, 0)
+    del r_tmp
+
+    def errors(r):
+        d = (r.double() - r64).abs()
+        return float(d.sum() / r64.abs().sum()), float((d / r64.abs()).max())
+
+    l1_fp32, maxrel_fp32 = errors(r_out)
+    l1_bf, maxrel_bf = errors(r_bf)
 
     # end to end through the host-buffer entry point
     uh = u.cpu().pin_memory()
@@ -268,18 +277,24 @@ def run_ours(args):
     peak, peak_kind = _peaks()
     b1, P = k1_bytes(M, scale)
     b2 = k2_bytes(M, N, nnz0, nnz, scale)
-    b3 = k3_bytes_per_iter(nnz, N, args.dtype) * iters
+    b3_iter = k3_bytes_per_iter(nnz, N, args.dtype)
+    b3 = b3_iter * iters
     med = statistics.median
     stages = {"k1_sort": (med(k1), b1), "k2_filter": (med(k2), b2), "k3_pagerank": (med(k3), b3)}
     dom = max(stages, key=lambda s: stages[s][0])
     dom_ms, dom_bytes = stages[dom]
+    iter_ms = (med(k3) - k3_setup) / iters
     if dom == "k3_pagerank":
+        # per launch of the iteration kernel: one iteration's bytes over its average duration
         kname, launches_per_stage = "k3 iterate_kernel (warp-tiled, degree-bucketed pull SpMV)", iters
-    elif dom == "k1_sort":
-        kname, launches_per_stage = "k1 onesweep pass_kernel (8-bit LSD pass)", P
+        achieved = b3_iter / (iter_ms * 1e-3) / 1e9
+        per_launch = {"bytes": b3_iter, "ms": iter_ms,
+                      "how": "(K3 stage time - same call with 0 iterations) / iterations, CUDA events"}
     else:
-        kname, launches_per_stage = "k2 stage (unique + transpose passes)", 1
-    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+        kname = "k1 onesweep pass_kernel (8-bit LSD pass)" if dom == "k1_sort" else "k2 stage"
+        launches_per_stage = P if dom == "k1_sort" else 1
+        achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+        per_launch = {"bytes": dom_bytes, "ms": dom_ms, "how": "whole stage, CUDA events"}
     tr = TRAFFIC.get(dom)
     traffic = None
     if tr and tr.get("sha") == _sha(tr["source"]):
@@ -308,11 +323,15 @@ def run_ours(args):
             "k3_pagerank": {"ms": med(k3), "edges_per_s": iters * M / (med(k3) * 1e-3), "gbs": b3 / med(k3) / 1e6},
             "k3_pagerank_fp64": {"ms": k3_64, "edges_per_s": iters * M / (k3_64 * 1e-3),
                                  "gbs": k3_bytes_per_iter(nnz, N, "fp64") * iters / k3_64 / 1e6},
+            "k3_pagerank_bf16": {"ms": k3_bf, "edges_per_s": iters * M / (k3_bf * 1e-3),
+                                 "gbs": k3_bytes_per_iter(nnz, N, "bf16") * iters / k3_bf / 1e6},
+            "k3_iteration": {"ms": iter_ms, "setup_ms": k3_setup},
         },
-        "accuracy": {"fp32_vs_gpu_fp64_l1": l1_fp32, "fp32_vs_gpu_fp64_max_rel": maxrel_fp32},
+        "accuracy": {"fp32_vs_gpu_fp64_l1": l1_fp32, "fp32_vs_gpu_fp64_max_rel": maxrel_fp32,
+                     "bf16_vs_gpu_fp64_l1": l1_bf, "bf16_vs_gpu_fp64_max_rel": maxrel_bf},
         "roofline": {"bound": "hbm", "kernel": kname, "stage": dom, "launches_per_step": launches_per_stage,
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic,
+                     "frac": achieved / peak, "traffic": traffic, "per_launch": per_launch,
                      "algorithmic_bytes_per_step": dom_bytes},
         "e2e": {"value": world * M / (e2e_ms * 1e-3), "unit": "edges/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": 8 * M + 8 * N, "d2h_bytes_per_step": 4 * N + 8 * pp.INFO_LEN},
@@ -399,7 +418,19 @@ def run_batched(dev, steps=3, warmup=1, nrhs=32, n_graphs=64, lo=12, hi=18):
         pp.pagerank_batched(graphs, r0d, nrhs, ITERS, DAMPING, out=out)
     e[1].record()
     torch.cuda.synchronize()
+    ms_stream = e[0].elapsed_time(e[1]) / steps
+    # the stage captured once as a CUDA graph and replayed (the headline batched number)
+    ex = pp.BatchedExec(graphs, r0d, nrhs, ITERS, DAMPING, out=out)
+    for _ in range(warmup):
+        ex.launch()
+    torch.cuda.synchronize()
+    e[0].record()
+    for _ in range(steps):
+        ex.launch()
+    e[1].record()
+    torch.cuda.synchronize()
     ms_b = e[0].elapsed_time(e[1]) / steps
+    ex.close()
     # the same 2048 runs one after another, binary64, single-vector path
     row = np.cumsum([0] + [1 << s for s in scales])
     cols = [[r0d[row[g]:row[g + 1], j].contiguous() for j in range(nrhs)] for g in range(n_graphs)]
@@ -420,7 +451,8 @@ def run_batched(dev, steps=3, warmup=1, nrhs=32, n_graphs=64, lo=12, hi=18):
     nz = ref != 0
     edges = int(sum(gr.M for gr in graphs))
     return {"graphs": n_graphs, "scales": "%d..%d" % (lo, hi), "start_vectors": nrhs, "edges": edges,
-            "ms": ms_b, "edges_per_s": ITERS * edges * nrhs / (ms_b * 1e-3),
+            "ms": ms_b, "launch": "one CUDA graph replay per stage", "ms_stream_launches": ms_stream,
+            "edges_per_s": ITERS * edges * nrhs / (ms_b * 1e-3),
             "sequential_fp64_ms": ms_s, "sequential_fp64_edges_per_s": ITERS * edges * nrhs / (ms_s * 1e-3),
             "speedup_vs_sequential_fp64": ms_s / ms_b, "max_l1_err_vs_fp64": l1,
             "max_rel_err_vs_fp64": float((d[nz] / ref[nz].abs()).max()),

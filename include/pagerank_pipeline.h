@@ -147,6 +147,20 @@ pp_status pp_sort_edges_static(const uint32_t *u, const uint32_t *v, uint64_t M,
                                uint32_t *u_out, uint32_t *v_out, void *stream);
 
 /*
+ * Self-test of the bounded cross-block wait (no counterpart in the paper;
+ * failure detection).  Runs one Kernel 1 scatter pass over a built-in
+ * two-tile input whose first tile is never processed, so the second tile's
+ * look-back polls a status word that nothing writes.  After `spin_limit`
+ * empty polls (each followed by a short sleep once the count passes 64) the
+ * wait gives up, PP_DEV_TIMEOUT is recorded in the device error word (read it
+ * with pp_last_device_error) and the kernel returns; the context stays usable.
+ * With ws == NULL the call only stores the workspace size in *bytes_needed.
+ * spin_limit == 0 gives PP_ERR_INVALID_ARG.
+ */
+pp_status pp_selftest_lookback_timeout(uint32_t spin_limit, void *workspace, size_t workspace_bytes,
+                                       size_t *bytes_needed, void *stream);
+
+/*
  * Kernel 2 (Sec. IV-C), from Kernel 1's output (u_sorted, v_sorted; M edges
  * sorted by (u, v)):
  *   step 1  A = sparse(u,v,1,N,N)           duplicate edges become counts
@@ -198,6 +212,26 @@ pp_status pp_pagerank_batched_workspace(const pp_graph *gs, uint32_t n_graphs, u
 pp_status pp_pagerank_batched(const pp_graph *gs, uint32_t n_graphs, const double *r0, uint32_t nrhs,
                               uint32_t iters, double c, float *r_out, void *workspace, size_t workspace_bytes,
                               void *stream);
+
+/*
+ * The same batched Kernel 3 captured once as a CUDA graph and replayed.
+ * pp_pagerank_batched_capture records the kernels that pp_pagerank_batched
+ * would enqueue with these exact arguments (stream capture on `stream`, or
+ * on a private stream when stream is NULL) and instantiates them; nothing
+ * runs.  pp_exec_launch replays the whole stage on `stream` with one call:
+ * it reads r0 and the graphs and writes r_out at launch time, so the caller
+ * may refill r0 (and rebuild the graphs in the same buffers) between
+ * launches.  The buffers, the workspace and the graphs' arrays must stay
+ * allocated until pp_exec_destroy; two launches of one exec must not
+ * overlap.  Argument errors are those of pp_pagerank_batched and leave
+ * *exec NULL.
+ */
+typedef struct pp_exec pp_exec;
+pp_status pp_pagerank_batched_capture(const pp_graph *gs, uint32_t n_graphs, const double *r0, uint32_t nrhs,
+                                      uint32_t iters, double c, float *r_out, void *workspace,
+                                      size_t workspace_bytes, void *stream, pp_exec **exec);
+pp_status pp_exec_launch(pp_exec *exec, void *stream);
+pp_status pp_exec_destroy(pp_exec *exec);
 
 /*
  * Kernels 1-3 back to back from HOST buffers: copies u_host, v_host (M ids

@@ -68,6 +68,11 @@ def _lib():
             "pp_last_device_error": [vp, ctypes.POINTER(ctypes.c_uint32)],
             "pp_pagerank_batched_workspace": [ctypes.POINTER(CGraph), u32, u32, u32, sz],
             "pp_pagerank_batched": [ctypes.POINTER(CGraph), u32, vp, u32, u32, dbl, vp, vp, ctypes.c_size_t, vp],
+            "pp_selftest_lookback_timeout": [u32, vp, ctypes.c_size_t, sz, vp],
+            "pp_pagerank_batched_capture": [ctypes.POINTER(CGraph), u32, vp, u32, u32, dbl, vp, vp, ctypes.c_size_t,
+                                            vp, ctypes.POINTER(vp)],
+            "pp_exec_launch": [vp, vp],
+            "pp_exec_destroy": [vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -131,6 +136,18 @@ def last_device_error(stream=None):
     if st not in (PP_OK, PP_ERR_DEVICE):
         raise PPError("pp_last_device_error", st)
     return int(code.value)
+
+
+def selftest_lookback_timeout(spin_limit, device=None, stream=None):
+    """Run the bounded-wait self-test; returns the device error bits it left."""
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    need = ctypes.c_size_t(0)
+    _check("pp_selftest_lookback_timeout",
+           _lib().pp_selftest_lookback_timeout(spin_limit, None, 0, ctypes.byref(need), None))
+    ws = torch.empty(need.value, dtype=torch.uint8, device=dev)
+    _check("pp_selftest_lookback_timeout",
+           _lib().pp_selftest_lookback_timeout(spin_limit, _ptr(ws), ws.numel(), None, _stream(stream, dev)))
+    return last_device_error(stream)
 
 
 def graph_lengths(M, scale):
@@ -245,6 +262,49 @@ def pagerank_batched(graphs, r0, nrhs, iters=20, c=0.85, out=None, workspace=Non
                                     _stream(stream, dev))
     _check("pp_pagerank_batched", st)
     return out
+
+
+class BatchedExec:
+    """Batched Kernel 3 captured as one CUDA graph (pp_pagerank_batched_capture).
+
+    launch() replays the stage; it reads r0 and writes out as they are at
+    launch time.  Keeps references to every buffer it was captured with."""
+
+    def __init__(self, graphs, r0, nrhs, iters=20, c=0.85, out=None, workspace=None, stream=None):
+        n = len(graphs)
+        self._arr = (CGraph * n)(*[g.c for g in graphs])
+        rows = sum(g.N for g in graphs)
+        assert r0.shape == (rows, nrhs) and r0.dtype == torch.float64 and r0.is_contiguous()
+        dev = r0.device
+        self.out = out if out is not None else torch.empty(rows, nrhs, dtype=torch.float32, device=dev)
+        need = ctypes.c_size_t(0)
+        _check("pp_pagerank_batched_workspace",
+               _lib().pp_pagerank_batched_workspace(self._arr, n, nrhs, iters, ctypes.byref(need)))
+        self.ws = workspace if workspace is not None and workspace.numel() >= need.value else _workspace(need.value,
+                                                                                                      dev)
+        self._keep = (list(graphs), r0)
+        self._dev = dev
+        h = ctypes.c_void_p(None)
+        _check("pp_pagerank_batched_capture",
+               _lib().pp_pagerank_batched_capture(self._arr, n, _ptr(r0), nrhs, iters, c, _ptr(self.out),
+                                                  _ptr(self.ws), self.ws.numel(), _stream(stream, dev),
+                                                  ctypes.byref(h)))
+        self._h = h
+
+    def launch(self, stream=None):
+        _check("pp_exec_launch", _lib().pp_exec_launch(self._h, _stream(stream, self._dev)))
+        return self.out
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _lib().pp_exec_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def pipeline_host(u, v, scale, r0, iters=20, c=0.85, dtype="fp32", rule="lowest", out=None, info=None,

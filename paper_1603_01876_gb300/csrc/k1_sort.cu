@@ -188,3 +188,61 @@ extern "C" pp_status pp_sort_edges_static(const uint32_t *u, const uint32_t *v, 
         k1::run<uint64_t>(u, v, M, scale, u_out, v_out, L, s);
     return launch_status();
 }
+
+// ---------------------------------------------------------------------------
+// Self-test of the bounded look-back wait (no counterpart in the paper).  A
+// two-tile scatter pass starts with its tile counter at 1, so tile 0 is never
+// processed and tile 1 waits for a status word that nothing writes.  After
+// spin_limit empty polls the wait gives up, PP_DEV_TIMEOUT lands in the
+// device error word, and the kernel finishes (its output is meaningless).
+
+namespace {
+__global__ void k1_set_u32(uint32_t *p, uint32_t v) { *p = v; }
+constexpr uint64_t kSelftestEdges = 2 * os::TILE;
+constexpr uint32_t kSelftestScale = 8;
+
+struct SelftestLayout {
+    uint32_t *u, *v;
+    k1::Layout k1;
+    size_t bytes;
+};
+
+SelftestLayout selftest_layout(void *ws) {
+    Carver c(ws);
+    SelftestLayout L;
+    L.u = c.take<uint32_t>(kSelftestEdges);
+    L.v = c.take<uint32_t>(kSelftestEdges);
+    const size_t head = c.size();
+    L.k1 = k1::layout(ws ? static_cast<char *>(ws) + head : nullptr, kSelftestEdges, kSelftestScale);
+    L.bytes = head + L.k1.bytes;
+    return L;
+}
+}  // namespace
+
+extern "C" pp_status pp_selftest_lookback_timeout(uint32_t spin_limit, void *ws, size_t ws_bytes,
+                                                  size_t *bytes_needed, void *stream) {
+    const size_t need = selftest_layout(nullptr).bytes;
+    if (bytes_needed) *bytes_needed = need;
+    if (!ws) return bytes_needed ? PP_OK : PP_ERR_INVALID_ARG;
+    if (spin_limit == 0) return PP_ERR_INVALID_ARG;
+    pp_status st = check_ws(ws, ws_bytes, need);
+    if (st != PP_OK) return st;
+    const SelftestLayout L = selftest_layout(ws);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const uint64_t M = kSelftestEdges;
+    const uint32_t scale = kSelftestScale;
+    const int P = k1::num_passes(scale);
+    const size_t word = L.k1.sort.wide ? 8 : 4;
+    cudaMemsetAsync(L.u, 0, M * sizeof(uint32_t), s);
+    cudaMemsetAsync(L.v, 0, M * sizeof(uint32_t), s);
+    cudaMemsetAsync(L.k1.sort.hist, 0, os::kCtlBytes, s);
+    os::hist_kernel<uint32_t, k1::PackSrc<uint32_t, true>><<<2, 256, 0, s>>>(
+        k1::PackSrc<uint32_t, true>{L.u, L.v, scale}, nullptr, M, P, L.k1.sort.hist,
+        static_cast<uint32_t *>(L.k1.sort.status[0]), ceil_div(M, os::TILE) * os::RADIX * word / 4);
+    k1_set_u32<<<1, 1, 0, s>>>(L.k1.sort.tile_ctr, 1u);
+    count_launch(2);
+    os::launch_pass<uint32_t, false>(L.k1.sort, 0, P, k1::PackSrc<uint32_t, false>{L.u, L.v, scale},
+                                     k1::KeyDst<uint32_t>{static_cast<uint32_t *>(L.k1.keys[0])}, nullptr, M, s, 0,
+                                     spin_limit);
+    return launch_status();
+}

@@ -58,6 +58,7 @@ struct PassCtl {
     uint32_t *tile_ctr;     // zero on entry
     const uint64_t *n_dev;  // element count on the device (nullptr: use n_host)
     uint64_t n_host;
+    uint32_t spin_limit;    // empty polls before a look-back gives up
 };
 
 // Status words are 32-bit while every count fits in 30 bits.
@@ -156,7 +157,7 @@ __global__ void __launch_bounds__(THREADS, 3) pass_kernel(Src src, Dst dst, Pass
             if (done) break;
             p -= used;  // tile 0 always publishes an inclusive word, so p stays >= 0
             if (used == 0) {
-                if (++spins > kSpinLimit) {
+                if (++spins > ctl.spin_limit) {
                     pp_set_error(PP_DEV_TIMEOUT);
                     break;
                 }
@@ -248,7 +249,8 @@ inline bool prefer_shared(K kernel) {
 // Launches pass `p` (of npasses) of a sort prepared in `w`.
 template <typename KeyT, bool HAS_VAL, class Src, class Dst>
 inline void launch_pass(const SortWs &w, int p, int npasses, Src src, Dst dst, const uint64_t *n_dev,
-                        uint64_t n_max, cudaStream_t s, uint32_t shift0 = 0) {
+                        uint64_t n_max, cudaStream_t s, uint32_t shift0 = 0,
+                        uint32_t spin_limit = kSpinLimit) {
     PassCtl ctl;
     ctl.shift = shift0 + 8u * (uint32_t)p;
     ctl.hist = w.hist + p * RADIX;
@@ -257,6 +259,7 @@ inline void launch_pass(const SortWs &w, int p, int npasses, Src src, Dst dst, c
     ctl.tile_ctr = w.tile_ctr + p;
     ctl.n_dev = n_dev;
     ctl.n_host = n_max;
+    ctl.spin_limit = spin_limit;
     const unsigned grid = (unsigned)ceil_div(n_max ? n_max : 1, TILE);
     if (w.wide) {
         static const bool once = prefer_shared(pass_kernel<KeyT, uint64_t, HAS_VAL, Src, Dst>);

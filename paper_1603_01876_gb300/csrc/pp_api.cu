@@ -172,3 +172,57 @@ extern "C" pp_status pp_pipeline_host(const uint32_t *u_host, const uint32_t *v_
         return PP_ERR_CUDA;
     return PP_OK;
 }
+
+// ---------------------------------------------------------------------------
+// CUDA-graph capture of the batched Kernel 3 stage.
+
+struct pp_exec {
+    cudaGraphExec_t exec;
+    uint64_t kernels;  // kernels in the graph, for pp_launch_count
+};
+
+extern "C" pp_status pp_pagerank_batched_capture(const pp_graph *gs, uint32_t n_graphs, const double *r0,
+                                                 uint32_t nrhs, uint32_t iters, double c, float *r_out, void *ws,
+                                                 size_t ws_bytes, void *stream, pp_exec **exec) {
+    if (!exec) return PP_ERR_INVALID_ARG;
+    *exec = nullptr;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool own = s == nullptr;  // the legacy default stream cannot be captured
+    if (own && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return PP_ERR_CUDA;
+    pp_status st = PP_ERR_CUDA;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+        const uint64_t before = g_launches.load();
+        st = pp_pagerank_batched(gs, n_graphs, r0, nrhs, iters, c, r_out, ws, ws_bytes, s);
+        const uint64_t kernels = g_launches.load() - before;
+        g_launches.fetch_sub(kernels);  // recorded, not launched
+        const cudaError_t e = cudaStreamEndCapture(s, &graph);
+        if (st == PP_OK && (e != cudaSuccess || !graph)) st = PP_ERR_CUDA;
+        if (st == PP_OK) {
+            cudaGraphExec_t ge = nullptr;
+            if (cudaGraphInstantiate(&ge, graph, 0) == cudaSuccess) {
+                *exec = new pp_exec{ge, kernels};
+            } else {
+                st = PP_ERR_CUDA;
+            }
+        }
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (st != PP_OK) cudaGetLastError();
+    if (own) cudaStreamDestroy(s);
+    return st;
+}
+
+extern "C" pp_status pp_exec_launch(pp_exec *exec, void *stream) {
+    if (!exec) return PP_ERR_INVALID_ARG;
+    if (cudaGraphLaunch(exec->exec, static_cast<cudaStream_t>(stream)) != cudaSuccess) return PP_ERR_CUDA;
+    count_launch(exec->kernels);
+    return PP_OK;
+}
+
+extern "C" pp_status pp_exec_destroy(pp_exec *exec) {
+    if (!exec) return PP_OK;
+    const cudaError_t e = cudaGraphExecDestroy(exec->exec);
+    delete exec;
+    return e == cudaSuccess ? PP_OK : PP_ERR_CUDA;
+}

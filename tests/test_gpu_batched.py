@@ -110,3 +110,44 @@ def test_batched_64_graphs_scales_12_to_18(pp, k0, oracle_mod):
             assert e["l1"] <= 1e-6 and e["max_rel"] <= 1e-4, (g, j, e)
     small = int(np.argmin(scales))
     check_against_oracle(oracle_mod, gotn, scales, edges, r0, [(small, 0), (small, 31)])
+
+
+def test_batched_cuda_graph_replay(pp, k0):
+    """The captured stage gives the direct call's result bit for bit, and a
+    replay after refilling r0 in place gives the direct call's result for the
+    new start vectors."""
+    import torch
+
+    scales = [9, 12, 10]
+    graphs, _ = build_batch(pp, k0, scales, 23)
+    r0d = torch.from_numpy(start_vectors(k0, scales, 32, 4)).cuda()
+    direct = pp.pagerank_batched(graphs, r0d, 32)
+    before = pp.launch_count()
+    ex = pp.BatchedExec(graphs, r0d, 32)
+    assert pp.launch_count() == before, "capture must not count as launches"
+    got = ex.launch().clone()
+    torch.cuda.synchronize()
+    assert pp.launch_count() > before
+    assert torch.equal(got, direct)
+    r0d.copy_(torch.from_numpy(start_vectors(k0, scales, 32, 8)))
+    direct2 = pp.pagerank_batched(graphs, r0d, 32)
+    got2 = ex.launch().clone()
+    torch.cuda.synchronize()
+    assert pp.last_device_error() == 0
+    assert torch.equal(got2, direct2)
+    assert not torch.equal(got2, got)
+    ex.close()
+
+
+def test_batched_capture_argument_error(pp, k0):
+    import torch
+
+    scales = [8]
+    graphs, _ = build_batch(pp, k0, scales, 2)
+    r0d = torch.from_numpy(start_vectors(k0, scales, 4, 1)).cuda()
+    with pytest.raises(pp.PPError):
+        pp.BatchedExec(graphs, r0d, 4, iters=20, c=1.5)
+    # the failed capture leaves the stream usable
+    out = pp.pagerank_batched(graphs, r0d, 4)
+    torch.cuda.synchronize()
+    assert torch.isfinite(out).all()

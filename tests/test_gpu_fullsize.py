@@ -1,0 +1,190 @@
+"""Parity at full size, in the configuration the benchmark times.
+
+The oracle cannot rerun a 2^28-edge pipeline within a test, so the checks at
+scale 24 (and 26, when PP_FULLSIZE_26=1) are the definitions evaluated
+directly on the host and properties that hold at any size:
+
+- Kernel 1: the output is ordered by (u, v) and is a permutation of the input
+  (compared with a library sort of the same keys).
+- Kernel 2: d_in = sum(A,1) and d_out = sum(A,2) after the filter, the column
+  pointers, nnz0, nnz, max(d_in), its lowest column and the tie count, all
+  from bincounts of Kernel 1's output, bit for bit; 1/d_out bit for bit; rows
+  strictly ascending inside each column; the (u, v, count) entry set through
+  two independent 64-bit hashes of every entry.
+- Kernel 3: one binary64 step from the GPU's r after 19 iterations to its r
+  after 20, recomputed in binary64 for sampled columns (Eq. 1 with the
+  teleport term), the mass balance of that step, and the binary32 ranks
+  against the binary64 ranks within the stated tolerances.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from gpu_helpers import host_u32, rank_errors
+
+pytestmark = pytest.mark.gpu
+
+SEED = 1
+C = 0.85
+ITERS = 20
+
+
+def _mix(x, k1, k2):
+    """A 64-bit mixing function (the splitmix64 finaliser, two constants)."""
+    with np.errstate(over="ignore"):
+        x = x.astype(np.uint64)
+        x ^= x >> np.uint64(30)
+        x *= np.uint64(k1)
+        x ^= x >> np.uint64(27)
+        x *= np.uint64(k2)
+        x ^= x >> np.uint64(31)
+    return x
+
+
+def _hashes(u, v, cnt, scale):
+    key = (u.astype(np.uint64) << np.uint64(scale)) | v.astype(np.uint64)
+    h1 = _mix(key, 0xBF58476D1CE4E5B9, 0x94D049BB133111EB)
+    h2 = _mix(key ^ np.uint64(0x9E3779B97F4A7C15), 0xFF51AFD7ED558CCD, 0xC4CEB9FE1A85EC53)
+    with np.errstate(over="ignore"):
+        return (int(h1.sum(dtype=np.uint64)), int(h2.sum(dtype=np.uint64)),
+                int((h1 * cnt.astype(np.uint64)).sum(dtype=np.uint64)))
+
+
+@pytest.fixture(scope="module", params=[24, 26])
+def fullsize(request):
+    import torch
+
+    import kernel0
+    import paper_1603_01876_gb300 as pp
+
+    scale = request.param
+    if scale == 26 and os.environ.get("PP_FULLSIZE_26") != "1":
+        pytest.skip("scale 26 runs with PP_FULLSIZE_26=1 (about 40 GB of host memory)")
+    N, M = 1 << scale, 16 << scale
+    dev = torch.device("cuda", 0)
+    u, v = kernel0.edges_device(scale, SEED, device=dev)
+    r0 = torch.from_numpy(kernel0.r0_host(N, SEED)).to(dev)
+    ws = torch.empty(max(pp.workspace_bytes("sort", M, scale), pp.workspace_bytes("build", M, scale),
+                         pp.workspace_bytes("pagerank", M, scale, ITERS, "fp64")), dtype=torch.uint8, device=dev)
+    us, vs = torch.empty_like(u), torch.empty_like(v)
+    pp.sort_edges(u, v, scale, out=(us, vs), workspace=ws)
+    g = pp.Graph(M, scale, dev)
+    pp.build_filter_normalize(us, vs, scale, "lowest", graph=g, workspace=ws)
+    torch.cuda.synchronize()
+    assert pp.last_device_error() == 0
+    return dict(pp=pp, scale=scale, N=N, M=M, u=u, v=v, us=us, vs=vs, g=g, r0=r0, ws=ws)
+
+
+def test_k1_ordered_permutation(fullsize):
+    import torch
+
+    f = fullsize
+    S = f["scale"]
+    key_out = (f["us"].long() << S) | f["vs"].long()
+    assert bool((key_out[1:] >= key_out[:-1]).all()), "Kernel 1 output not ordered by (u, v)"
+    key_in = (f["u"].long() << S) | f["v"].long()
+    assert torch.equal(torch.sort(key_in).values, key_out), "Kernel 1 output is not a permutation of its input"
+
+
+def test_k2_structure_bit_exact(fullsize):
+    f = fullsize
+    S, N, M, g = f["scale"], f["N"], f["M"], f["g"]
+    us, vs = host_u32(f["us"]), host_u32(f["vs"])
+    info = g.info_dict()
+
+    # step 1: runs of equal (u, v) are the entries, their lengths the counts
+    key = (us.astype(np.uint64) << np.uint64(S)) | vs.astype(np.uint64)
+    first = np.ones(M, dtype=bool)
+    first[1:] = key[1:] != key[:-1]
+    assert info["nnz0"] == int(first.sum())
+    # step 2: d_in = sum(A,1), the sum of counts
+    d_in = np.bincount(vs, minlength=N)
+    np.testing.assert_array_equal(host_u32(g.d_in)[:N], d_in.astype(np.uint32))
+    # step 3: the supernode (lowest index on ties) and the leaves
+    dmax = int(d_in.max())
+    vmax = int(np.argmax(d_in))
+    assert (info["dmax"], info["vmax"], info["ties"]) == (dmax, vmax, int((d_in == dmax).sum()))
+    keep = d_in != 1
+    keep[vmax] = False
+    kept_edge = keep[vs]
+    kept_entry = first & kept_edge
+    assert info["nnz"] == int(kept_entry.sum())
+    # step 4: d_out = sum(A,2) after the filter, 1/d_out in both precisions
+    d_out = np.bincount(us[kept_edge], minlength=N)
+    np.testing.assert_array_equal(host_u32(g.d_out)[:N], d_out.astype(np.uint32))
+    with np.errstate(divide="ignore"):
+        inv32 = np.where(d_out > 0, np.float32(1) / d_out.astype(np.float32), np.float32(0))
+        inv64 = np.where(d_out > 0, 1.0 / d_out.astype(np.float64), 0.0)
+    np.testing.assert_array_equal(g.inv_dout32.cpu().numpy()[:N].view(np.uint32), inv32.view(np.uint32))
+    np.testing.assert_array_equal(g.inv_dout64.cpu().numpy()[:N].view(np.uint64), inv64.view(np.uint64))
+    colptr = np.concatenate([[0], np.cumsum(np.bincount(vs[kept_entry], minlength=N))])
+    np.testing.assert_array_equal(host_u32(g.colptr)[:N + 1].astype(np.int64), colptr)
+
+    # the entry set, through hashes of (u, v) and of (u, v) weighted by the count
+    starts = np.flatnonzero(first)
+    runs = np.diff(np.append(starts, M))
+    sel = keep[vs[starts]]
+    want = _hashes(us[starts][sel], vs[starts][sel], runs[sel], S)
+    del key, first, kept_edge, kept_entry, starts, runs, sel
+    gu, gv, gc, colptr_dev = _decode_csc(g)
+    same_col = gv[1:] == gv[:-1]
+    assert bool((gu[1:][same_col] > gu[:-1][same_col]).all()), "rows not strictly ascending in a column"
+    assert _hashes(gu, gv, gc, S) == want
+
+
+def _decode_csc(g):
+    """(u, v, count) of every kept entry in column order (test-side decode)."""
+    info = g.info_dict()
+    nnz, novf = info["nnz"], info["novf"]
+    colptr = host_u32(g.colptr)[: g.N + 1].astype(np.int64)
+    rowc = host_u32(g.rowc)[:nnz]
+    u = rowc & np.uint32(g.N - 1)
+    cf = (rowc >> np.uint32(g.scale)).astype(np.uint32)
+    v = np.repeat(np.arange(g.N, dtype=np.uint32), np.diff(colptr))
+    esc = cf == np.uint32((1 << (32 - g.scale)) - 1)
+    if esc.any():
+        ovk = g.ovf_key.cpu().numpy().view(np.uint64)[:novf]
+        ovc = host_u32(g.ovf_cnt)[:novf]
+        k = (u[esc].astype(np.uint64) << np.uint64(32)) | v[esc].astype(np.uint64)
+        i = np.searchsorted(ovk, k)
+        assert (i < novf).all() and (ovk[i] == k).all()
+        cf[esc] = ovc[i]
+    return u, v, cf, colptr
+
+
+def test_k3_one_step_and_precisions(fullsize):
+    import torch
+
+    f = fullsize
+    pp, g, N, r0, ws = f["pp"], f["g"], f["N"], f["r0"], f["ws"]
+    r19 = pp.pagerank(g, r0, ITERS - 1, C, "fp64", workspace=ws).cpu().numpy()
+    r20 = pp.pagerank(g, r0, ITERS, C, "fp64", workspace=ws).cpu().numpy()
+    r32 = pp.pagerank(g, r0, ITERS, C, "fp32", workspace=ws).cpu().numpy()
+    torch.cuda.synchronize()
+    assert pp.last_device_error() == 0
+
+    colptr = host_u32(g.colptr)[:N + 1].astype(np.int64)
+    d_out = host_u32(g.d_out)[:N]
+    inv64 = g.inv_dout64.cpu().numpy()[:N]
+    S19 = float(np.sum(r19))
+    # mass balance of one step: sum(r') = c * sum_{d_out(u)>0} r(u) + (1-c) * sum(r)
+    want_mass = C * float(np.sum(r19[d_out > 0])) + (1 - C) * S19
+    assert abs(float(np.sum(r20)) - want_mass) <= 1e-12 * want_mass
+
+    # Eq. 1 for sampled columns: the heaviest kept column, removed columns, random ones
+    u, v, cnt, _ = _decode_csc(g)
+    rng = np.random.default_rng(7)
+    deg = np.diff(colptr)
+    cols = np.unique(np.concatenate([[int(np.argmax(deg))], np.flatnonzero(deg == 0)[:50],
+                                     rng.integers(0, N, 4000)]))
+    x = r19 * inv64
+    tele = (1 - C) / N * S19
+    for col in cols:
+        a, b = colptr[col], colptr[col + 1]
+        y = float(np.dot(cnt[a:b].astype(np.float64), x[u[a:b]]))
+        want = C * y + tele
+        assert abs(r20[col] - want) <= 1e-12 * want, (int(col), r20[col], want)
+
+    e = rank_errors(r32, r20)
+    assert e["l1"] <= 1e-6 and e["max_rel"] <= 1e-4, e
