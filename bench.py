@@ -39,7 +39,12 @@ WORKLOAD = ("Kronecker graph, scale 24 (N=2^24, M=16N=268,435,456 edges, initiat
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from an ncu capture
 # (profiles/), valid only while the kernel's source file is unchanged.
-TRAFFIC = {}
+# DRAM bytes (read + write) per launch of each stage's dominant kernel from
+# one ncu capture (profiles/), valid while its source file is unchanged.
+TRAFFIC = {
+    "k3_pagerank": {"source": "paper_1603_01876_gb300/csrc/k3_pagerank.cu", "sha": "98a5c0cae0944030", "bytes_per_launch": 2064349000 + 79102720,
+                    "dtype": "fp32", "scale": 24, "capture": "profiles/k3_iterate_fp32_scale24.md"},
+}
 
 
 def _sha(path):
@@ -297,7 +302,7 @@ def run_ours(args):
         per_launch = {"bytes": dom_bytes, "ms": dom_ms, "how": "whole stage, CUDA events"}
     tr = TRAFFIC.get(dom)
     traffic = None
-    if tr and tr.get("sha") == _sha(tr["source"]):
+    if tr and tr.get("sha") == _sha(tr["source"]) and (tr.get("dtype"), tr.get("scale")) == (args.dtype, scale):
         traffic = tr["bytes_per_launch"]
 
     out = {
