@@ -117,13 +117,15 @@ struct UniqueArgs {
 };
 
 // Persistent: each block claims tiles in order until none is left.
-__global__ void __launch_bounds__(UQ_THREADS) unique_kernel(UniqueArgs a) {
+__global__ void __launch_bounds__(UQ_THREADS, 3) unique_kernel(UniqueArgs a) {
     __shared__ uint32_t s_tile;
     __shared__ uint64_t s_scan[40];
     __shared__ long long s_max[UQ_THREADS / 32];
     __shared__ uint64_t s_excl;
     __shared__ uint32_t s_hist[os::MAX_PASSES][os::RADIX];
-    __shared__ unsigned long long s_out[UQ_TILE];  // the tile's entries, written out coalesced
+    // the tile's entries, written out coalesced; one pad word per 16 so that
+    // the threads' consecutive runs of stores hit different banks
+    __shared__ unsigned long long s_out[UQ_TILE + UQ_TILE / 16];
     const int tid = threadIdx.x;
     for (int i = tid; i < os::MAX_PASSES * os::RADIX; i += UQ_THREADS) (&s_hist[0][0])[i] = 0;
     const uint64_t ntiles = uq_tiles(a.M);
@@ -202,18 +204,17 @@ __global__ void __launch_bounds__(UQ_THREADS) unique_kernel(UniqueArgs a) {
             }
         }
 
-        uint32_t cnt[UQ_ITEMS];
+        const uint64_t start0 = start;
         uint32_t nt = 0, ne = 0;
 #pragma unroll
         for (int j = 0; j < UQ_ITEMS; ++j) {
-            cnt[j] = 0;
             if (tails >> j & 1u) {
-                cnt[j] = (uint32_t)(my0 + j - start + 1);
+                ne += (uint32_t)(my0 + j - start + 1) >= a.cmax;
                 start = my0 + j + 1;
                 ++nt;
-                ne += cnt[j] >= a.cmax;
             }
         }
+        start = start0;
 
         // bits 61:32 count overflow entries, bits 31:0 entries
         uint64_t total;
@@ -240,9 +241,10 @@ __global__ void __launch_bounds__(UQ_THREADS) unique_kernel(UniqueArgs a) {
                 u &= umask;
                 v &= umask;
             }
-            const uint32_t c = cnt[j];
+            const uint32_t c = (uint32_t)(my0 + j - start + 1);
+            start = my0 + j + 1;
             const uint32_t field = c >= a.cmax ? a.cmax : c;
-            s_out[lpos] = ((unsigned long long)v << 32) | (u | (field << a.scale));
+            s_out[lpos + lpos / 16] = ((unsigned long long)v << 32) | (u | (field << a.scale));
             if (c >= a.cmax) {
                 a.ovf_key[epos] = ((uint64_t)u << 32) | v;
                 a.ovf_cnt[epos] = c;
@@ -263,7 +265,7 @@ __global__ void __launch_bounds__(UQ_THREADS) unique_kernel(UniqueArgs a) {
         {
             unsigned long long *dst = a.ent + (s_excl & 0xffffffffull);
             const uint32_t n_out = (uint32_t)total;
-            for (uint32_t i = tid; i < n_out; i += UQ_THREADS) dst[i] = s_out[i];
+            for (uint32_t i = tid; i < n_out; i += UQ_THREADS) dst[i] = s_out[i + i / 16];
         }
         __syncthreads();  // shared scratch is reused by the next tile
     }
