@@ -321,7 +321,8 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "scale": scale, "vertices": N, "edges": M, "iters": iters,
                    "rank_dtype": args.dtype, "supernode_rule": "lowest", "nnz0": nnz0, "nnz": nnz,
                    "l2": "inputs larger than L2 (2 GiB edge list; 126 MB L2), no flush",
-                   "parallelism": "independent graph per GPU" if world > 1 else "single GPU"},
+                   "parallelism": "independent graph per GPU" if world > 1 else "single GPU",
+                   "tuning": dict(args.tuned, **{kv.split("=")[0]: int(kv.split("=")[1]) for kv in args.tune})},
         "kernels": {
             "k1_sort": {"ms": med(k1), "edges_per_s": M / (med(k1) * 1e-3), "gbs": b1 / med(k1) / 1e6},
             "k2_filter": {"ms": med(k2), "edges_per_s": M / (med(k2) * 1e-3), "gbs": b2 / med(k2) / 1e6},
@@ -389,7 +390,7 @@ def run_k3_only(args):
     torch.cuda.synchronize()
     ms = e[0].elapsed_time(e[1]) / args.steps
     b = k3_bytes_per_iter(info["nnz"], N, args.dtype) * iters
-    print(json.dumps({"stage": "k3", "scale": scale, "dtype": args.dtype, "tune": args.tune, "ms": ms, "nnz": info["nnz"],
+    print(json.dumps({"stage": "k3", "scale": scale, "dtype": args.dtype, "tune": args.tune, "tuned": args.tuned, "ms": ms, "nnz": info["nnz"],
                       "edges_per_s": iters * M / (ms * 1e-3), "gbs": b / ms / 1e6,
                       "device_error": pp.last_device_error()}))
 
@@ -546,7 +547,14 @@ def main():
                     help="set a library tuning knob before running (repeatable)")
     ap.add_argument("--stage", choices=["all", "k3", "batched"], default="all",
                     help="k3: time Kernel 3 alone (profiling aid); the default times the whole pipeline")
+    ap.add_argument("--tuning", default="default",
+                    help="autotuner result to apply (JSON from paper_1603_01876_gb300.tune; 'none' to skip)")
     args = ap.parse_args()
+    args.tuned = {}
+    if args.impl == "ours" and args.tuning != "none":
+        from paper_1603_01876_gb300 import tune
+
+        args.tuned = tune.apply(tune.DEFAULT_PATH if args.tuning == "default" else args.tuning)
     if args.tune:
         import paper_1603_01876_gb300 as pp
 

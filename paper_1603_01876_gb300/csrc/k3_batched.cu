@@ -10,7 +10,7 @@
 //
 // One persistent launch per iteration covers every graph of the batch.  The
 // columns of all graphs are planned together into warp work items (tiles of
-// up to 32 short columns; chunks of CHUNK entries of long columns), dealt to
+// up to 32 short columns; chunks of `chunk` entries of long columns), dealt to
 // warps round-robin so that the warps work on neighbouring items of the same
 // graph at any moment and that graph's X stays in L2.  Each column is summed
 // in entry order (a long column's chunk sums are added in chunk order by the
@@ -31,9 +31,10 @@ namespace k3b {
 constexpr int THREADS = 256;
 constexpr int WARPS = THREADS / 32;
 constexpr int TILE_COLS = 32;
-constexpr int SHORTMAX = 256;  // columns longer than this are cut into chunks
-constexpr int TILE_ENTRIES = 2 * SHORTMAX;
-constexpr int CHUNK = 512;     // entries of a long column per work item
+constexpr int SHORTMAX_MAX = 256;  // largest long-column threshold (k3b_shortmax)
+constexpr int SHORTMAX_MIN = 128;
+constexpr int TILE_ENTRIES = 2 * SHORTMAX_MAX;
+constexpr int CHUNK_MIN = 256;     // smallest long-column chunk (k3b_chunk)
 constexpr int GATHERS = 8;     // gathers in flight per lane
 constexpr int MAXG = PP_BATCH_MAX_GRAPHS;
 constexpr int NORM_ROWS = 2048;  // rows per block of the start-vector passes
@@ -58,6 +59,8 @@ struct BG {
 struct Desc {
     BG g[MAXG];
     uint32_t ng, nrhs, iters, pad;
+    uint32_t shortmax;  // columns longer than this are cut into chunks (power of two)
+    uint32_t chunk;     // entries of a long column per work item
     uint64_t rows;  // rows of all graphs together
     double c;
 };
@@ -105,8 +108,8 @@ __device__ __forceinline__ uint32_t ovf_lookup(const uint64_t *keys, const uint3
     return (lo < n && __ldg(keys + lo) == key) ? __ldg(cnts + lo) : 0u;
 }
 
-__device__ __forceinline__ uint32_t item_count(uint32_t len) {
-    return len > (uint32_t)SHORTMAX ? (len + CHUNK - 1) / CHUNK : 1u;
+__device__ __forceinline__ uint32_t item_count(const Desc &d, uint32_t len) {
+    return len > d.shortmax ? (len + d.chunk - 1) / d.chunk : 1u;
 }
 
 // ------------------------------------------------------------------ set-up
@@ -186,19 +189,19 @@ __global__ void __launch_bounds__(256) normalize_kernel(const __grid_constant__ 
 }
 
 // Column gc (global numbering) starts a work item if it starts its graph, is
-// long, follows a long column, starts in a new SHORTMAX-entry chunk of its
+// long, follows a long column, starts in a new shortmax-entry span of its
 // graph's entry array, or is a multiple of TILE_COLS within its graph.
 __device__ __forceinline__ void classify(const Desc &d, uint64_t gc, bool &bound, uint32_t &nitems) {
     const int g = graph_of(d, gc);
     const BG &G = d.g[g];
     const uint32_t v = (uint32_t)(gc - G.row0);
     const uint32_t s = __ldg(G.colptr + v), e = __ldg(G.colptr + v + 1);
-    nitems = item_count(e - s);
+    nitems = item_count(d, e - s);
     bound = true;
-    if (v == 0 || e - s > (uint32_t)SHORTMAX || v % TILE_COLS == 0) return;
+    if (v == 0 || e - s > d.shortmax || v % TILE_COLS == 0) return;
     const uint32_t ps = __ldg(G.colptr + v - 1);
-    if (s - ps > (uint32_t)SHORTMAX) return;
-    bound = (s / SHORTMAX) != (ps / SHORTMAX);
+    if (s - ps > d.shortmax) return;
+    bound = (s / d.shortmax) != (ps / d.shortmax);
 }
 
 __global__ void __launch_bounds__(PLAN_THREADS) plan_kernel(const __grid_constant__ Desc d, Ws w) {
@@ -260,7 +263,7 @@ __global__ void __launch_bounds__(PLAN_THREADS) plan_kernel(const __grid_constan
         const int g = graph_of(d, gc);
         const uint32_t v = (uint32_t)(gc - d.g[g].row0);
         if (v == 0) w.first_item[g] = ii;
-        ii += item_count(__ldg(d.g[g].colptr + v + 1) - __ldg(d.g[g].colptr + v));
+        ii += item_count(d, __ldg(d.g[g].colptr + v + 1) - __ldg(d.g[g].colptr + v));
         ++bi;
     }
 }
@@ -273,11 +276,12 @@ __global__ void __launch_bounds__(256) plan_items_kernel(const __grid_constant__
         const BG &G = d.g[g];
         const uint32_t v = (uint32_t)(gc - G.row0), o = w.bound_item[i];
         const uint32_t s = __ldg(G.colptr + v), e = __ldg(G.colptr + v + 1);
-        if (e - s > (uint32_t)SHORTMAX) {
-            const uint32_t nc = (e - s + CHUNK - 1) / CHUNK;
+        if (e - s > d.shortmax) {
+            // graphs here have scale <= 24: a kept column has < 2^27 entries, so nc < 2^20
+            const uint32_t nc = (e - s + d.chunk - 1) / d.chunk;
             for (uint32_t k = 0; k < nc; ++k) {
-                const uint32_t cs = s + k * CHUNK;
-                w.item[o + k] = make_uint4(v | LONG_FLAG, o, cs, min((uint32_t)CHUNK, e - cs) | (nc << 12));
+                const uint32_t cs = s + k * d.chunk;
+                w.item[o + k] = make_uint4(v | LONG_FLAG, o, cs, min(d.chunk, e - cs) | (nc << 12));
                 w.item_g[o + k] = (uint8_t)g;
                 w.ticket[o + k] = 0;
             }
@@ -467,8 +471,8 @@ inline bool batch_sizes(const pp_graph *gs, uint32_t ng, uint64_t &rows, uint64_
 
 inline uint64_t max_items(uint32_t ng, uint64_t rows, uint64_t edges) {
     // boundaries: graph starts, multiples of TILE_COLS, long columns, columns after
-    // them, and SHORTMAX-entry chunk starts; plus up to one chunk per CHUNK entries
-    return 3ull * ng + rows / TILE_COLS + 4 * (edges / SHORTMAX) + 64;
+    // them, and shortmax-entry span starts; plus up to one chunk per chunk entries
+    return 3ull * ng + rows / TILE_COLS + 4 * (edges / SHORTMAX_MIN) + edges / CHUNK_MIN + 64;
 }
 
 inline Layout layout(void *ws, uint32_t ng, uint64_t rows, uint64_t edges, uint32_t nrhs, uint32_t iters,
@@ -561,6 +565,8 @@ extern "C" pp_status pp_pagerank_batched(const pp_graph *gs, uint32_t n_graphs, 
     d.iters = iters;
     d.rows = rows;
     d.c = c;
+    d.shortmax = (uint32_t)tuning("k3b_shortmax");
+    d.chunk = (uint32_t)tuning("k3b_chunk");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const k3b::Ws &w = L.w;
     k3b::setup_kernel<<<512, 256, 0, s>>>(d, w);

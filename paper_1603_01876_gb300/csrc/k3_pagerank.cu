@@ -11,15 +11,17 @@
 // Work split by column length (a degree-bucketed pull SpMV), one warp per
 // work item and no block-wide barriers, so each warp's gathers overlap other
 // warps' arithmetic:
-//   - a column longer than SHORTMAX entries is cut into chunks of CHUNK
+//   - a column longer than `shortmax` entries is cut into chunks of `chunk`
 //     entries; a warp sums a chunk with coalesced index loads and a group of
 //     gathers in flight per lane, reduces it in a fixed shuffle tree, and the
 //     warp that finishes a column's last chunk adds the chunk sums in order;
 //   - the other columns form tiles of at most 32 consecutive columns and
-//     2*SHORTMAX entries; a warp gathers count * x(u) for the tile's entries
-//     into its shared-memory slab, then each lane sums one short column in
-//     order, and the whole warp takes each medium column (lanes stride, fixed
-//     shuffle tree).
+//     2*shortmax entries; a warp gathers count * x(u) for the tile's entries
+//     into its shared-memory slab, then each lane sums one short column (at
+//     most `lane_short` entries) in order, and the whole warp takes each
+//     medium column (lanes stride, fixed shuffle tree).
+// shortmax, chunk and lane_short are tuning knobs (k3_shortmax, k3_chunk,
+// k3_lane_short); for one setting every run gives the same bits.
 // Items are dealt to warps round-robin.  Every column sum has a fixed order
 // and sum(r) is accumulated exactly in 128-bit fixed point, so results are
 // bitwise reproducible whichever warp takes which item.
@@ -38,10 +40,10 @@ namespace k3 {
 constexpr int THREADS = 256;
 constexpr int WARPS = THREADS / 32;
 constexpr int TILE_COLS = 32;      // one lane per column in a tile
-constexpr int SHORTMAX = 256;      // columns longer than this are cut into chunks
-constexpr int TILE_ENTRIES = 2 * SHORTMAX;
-constexpr int CHUNK = 2048;        // entries of a long column per work item
-constexpr int LANE_SHORT = 16;     // columns up to this long are summed by one lane
+constexpr int SHORTMAX_MAX = 256;  // largest long-column threshold (k3_shortmax)
+constexpr int TILE_ENTRIES = 2 * SHORTMAX_MAX;
+constexpr int CHUNK_MIN = 2048;    // smallest long-column chunk (k3_chunk)
+constexpr uint32_t NENT_BITS = 13; // a long chunk's item: entries | chunks of the column << NENT_BITS
 constexpr uint32_t LONG_FLAG = 0x80000000u;
 constexpr int SETUP_BLOCKS = 512;  // fixed, so the start-vector reduction is reproducible
 constexpr int PLAN_THREADS = 256;
@@ -75,7 +77,7 @@ struct Args {
     const uint64_t *info;
     uint32_t *bound;          // [N] boundary columns, ascending (plan)
     uint32_t *bound_item;     // [N] index of each boundary's first work item
-    uint4 *item;              // [N + M/CHUNK + 1] work items, see plan_items_kernel
+    uint4 *item;              // [N + M/CHUNK_MIN + 1] work items, see plan_items_kernel
     double *chunk_sum;        // [same] partial sums of long-column chunks
     uint32_t *ticket;         // [same] finished-chunk counters, at a column's first item
     uint64_t *plan_status;    // [N / PLAN_TILE + 1] look-back words of the plan scan
@@ -85,6 +87,9 @@ struct Args {
     Ctl *ctl;
     uint32_t *ctr;            // [1] plan tile counter
     double c;
+    uint32_t shortmax;    // columns longer than this are cut into chunks (power of two)
+    uint32_t chunk;       // entries of a long column per work item
+    uint32_t lane_short;  // tile columns up to this long are summed by one lane
 };
 
 __device__ __forceinline__ uint32_t ovf_lookup(const uint64_t *keys, const uint32_t *cnts, uint64_t n,
@@ -105,19 +110,23 @@ __device__ __forceinline__ uint32_t ovf_lookup(const uint64_t *keys, const uint3
 constexpr uint64_t F_AGG = 1ull << 62, F_INC = 2ull << 62;
 
 // Column v starts a work item if it is long, follows a long column, starts in
-// a new SHORTMAX-entry chunk of the entry array, or is a multiple of
+// a new shortmax-entry span of the entry array, or is a multiple of
 // TILE_COLS.  So a tile holds at most TILE_COLS columns, all starting in one
-// chunk, and its last column ends at most SHORTMAX entries past that chunk:
-// at most 2*SHORTMAX entries.
-__device__ __forceinline__ void classify(const uint32_t *colptr, uint32_t v, bool &bound, uint32_t &nitems) {
-    const uint32_t s = __ldg(colptr + v), e = __ldg(colptr + v + 1);
-    const bool is_long = e - s > (uint32_t)SHORTMAX;
-    nitems = is_long ? (e - s + CHUNK - 1) / CHUNK : 1u;
+// span, and its last column ends at most shortmax entries past that span:
+// at most 2*shortmax entries.
+__device__ __forceinline__ uint32_t item_count(const Args &a, uint32_t len) {
+    return len > a.shortmax ? (len + a.chunk - 1) / a.chunk : 1u;
+}
+
+__device__ __forceinline__ void classify(const Args &a, uint32_t v, bool &bound, uint32_t &nitems) {
+    const uint32_t s = __ldg(a.colptr + v), e = __ldg(a.colptr + v + 1);
+    const bool is_long = e - s > a.shortmax;
+    nitems = item_count(a, e - s);
     bound = true;
     if (v == 0 || is_long || v % TILE_COLS == 0) return;
-    const uint32_t ps = __ldg(colptr + v - 1);
-    if (s - ps > (uint32_t)SHORTMAX) return;  // the previous column is long
-    bound = (s / SHORTMAX) != (ps / SHORTMAX);
+    const uint32_t ps = __ldg(a.colptr + v - 1);
+    if (s - ps > a.shortmax) return;  // the previous column is long
+    bound = (s / a.shortmax) != (ps / a.shortmax);
 }
 
 // Compacts the boundary columns in order and numbers their work items (one
@@ -140,7 +149,7 @@ __global__ void __launch_bounds__(PLAN_THREADS) plan_kernel(Args a) {
         if (v < a.N) {
             bool b;
             uint32_t ni;
-            classify(a.colptr, (uint32_t)v, b, ni);
+            classify(a, (uint32_t)v, b, ni);
             if (b) {
                 bmask |= 1u << j;
                 nitems += ni;
@@ -181,7 +190,7 @@ __global__ void __launch_bounds__(PLAN_THREADS) plan_kernel(Args a) {
         a.bound[bi] = v;
         a.bound_item[bi] = ii;
         const uint32_t s = __ldg(a.colptr + v), e = __ldg(a.colptr + v + 1);
-        ii += e - s > (uint32_t)SHORTMAX ? (e - s + CHUNK - 1) / CHUNK : 1u;
+        ii += item_count(a, e - s);
         ++bi;
     }
 }
@@ -190,18 +199,19 @@ __global__ void __launch_bounds__(PLAN_THREADS) plan_kernel(Args a) {
 // entries without reading the column pointers first:
 //   tile:        (first column, number of columns, first entry, entries)
 //   long chunk:  (column | LONG_FLAG, first item of the column, first entry,
-//                 entries | chunks of the column << 12)
+//                 entries | chunks of the column << NENT_BITS)
 // A tile runs to the next boundary; a long column gets one item per chunk.
 __global__ void __launch_bounds__(256) plan_items_kernel(Args a) {
     const uint32_t nb = a.ctl->n_bound;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x) {
         const uint32_t v = a.bound[i], o = a.bound_item[i];
         const uint32_t s = __ldg(a.colptr + v), e = __ldg(a.colptr + v + 1);
-        if (e - s > (uint32_t)SHORTMAX) {
-            const uint32_t nc = (e - s + CHUNK - 1) / CHUNK;
+        if (e - s > a.shortmax) {
+            // a kept column has at most M/2 <= 2^30 entries (the largest one is removed), so nc < 2^19
+            const uint32_t nc = (e - s + a.chunk - 1) / a.chunk;
             for (uint32_t k = 0; k < nc; ++k) {
-                const uint32_t cs = s + k * CHUNK;
-                a.item[o + k] = make_uint4(v | LONG_FLAG, o, cs, min((uint32_t)CHUNK, e - cs) | (nc << 12));
+                const uint32_t cs = s + k * a.chunk;
+                a.item[o + k] = make_uint4(v | LONG_FLAG, o, cs, min(a.chunk, e - cs) | (nc << NENT_BITS));
                 a.ticket[o + k] = 0;
             }
         } else {
@@ -307,7 +317,7 @@ __device__ __forceinline__ TA warp_sum(TA y) {
 template <typename TS, typename TA, typename TO, bool LAST, int UNROLL, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB) iterate_kernel(Args a, const TA *inv, const TS *__restrict__ x_in,
                                                           TS *__restrict__ x_out, TO *r_out, uint32_t iter) {
-    static_assert(TILE_ENTRIES % (32 * UNROLL) == 0 && CHUNK % (32 * UNROLL) == 0, "unroll must divide the work");
+    static_assert(TILE_ENTRIES % (32 * UNROLL) == 0, "unroll must divide the work");
     __shared__ TA s_prod[WARPS][TILE_ENTRIES];
     __shared__ uint32_t s_cp[WARPS][TILE_COLS + 1];
     __shared__ uint64_t s_fx[2 * WARPS];
@@ -336,7 +346,7 @@ __global__ void __launch_bounds__(THREADS, MINB) iterate_kernel(Args a, const TA
         if (it.x & LONG_FLAG) {
             // ---- one chunk of a long column
             const uint32_t col = it.x & ~LONG_FLAG, first = it.y;
-            const uint32_t nent = it.w & 0xfffu, nchunks = it.w >> 12;
+            const uint32_t nent = it.w & ((1u << NENT_BITS) - 1), nchunks = it.w >> NENT_BITS;
             TA part = TA(0);
             for (uint32_t base = 0; base < nent; base += 32 * UNROLL) {
                 uint32_t w[UNROLL];
@@ -430,7 +440,7 @@ __global__ void __launch_bounds__(THREADS, MINB) iterate_kernel(Args a, const TA
             uint32_t medium = 0;
             if (lane < (int)ncol) {
                 const uint32_t s = cp[lane], e = cp[lane + 1];
-                if (e - s <= (uint32_t)LANE_SHORT) {
+                if (e - s <= a.lane_short) {
                     TA y = TA(0);
                     for (uint32_t k = s; k < e; ++k) y += prod[k];
                     epi(c0 + lane, y, myinv, acc);
@@ -503,7 +513,7 @@ inline Layout layout(void *ws, uint64_t M, uint32_t scale, uint32_t iters, pp_dt
     Carver c(ws);
     Layout L;
     const uint64_t N = 1ull << scale;
-    const uint64_t max_items = N + M / CHUNK + 1;
+    const uint64_t max_items = N + M / CHUNK_MIN + 1;
     const size_t xs = dt == PP_FP64 ? 8 : (dt == PP_FP32 ? 4 : 2);
     L.x[0] = c.take<char>(N * xs);
     L.x[1] = c.take<char>(N * xs);
@@ -555,6 +565,9 @@ pp_status run_unroll(const pp_graph *g, const double *r0, uint32_t iters, double
     a.ctl = L.ctl;
     a.ctr = L.ctr;
     a.c = c;
+    a.shortmax = (uint32_t)tuning("k3_shortmax");
+    a.chunk = (uint32_t)tuning("k3_chunk");
+    a.lane_short = (uint32_t)tuning("k3_lane_short");
     const TA *inv = dt == PP_FP64 ? reinterpret_cast<const TA *>(g->inv_dout64)
                                   : reinterpret_cast<const TA *>(g->inv_dout32);
     if (!inv) return PP_ERR_INVALID_ARG;

@@ -24,6 +24,11 @@ Knob g_knobs[] = {
     {"k3_unroll_f32", {8}, {4, 8, 0, 0}},
     {"k3_unroll_f64", {8}, {4, 8, 0, 0}},
     {"k3_minblocks", {4}, {4, 5, 6, 0}},
+    {"k3_shortmax", {256}, {64, 128, 256, 0}},
+    {"k3_chunk", {2048}, {2048, 4096, 0, 0}},
+    {"k3_lane_short", {16}, {8, 16, 32, 0}},
+    {"k3b_shortmax", {256}, {128, 256, 0, 0}},
+    {"k3b_chunk", {512}, {256, 512, 1024, 0}},
 };
 Knob *find_knob(const char *key) {
     if (!key) return nullptr;

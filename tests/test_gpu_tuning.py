@@ -1,0 +1,87 @@
+"""Kernel 3 under non-default tuning knobs, against the oracle.
+
+The thresholds move columns between the tile, warp and chunk paths; every
+setting must stay within the stated tolerances (binary64 L1 <= 1e-12,
+binary32 L1 <= 1e-6 and max relative <= 1e-4) and be reproducible.
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import host_u32, rank_errors
+
+pytestmark = pytest.mark.gpu
+
+SINGLE = [
+    {"k3_shortmax": 64, "k3_lane_short": 8},
+    {"k3_chunk": 4096, "k3_lane_short": 32},
+    {"k3_shortmax": 128, "k3_minblocks": 6, "k3_unroll_f32": 4, "k3_unroll_f64": 4},
+    {"k3_minblocks": 5, "k3_chunk": 4096, "k3_shortmax": 64},
+]
+BATCHED = [{"k3b_shortmax": 128, "k3b_chunk": 256}, {"k3b_chunk": 1024}]
+
+
+@pytest.fixture(scope="module")
+def graph17(k0, oracle_mod):
+    import torch
+
+    import paper_1603_01876_gb300 as pp
+
+    scale = 17  # columns of over 4096 entries: several chunks at either chunk size
+    u, v = k0.edges_device(scale, 21)
+    us, vs = pp.sort_edges(u, v, scale)
+    g = pp.build_filter_normalize(us, vs, scale)
+    R = oracle_mod.k2_filter(host_u32(us), host_u32(vs), 1 << scale)
+    r0h = k0.r0_host(1 << scale, 21)
+    want = oracle_mod.k3_pagerank(R, r0h, 20, 0.85)
+    assert np.bincount(R["col"].astype(np.int64), minlength=1 << scale).max() > 4096
+    return pp, g, torch.from_numpy(r0h).cuda(), want
+
+
+def _with(pp, knobs, fn):
+    old = {k: pp.get_tuning(k) for k in knobs}
+    try:
+        for k, v in knobs.items():
+            pp.set_tuning(k, v)
+        return fn()
+    finally:
+        for k, v in old.items():
+            pp.set_tuning(k, v)
+
+
+@pytest.mark.parametrize("knobs", SINGLE, ids=lambda d: ",".join("%s=%d" % kv for kv in d.items()))
+def test_single_vector_knobs(graph17, knobs):
+    pp, g, r0, want = graph17
+    for dtype, (l1, mr) in (("fp64", (1e-12, 1e-9)), ("fp32", (1e-6, 1e-4))):
+        a = _with(pp, knobs, lambda: pp.pagerank(g, r0, 20, 0.85, dtype).cpu().numpy())
+        b = _with(pp, knobs, lambda: pp.pagerank(g, r0, 20, 0.85, dtype).cpu().numpy())
+        assert pp.last_device_error() == 0
+        assert np.array_equal(a, b), "not reproducible under %s" % knobs
+        e = rank_errors(a, want)
+        assert e["l1"] <= l1 and e["max_rel"] <= mr, (dtype, knobs, e)
+
+
+@pytest.mark.parametrize("knobs", BATCHED, ids=lambda d: ",".join("%s=%d" % kv for kv in d.items()))
+def test_batched_knobs(k0, oracle_mod, knobs):
+    import torch
+
+    import paper_1603_01876_gb300 as pp
+
+    scales = [14, 9, 12]
+    graphs, edges = [], []
+    for i, s in enumerate(scales):
+        u, v = k0.edges_device(s, 31, graph=i)
+        us, vs = pp.sort_edges(u, v, s)
+        graphs.append(pp.build_filter_normalize(us, vs, s))
+        edges.append((host_u32(us), host_u32(vs)))
+    nrhs = 3
+    r0 = np.concatenate([np.stack([k0.r0_host(1 << s, 31, graph=i, rhs=j) for j in range(nrhs)], axis=1)
+                         for i, s in enumerate(scales)])
+    got = _with(pp, knobs, lambda: pp.pagerank_batched(graphs, torch.from_numpy(r0).cuda(), nrhs).cpu().numpy())
+    assert pp.last_device_error() == 0
+    row = np.cumsum([0] + [1 << s for s in scales])
+    for i, s in enumerate(scales):
+        R = oracle_mod.k2_filter(edges[i][0], edges[i][1], 1 << s)
+        for j in range(nrhs):
+            want = oracle_mod.k3_pagerank(R, r0[row[i]:row[i + 1], j], 20, 0.85)
+            e = rank_errors(got[row[i]:row[i + 1], j], want)
+            assert e["l1"] <= 1e-6 and e["max_rel"] <= 1e-4, (knobs, i, j, e)
