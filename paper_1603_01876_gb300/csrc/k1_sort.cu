@@ -88,17 +88,17 @@ void run(const uint32_t *u, const uint32_t *v, uint64_t M, uint32_t scale, uint3
     const PackSrc<KeyT, false> pack{u, v, scale};
     const UnpackDst<KeyT> unpack{u_out, v_out, scale};
     if (P == 1) {
-        os::launch_pass<KeyT, false>(L.sort, 0, P, pack, unpack, nullptr, M, s);
+        os::launch_pass<KeyT>(L.sort, 0, P, pack, unpack, nullptr, M, s);
         return;
     }
-    os::launch_pass<KeyT, false>(L.sort, 0, P, pack, KeyDst<KeyT>{A}, nullptr, M, s);
+    os::launch_pass<KeyT>(L.sort, 0, P, pack, KeyDst<KeyT>{A}, nullptr, M, s);
     for (int p = 1; p < P - 1; ++p) {
         KeyT *in = (p & 1) ? A : B;
         KeyT *out = (p & 1) ? B : A;
-        os::launch_pass<KeyT, false>(L.sort, p, P, KeySrc<KeyT>{in}, KeyDst<KeyT>{out}, nullptr, M, s);
+        os::launch_pass<KeyT>(L.sort, p, P, KeySrc<KeyT>{in}, KeyDst<KeyT>{out}, nullptr, M, s);
     }
     KeyT *last_in = ((P - 1) & 1) ? A : B;
-    os::launch_pass<KeyT, false>(L.sort, P - 1, P, KeySrc<KeyT>{last_in}, unpack, nullptr, M, s);
+    os::launch_pass<KeyT>(L.sort, P - 1, P, KeySrc<KeyT>{last_in}, unpack, nullptr, M, s);
 }
 
 }  // namespace k1
@@ -241,7 +241,7 @@ extern "C" pp_status pp_selftest_lookback_timeout(uint32_t spin_limit, void *ws,
         static_cast<uint32_t *>(L.k1.sort.status[0]), ceil_div(M, os::TILE) * os::RADIX * word / 4);
     k1_set_u32<<<1, 1, 0, s>>>(L.k1.sort.tile_ctr, 1u);
     count_launch(2);
-    os::launch_pass<uint32_t, false>(L.k1.sort, 0, P, k1::PackSrc<uint32_t, false>{L.u, L.v, scale},
+    os::launch_pass<uint32_t>(L.k1.sort, 0, P, k1::PackSrc<uint32_t, false>{L.u, L.v, scale},
                                      k1::KeyDst<uint32_t>{static_cast<uint32_t *>(L.k1.keys[0])}, nullptr, M, s, 0,
                                      spin_limit);
     return launch_status();

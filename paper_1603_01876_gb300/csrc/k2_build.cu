@@ -599,7 +599,7 @@ extern "C" pp_status pp_build_filter_normalize(const uint32_t *us, const uint32_
         // transpose: every entry sorted by column, P passes over bits 32 .. 32+scale
         const uint64_t *n_dev = g->info + PP_INFO_NNZ0;
         for (int p = 0; p < P; ++p) {
-            os::launch_pass<unsigned long long, false>(L.sort, p, P, k2::EntSrc{L.ent[p & 1]},
+            os::launch_pass<unsigned long long>(L.sort, p, P, k2::EntSrc{L.ent[p & 1]},
                                                        k2::EntDst{L.ent[(p + 1) & 1]}, n_dev, M, s, 32);
         }
         sorted = L.ent[P & 1];

@@ -64,14 +64,16 @@ struct PassCtl {
 // Status words are 32-bit while every count fits in 30 bits.
 inline bool wide_status(uint64_t n_max) { return n_max >= (1ull << 30); }
 
-template <typename KeyT, typename StatT, bool HAS_VAL, class Src, class Dst>
-__global__ void __launch_bounds__(THREADS, 3) pass_kernel(Src src, Dst dst, PassCtl ctl) {
+// Blocks per SM the registers are budgeted for: five (the most the 42 KB of
+// shared memory allows with 64-bit keys) beat three without spills on GB300.
+constexpr int PASS_MINB = 5;
+
+template <typename KeyT, typename StatT, class Src, class Dst>
+__global__ void __launch_bounds__(THREADS, PASS_MINB) pass_kernel(Src src, Dst dst, PassCtl ctl) {
     using F = Flags<StatT>;
-    __shared__ KeyT s_keys[TILE];
-    __shared__ uint32_t s_vals[HAS_VAL ? TILE : 1];
-    __shared__ uint32_t s_whist[WARPS][RADIX];
-    __shared__ uint32_t s_binstart[RADIX];
-    __shared__ long long s_gbase[RADIX];
+    __shared__ KeyT s_keys[TILE];               // the tile in input order, then in digit order
+    __shared__ uint32_t s_whist[WARPS][RADIX];  // per-warp digit counters, then staging offsets
+    __shared__ uint32_t s_gbase[RADIX];  // global index of the digit's first key minus its staging offset (mod 2^32)
     __shared__ uint32_t s_scan[40];
     __shared__ uint32_t s_tile;
 
@@ -92,18 +94,22 @@ __global__ void __launch_bounds__(THREADS, 3) pass_kernel(Src src, Dst dst, Pass
     // Warp-striped load: warp w owns elements [w*ITEMS*32, (w+1)*ITEMS*32) of
     // the tile; item i of a lane is element i*32 + lane of that range, so the
     // order (warp, item, lane) is the input order.
-    const uint64_t base = (uint64_t)tile * TILE + (uint64_t)warp * (ITEMS * 32);
-    KeyT keys[ITEMS];
-    uint32_t vals[ITEMS];
-    uint32_t dig[ITEMS];  // digit, or RADIX for an absent / filtered element
+    const uint32_t wbase = (uint32_t)warp * (ITEMS * 32);
+    const uint64_t base = (uint64_t)tile * TILE + wbase;
+    uint32_t dig[ITEMS];  // digit, or RADIX for an absent element
+    {
+        KeyT keys[ITEMS];
+        uint32_t unused;
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-        const uint64_t idx = base + (uint64_t)i * 32 + lane;
-        bool ok = false;
-        keys[i] = 0;
-        vals[i] = 0;
-        if (idx < n) ok = src.load(idx, keys[i], vals[i]);
-        dig[i] = ok ? (uint32_t)(keys[i] >> ctl.shift) & (RADIX - 1) : RADIX;
+        for (int i = 0; i < ITEMS; ++i) {
+            const uint64_t idx = base + (uint64_t)i * 32 + lane;
+            keys[i] = 0;
+            if (idx < n) src.load(idx, keys[i], unused);
+            dig[i] = idx < n ? (uint32_t)(keys[i] >> ctl.shift) & (RADIX - 1) : RADIX;
+        }
+        // park the keys in shared memory (input order) while the tile is ranked and looks back
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) s_keys[wbase + i * 32 + lane] = keys[i];
     }
 
     // Warp-level multisplit: rank of each key among equal digits of its warp.
@@ -134,7 +140,9 @@ __global__ void __launch_bounds__(THREADS, 3) pass_kernel(Src src, Dst dst, Pass
 
     uint32_t nvalid;
     const uint32_t bstart = block_exclusive_sum<uint32_t, THREADS>(tcount, s_scan, &nvalid);
-    s_binstart[tid] = bstart;
+    // staging offset of warp w's first key of digit tid (one lookup per key below)
+#pragma unroll
+    for (int w = 0; w < WARPS; ++w) s_whist[w][tid] += bstart;
 
     // Decoupled look-back for this digit, four predecessors per round trip.
     StatT excl = 0;
@@ -166,18 +174,18 @@ __global__ void __launch_bounds__(THREADS, 3) pass_kernel(Src src, Dst dst, Pass
         }
         st_status(mine, F::INC | (excl + (StatT)tcount));
     }
-    s_gbase[tid] = (long long)hexcl + (long long)excl - (long long)bstart;
-    __syncthreads();
+    // every global index is below 2^31, so the offset arithmetic may wrap mod 2^32
+    s_gbase[tid] = (uint32_t)((uint64_t)hexcl + (uint64_t)excl) - bstart;
 
-    // Stage the tile in digit order in shared memory.
+    // Stage the tile in digit order, in place: every key is read before any is written.
+    KeyT keys[ITEMS];
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) keys[i] = s_keys[wbase + i * 32 + lane];
+    __syncthreads();
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         const uint32_t d = dig[i] & 0xffffu;
-        if (d < RADIX) {
-            const uint32_t pos = s_binstart[d] + s_whist[warp][d] + (dig[i] >> 16);
-            s_keys[pos] = keys[i];
-            if (HAS_VAL) s_vals[pos] = vals[i];
-        }
+        if (d < RADIX) s_keys[s_whist[warp][d] + (dig[i] >> 16)] = keys[i];
     }
     __syncthreads();
 
@@ -185,7 +193,7 @@ __global__ void __launch_bounds__(THREADS, 3) pass_kernel(Src src, Dst dst, Pass
     for (uint32_t j = tid; j < nvalid; j += THREADS) {
         const KeyT k = s_keys[j];
         const uint32_t d = (uint32_t)(k >> ctl.shift) & (RADIX - 1);
-        dst.store((uint64_t)(s_gbase[d] + (long long)j), k, HAS_VAL ? s_vals[j] : 0u);
+        dst.store((uint64_t)(uint32_t)(s_gbase[d] + j), k, 0u);
     }
 }
 
@@ -247,7 +255,7 @@ inline bool prefer_shared(K kernel) {
 }
 
 // Launches pass `p` (of npasses) of a sort prepared in `w`.
-template <typename KeyT, bool HAS_VAL, class Src, class Dst>
+template <typename KeyT, class Src, class Dst>
 inline void launch_pass(const SortWs &w, int p, int npasses, Src src, Dst dst, const uint64_t *n_dev,
                         uint64_t n_max, cudaStream_t s, uint32_t shift0 = 0,
                         uint32_t spin_limit = kSpinLimit) {
@@ -262,13 +270,13 @@ inline void launch_pass(const SortWs &w, int p, int npasses, Src src, Dst dst, c
     ctl.spin_limit = spin_limit;
     const unsigned grid = (unsigned)ceil_div(n_max ? n_max : 1, TILE);
     if (w.wide) {
-        static const bool once = prefer_shared(pass_kernel<KeyT, uint64_t, HAS_VAL, Src, Dst>);
+        static const bool once = prefer_shared(pass_kernel<KeyT, uint64_t, Src, Dst>);
         (void)once;
-        pass_kernel<KeyT, uint64_t, HAS_VAL, Src, Dst><<<grid, THREADS, 0, s>>>(src, dst, ctl);
+        pass_kernel<KeyT, uint64_t, Src, Dst><<<grid, THREADS, 0, s>>>(src, dst, ctl);
     } else {
-        static const bool once = prefer_shared(pass_kernel<KeyT, uint32_t, HAS_VAL, Src, Dst>);
+        static const bool once = prefer_shared(pass_kernel<KeyT, uint32_t, Src, Dst>);
         (void)once;
-        pass_kernel<KeyT, uint32_t, HAS_VAL, Src, Dst><<<grid, THREADS, 0, s>>>(src, dst, ctl);
+        pass_kernel<KeyT, uint32_t, Src, Dst><<<grid, THREADS, 0, s>>>(src, dst, ctl);
     }
     count_launch();
 }
