@@ -96,32 +96,39 @@ __global__ void __launch_bounds__(THREADS, PASS_MINB) pass_kernel(Src src, Dst d
     // order (warp, item, lane) is the input order.
     const uint32_t wbase = (uint32_t)warp * (ITEMS * 32);
     const uint64_t base = (uint64_t)tile * TILE + wbase;
-    uint32_t dig[ITEMS];  // digit, or RADIX for an absent element
+    // valid items of this lane (the tile's tail may be short)
+    const uint64_t first = base + lane;
+    const uint64_t left = first < n ? (n - first + 31) / 32 : 0;
+    const int nv = left < (uint64_t)ITEMS ? (int)left : ITEMS;
     {
         KeyT keys[ITEMS];
         uint32_t unused;
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
-            const uint64_t idx = base + (uint64_t)i * 32 + lane;
             keys[i] = 0;
-            if (idx < n) src.load(idx, keys[i], unused);
-            dig[i] = idx < n ? (uint32_t)(keys[i] >> ctl.shift) & (RADIX - 1) : RADIX;
+            if (i < nv) src.load(base + (uint64_t)i * 32 + lane, keys[i], unused);
         }
         // park the keys in shared memory (input order) while the tile is ranked and looks back
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) s_keys[wbase + i * 32 + lane] = keys[i];
     }
+    __syncwarp();
 
-    // Warp-level multisplit: rank of each key among equal digits of its warp.
+    // Warp-level multisplit: rank of each key among equal digits of its warp,
+    // kept three 10-bit ranks to a register (the digit is read again later).
+    constexpr int RW = (ITEMS + 2) / 3;
+    uint32_t rank[RW];
+#pragma unroll
+    for (int q = 0; q < RW; ++q) rank[q] = 0;
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        const uint32_t d = dig[i];
+        const uint32_t d = i < nv ? (uint32_t)(s_keys[wbase + i * 32 + lane] >> ctl.shift) & (RADIX - 1) : RADIX;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
         const uint32_t before = d < RADIX ? s_whist[warp][d] : 0u;
         __syncwarp();
         if (d < RADIX && (peers >> lane) == 1u) s_whist[warp][d] = before + __popc(peers);
         __syncwarp();
-        dig[i] = d | ((before + __popc(peers & lanemask_lt())) << 16);
+        rank[i / 3] |= (before + __popc(peers & lanemask_lt())) << (10 * (i % 3));
     }
     __syncthreads();
 
@@ -184,8 +191,10 @@ __global__ void __launch_bounds__(THREADS, PASS_MINB) pass_kernel(Src src, Dst d
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        const uint32_t d = dig[i] & 0xffffu;
-        if (d < RADIX) s_keys[s_whist[warp][d] + (dig[i] >> 16)] = keys[i];
+        if (i < nv) {
+            const uint32_t d = (uint32_t)(keys[i] >> ctl.shift) & (RADIX - 1);
+            s_keys[s_whist[warp][d] + ((rank[i / 3] >> (10 * (i % 3))) & 1023u)] = keys[i];
+        }
     }
     __syncthreads();
 
