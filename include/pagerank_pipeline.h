@@ -80,11 +80,18 @@ typedef enum {
  *
  *   colptr[N+1]  column v holds entries colptr[v] .. colptr[v+1]-1;
  *                colptr[N] = nnz.
- *   rowc[M]      entry e (e < nnz) packs the row u (= start vertex) in its low
- *                `scale` bits and the count A(u,v) in the high 32-scale bits;
- *                within a column the rows ascend.  A count >= 2^(32-scale)-1
- *                is stored as the all-ones field and found in the overflow
- *                table.
+ *   rowc[M]      entry e (e < nnz) packs the position perm[u] of its row u
+ *                (= start vertex) in its low `scale` bits and the count
+ *                A(u,v) in the high 32-scale bits; within a column the
+ *                positions ascend.  A count >= 2^(32-scale)-1 is stored as the
+ *                all-ones field and found in the overflow table.
+ *   perm[N], iperm[N]  the order in which Kernel 3 stores the gathered
+ *                vector x: rows by decreasing floor(log2(out-degree before
+ *                the column filters)), ties by vertex id; perm[u] is the
+ *                position of row u and iperm[p] the row at position p.  Rows
+ *                gathered most often sit together, so a warp's gathers share
+ *                cache lines.  (A storage order only: A, the degrees and the
+ *                ranks are indexed by vertex id.)
  *   ovf_key[n], ovf_cnt[n]  the overflow table: key (u << 32 | v) ascending,
  *                count; n = info[PP_INFO_NOVF] <= pp_graph_lengths()[2].
  *   d_in[N]      sum(A,1) before the column filters (Sec. IV-C step 2).
@@ -106,12 +113,15 @@ typedef struct {
     float *inv_dout32;
     double *inv_dout64;
     uint64_t *info;
+    uint32_t *perm;
+    uint32_t *iperm;
 } pp_graph;
 
 /* Element counts of the pp_graph arrays for M edges at this scale, in the
  * order colptr, rowc, ovf_key, ovf_cnt, d_in, d_out, inv_dout32, inv_dout64,
- * info.  out[] must hold 9 values. */
-pp_status pp_graph_lengths(uint64_t M, uint32_t scale, uint64_t out[9]);
+ * info, perm, iperm.  out[] must hold 11 values. */
+#define PP_GRAPH_ARRAYS 11
+pp_status pp_graph_lengths(uint64_t M, uint32_t scale, uint64_t out[PP_GRAPH_ARRAYS]);
 
 /*
  * Kernel 1 (Sec. IV-B): sort the edges so that u_out is nondecreasing,

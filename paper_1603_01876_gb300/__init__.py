@@ -25,6 +25,7 @@ DTYPES = {"fp64": 0, "fp32": 1, "bf16": 2}
 RULES = {"lowest": 0, "all_ties": 1}
 INFO = {"nnz0": 0, "nnz": 1, "dmax": 2, "vmax": 3, "ties": 4, "novf": 5, "supernodes": 6}
 INFO_LEN = 8
+GRAPH_ARRAYS = 11
 DEV_RANGE, DEV_TIMEOUT = 1, 2
 
 
@@ -41,6 +42,7 @@ class CGraph(ctypes.Structure):
         ("colptr", ctypes.c_void_p), ("rowc", ctypes.c_void_p), ("ovf_key", ctypes.c_void_p),
         ("ovf_cnt", ctypes.c_void_p), ("d_in", ctypes.c_void_p), ("d_out", ctypes.c_void_p),
         ("inv_dout32", ctypes.c_void_p), ("inv_dout64", ctypes.c_void_p), ("info", ctypes.c_void_p),
+        ("perm", ctypes.c_void_p), ("iperm", ctypes.c_void_p),
     ]
 
 
@@ -151,7 +153,7 @@ def selftest_lookback_timeout(spin_limit, device=None, stream=None):
 
 
 def graph_lengths(M, scale):
-    out = (ctypes.c_uint64 * 9)()
+    out = (ctypes.c_uint64 * GRAPH_ARRAYS)()
     _check("pp_graph_lengths", _lib().pp_graph_lengths(M, scale, out))
     return list(out)
 
@@ -189,9 +191,12 @@ class Graph:
         self.inv_dout32 = torch.empty(lens[6], dtype=torch.float32, device=device)
         self.inv_dout64 = torch.empty(lens[7], dtype=torch.float64, device=device)
         self.info = torch.zeros(lens[8], dtype=i64, device=device)
+        self.perm = torch.empty(lens[9], dtype=i32, device=device)
+        self.iperm = torch.empty(lens[10], dtype=i32, device=device)
         self.c = CGraph(scale, 0, M, self.colptr.data_ptr(), self.rowc.data_ptr(), self.ovf_key.data_ptr(),
                         self.ovf_cnt.data_ptr(), self.d_in.data_ptr(), self.d_out.data_ptr(),
-                        self.inv_dout32.data_ptr(), self.inv_dout64.data_ptr(), self.info.data_ptr())
+                        self.inv_dout32.data_ptr(), self.inv_dout64.data_ptr(), self.info.data_ptr(),
+                        self.perm.data_ptr(), self.iperm.data_ptr())
 
     def info_dict(self):
         v = self.info.cpu().tolist()

@@ -7,8 +7,13 @@
 //                    each row's counts (entries arrive in row order) go to
 //                    the row's out-degree before filtering, and the column
 //                    digits to the transpose's histograms.
-//   transpose        stable LSD radix sort of the entry words by column (rows
-//                    stay ascending inside a column).
+//   relabel          rows ordered by decreasing floor(log2(out-degree)) (a
+//                    one-pass radix sort of the vertices): perm / iperm; the
+//                    entry words take the row's position perm[u], and one
+//                    radix pass on the row's bucket puts them in position
+//                    order (the storage order Kernel 3 gathers from).
+//   transpose        stable LSD radix sort of the entry words by column (row
+//                    positions stay ascending inside a column).
 //   colscan_kernel   step 2: with the entries grouped by column, the entry
 //                    count and d_in = sum(A,1) of each column, one atomic per
 //                    run of a column inside a thread's stretch.
@@ -108,6 +113,7 @@ struct UniqueArgs {
     uint64_t *ovf_key;
     uint32_t *ovf_cnt;
     uint32_t *d_out;          // [N]: row sums before the filter
+    uint32_t *row_nent;       // [N]: entries per row before the filter
     uint32_t *hist;           // [npasses * 256] column digits, for the transpose
     int npasses;
     int vec;                  // us and vs are 16-byte aligned: load 4 ids at a time
@@ -230,7 +236,7 @@ __global__ void __launch_bounds__(UQ_THREADS, 3) unique_kernel(UniqueArgs a) {
         const uint64_t gex = s_excl + texcl;
         uint32_t lpos = (uint32_t)texcl;  // place inside the tile's output
         uint64_t epos = (gex >> 32) & 0x3fffffffull;
-        uint32_t row = 0xffffffffu, rowsum = 0;
+        uint32_t row = 0xffffffffu, rowsum = 0, rowent = 0;
 #pragma unroll
         for (int j = 0; j < UQ_ITEMS; ++j) {
             if (!(tails >> j & 1u)) continue;
@@ -253,14 +259,22 @@ __global__ void __launch_bounds__(UQ_THREADS, 3) unique_kernel(UniqueArgs a) {
             for (int p = 0; p < a.npasses; ++p) atomicAdd(&s_hist[p][(v >> (8 * p)) & (os::RADIX - 1)], 1u);
             // this thread's entries ascend in u: add each row's run once
             if (u != row) {
-                if (rowsum) atomicAdd(&a.d_out[row], rowsum);
+                if (rowsum) {
+                    atomicAdd(&a.d_out[row], rowsum);
+                    atomicAdd(&a.row_nent[row], rowent);
+                }
                 row = u;
                 rowsum = 0;
+                rowent = 0;
             }
             rowsum += c;
+            ++rowent;
             ++lpos;
         }
-        if (rowsum) atomicAdd(&a.d_out[row], rowsum);
+        if (rowsum) {
+            atomicAdd(&a.d_out[row], rowsum);
+            atomicAdd(&a.row_nent[row], rowent);
+        }
         __syncthreads();
         {
             unsigned long long *dst = a.ent + (s_excl & 0xffffffffull);
@@ -285,7 +299,8 @@ constexpr int CS_TILE = 256 * CS_ITEMS;
 // and adds each run with one atomic.
 __global__ void __launch_bounds__(256) colscan_kernel(const unsigned long long *ent, const uint64_t *info,
                                                       uint32_t scale, uint32_t cmax, const uint64_t *ovf_key,
-                                                      const uint32_t *ovf_cnt, unsigned long long *deg) {
+                                                      const uint32_t *ovf_cnt, const uint32_t *iperm,
+                                                      unsigned long long *deg) {
     // row stride CS_ITEMS + 1 words: a half-warp's reads of its own rows hit distinct banks
     __shared__ unsigned long long s[256 * (CS_ITEMS + 1)];
     const int tid = threadIdx.x;
@@ -308,7 +323,7 @@ __global__ void __launch_bounds__(256) colscan_kernel(const unsigned long long *
                 const unsigned long long e = s[tid * (CS_ITEMS + 1) + j];
                 const uint32_t v = (uint32_t)(e >> 32), w = (uint32_t)e;
                 uint32_t c = w >> scale;
-                if (c == cmax) c = ovf_lookup(ovf_key, ovf_cnt, novf, ((uint64_t)(w & umask) << 32) | v);
+                if (c == cmax) c = ovf_lookup(ovf_key, ovf_cnt, novf, ((uint64_t)iperm[w & umask] << 32) | v);
                 if (v != col) {
                     if (acc) atomicAdd(&deg[col], acc);
                     col = v;
@@ -331,8 +346,8 @@ constexpr int CP_ITEMS = 4;
 // removal flag.
 __global__ void __launch_bounds__(256) compact_kernel(const unsigned long long *ent, const uint64_t *info,
                                                       uint32_t scale, uint32_t cmax, const uint64_t *ovf_key,
-                                                      const uint32_t *ovf_cnt, const uint32_t *shift, uint32_t *rowc,
-                                                      uint32_t *d_out) {
+                                                      const uint32_t *ovf_cnt, const uint32_t *iperm,
+                                                      const uint32_t *shift, uint32_t *rowc, uint32_t *d_out) {
     const uint64_t n = info[PP_INFO_NNZ0];
     const uint64_t novf = info[PP_INFO_NOVF];
     const uint32_t umask = (1u << scale) - 1u;
@@ -350,9 +365,10 @@ __global__ void __launch_bounds__(256) compact_kernel(const unsigned long long *
             if (i >= n) break;
             const uint32_t v = (uint32_t)(e[q] >> 32), w = (uint32_t)e[q];
             if (sh[q] & KILL_BIT) {
+                const uint32_t u = iperm[w & umask];
                 uint32_t c = w >> scale;
-                if (c == cmax) c = ovf_lookup(ovf_key, ovf_cnt, novf, ((uint64_t)(w & umask) << 32) | v);
-                atomicSub(&d_out[w & umask], c);
+                if (c == cmax) c = ovf_lookup(ovf_key, ovf_cnt, novf, ((uint64_t)u << 32) | v);
+                atomicSub(&d_out[u], c);
             } else {
                 rowc[i - sh[q]] = w;
             }
@@ -481,7 +497,75 @@ __global__ void __launch_bounds__(256) finalize_kernel(const uint32_t *d_out, ui
     }
 }
 
-// The transpose sorts the 64-bit entry words by their column (bits 63:32).
+// ----------------------------------------------------------------- relabel
+// A row's bucket is clz(d | 1) = 31 - floor(log2(max(d, 1))) of its
+// out-degree d before the filter: ascending buckets = descending degrees.
+__device__ __forceinline__ uint32_t row_bucket(uint32_t d) { return (uint32_t)__clz(d | 1u); }
+
+constexpr uint32_t VKEY_SHIFT = 27;  // vertex key: bucket << 27 | u (u < 2^27)
+constexpr uint32_t EKEY_SHIFT = 59;  // entry key: bucket in bits 63:59 above the column (< 2^27)
+
+// Histograms of the row buckets over the vertices (for the vertex pass) and
+// over the entries (for the entry pass), and pass 0's look-back words cleared.
+__global__ void __launch_bounds__(256) relabel_hist_kernel(const uint32_t *d_out, const uint32_t *row_nent,
+                                                           uint32_t N, uint32_t *vhist, uint32_t *ehist,
+                                                           uint32_t *vstatus0, uint64_t vstatus_words) {
+    __shared__ uint32_t sv[32], se[32];
+    if (threadIdx.x < 32) sv[threadIdx.x] = se[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < N; u += stride) {
+        const uint32_t b = row_bucket(d_out[u]);
+        atomicAdd(&sv[b], 1u);
+        const uint32_t ne = row_nent[u];
+        if (ne) atomicAdd(&se[b], ne);
+    }
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < vstatus_words; i += stride) vstatus0[i] = 0;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        if (sv[threadIdx.x]) atomicAdd(&vhist[threadIdx.x], sv[threadIdx.x]);
+        if (se[threadIdx.x]) atomicAdd(&ehist[threadIdx.x], se[threadIdx.x]);
+    }
+}
+
+// Vertex keys for the relabel pass and the permutation it writes.
+struct VertexSrc {
+    const uint32_t *d_out;
+    __device__ __forceinline__ bool load(uint64_t i, uint32_t &k, uint32_t &) const {
+        k = (row_bucket(d_out[i]) << VKEY_SHIFT) | (uint32_t)i;
+        return true;
+    }
+};
+struct PermDst {
+    uint32_t *perm, *iperm;
+    __device__ __forceinline__ void store(uint64_t pos, uint32_t k, uint32_t) const {
+        const uint32_t u = k & ((1u << VKEY_SHIFT) - 1u);
+        iperm[pos] = u;
+        perm[u] = (uint32_t)pos;
+    }
+};
+
+// The entry words as the unique pass wrote them, with the row replaced by its
+// position and the row's bucket on top; the pass writes them back without it.
+struct RelabelSrc {
+    const unsigned long long *e;
+    const uint32_t *d_out, *perm;
+    uint32_t umask;
+    __device__ __forceinline__ bool load(uint64_t i, unsigned long long &k, uint32_t &) const {
+        const unsigned long long w = e[i];
+        const uint32_t u = (uint32_t)w & umask;
+        k = ((unsigned long long)row_bucket(d_out[u]) << EKEY_SHIFT) | (w & ~(unsigned long long)umask) | perm[u];
+        return true;
+    }
+};
+struct ClearDst {
+    unsigned long long *e;
+    __device__ __forceinline__ void store(uint64_t pos, unsigned long long k, uint32_t) const {
+        e[pos] = k & ((1ull << EKEY_SHIFT) - 1ull);
+    }
+};
+
+// The transpose sorts the 64-bit entry words by their column (bits 58:32).
 struct EntSrc {
     const unsigned long long *e;
     __device__ __forceinline__ bool load(uint64_t i, unsigned long long &k, uint32_t &) const {
@@ -498,10 +582,12 @@ struct Layout {
     unsigned long long *ent[2];  // entry words, ping-pong
     unsigned long long *deg;
     uint32_t *shift;
+    uint32_t *row_nent;
     uint64_t *uq_status, *sc_status;
     uint32_t *ctr;                // [0] unique tiles, [1] scan tiles
     unsigned long long *dmaxkey;  // follows ctr in one control block
-    os::SortWs sort;
+    os::SortWs sort;   // the entry words: bucket pass + column passes
+    os::SortWs vsort;  // the vertices by bucket
     size_t bytes;
 };
 
@@ -516,11 +602,13 @@ inline Layout layout(void *ws, uint64_t M, uint32_t scale) {
     L.ent[1] = c.take<unsigned long long>(cap);
     L.deg = c.take<unsigned long long>(N);
     L.shift = c.take<uint32_t>(N);
+    L.row_nent = c.take<uint32_t>(N);
     L.uq_status = c.take<uint64_t>(ceil_div(cap, UQ_TILE));
     L.sc_status = c.take<uint64_t>(2 * ceil_div(N, SC_TILE));
     L.ctr = c.take<uint32_t>(4);  // two counters + the 8-byte max key
     L.dmaxkey = L.ctr ? reinterpret_cast<unsigned long long *>(L.ctr + 2) : nullptr;
     L.sort = os::carve_sort_ws(c, cap);
+    L.vsort = os::carve_sort_ws(c, N);
     L.bytes = c.size();
     return L;
 }
@@ -530,7 +618,7 @@ inline Layout layout(void *ws, uint64_t M, uint32_t scale) {
 
 using namespace pp;
 
-extern "C" pp_status pp_graph_lengths(uint64_t M, uint32_t scale, uint64_t out[9]) {
+extern "C" pp_status pp_graph_lengths(uint64_t M, uint32_t scale, uint64_t out[PP_GRAPH_ARRAYS]) {
     if (!out || scale < 1 || scale > 27 || M > (1ull << 31)) return PP_ERR_INVALID_ARG;
     const uint64_t N = 1ull << scale;
     const uint64_t cmax = (1ull << (32 - scale)) - 1;
@@ -543,6 +631,8 @@ extern "C" pp_status pp_graph_lengths(uint64_t M, uint32_t scale, uint64_t out[9
     out[6] = N;
     out[7] = N;
     out[8] = PP_INFO_LEN;
+    out[9] = N;
+    out[10] = N;
     return PP_OK;
 }
 
@@ -558,7 +648,8 @@ extern "C" pp_status pp_build_filter_normalize(const uint32_t *us, const uint32_
     if (scale < 1 || scale > 27 || M > (1ull << 31) || !g) return PP_ERR_INVALID_ARG;
     if (rule != PP_SUPERNODE_LOWEST && rule != PP_SUPERNODE_ALL_TIES) return PP_ERR_INVALID_ARG;
     if (g->scale != scale || g->M != M) return PP_ERR_INVALID_ARG;
-    if (!g->colptr || !g->rowc || !g->ovf_key || !g->ovf_cnt || !g->d_in || !g->d_out || !g->info)
+    if (!g->colptr || !g->rowc || !g->ovf_key || !g->ovf_cnt || !g->d_in || !g->d_out || !g->info || !g->perm ||
+        !g->iperm)
         return PP_ERR_INVALID_ARG;
     if (M && (!us || !vs)) return PP_ERR_INVALID_ARG;
     const k2::Layout need = k2::layout(nullptr, M, scale);
@@ -577,7 +668,9 @@ extern "C" pp_status pp_build_filter_normalize(const uint32_t *us, const uint32_
     cudaMemsetAsync(L.ctr, 0, 4 * sizeof(uint32_t), s);
     cudaMemsetAsync(L.deg, 0, (size_t)N * sizeof(unsigned long long), s);
     cudaMemsetAsync(g->d_out, 0, (size_t)N * sizeof(uint32_t), s);
+    cudaMemsetAsync(L.row_nent, 0, (size_t)N * sizeof(uint32_t), s);
     cudaMemsetAsync(L.sort.hist, 0, os::kCtlBytes, s);
+    cudaMemsetAsync(L.vsort.hist, 0, os::kCtlBytes, s);
     cudaMemsetAsync(L.uq_status, 0, ceil_div(M ? M : 1, k2::UQ_TILE) * sizeof(uint64_t), s);
     cudaMemsetAsync(L.sc_status, 0, 2 * sc_tiles * sizeof(uint64_t), s);
     cudaMemsetAsync(L.sort.status[0], 0, ceil_div(M ? M : 1, os::TILE) * os::RADIX * word, s);
@@ -592,19 +685,36 @@ extern "C" pp_status pp_build_filter_normalize(const uint32_t *us, const uint32_
         }
         const unsigned ugrid = (unsigned)std::min<uint64_t>(ceil_div(M, k2::UQ_TILE), (uint64_t)sms * uq_occ);
         const int vec = (((uintptr_t)us | (uintptr_t)vs) & 15u) == 0;
-        k2::UniqueArgs ua{us, vs, M, scale, cmax, L.ent[0], g->ovf_key, g->ovf_cnt, g->d_out, L.sort.hist, P, vec,
-                          L.uq_status, L.ctr, g->info};
+        // the column digits go to histogram slots 1..P (slot 0: the row buckets)
+        k2::UniqueArgs ua{us,       vs,         M,          scale,        cmax, L.ent[0], g->ovf_key, g->ovf_cnt,
+                          g->d_out, L.row_nent, L.sort.hist + os::RADIX, P, vec,  L.uq_status, L.ctr,     g->info};
         k2::unique_kernel<<<ugrid, k2::UQ_THREADS, 0, s>>>(ua);
         count_launch();
-        // transpose: every entry sorted by column, P passes over bits 32 .. 32+scale
+    }
+    // relabel: the vertices by row bucket (one pass), giving perm and iperm
+    const uint64_t vtiles = ceil_div(N, os::TILE);
+    const size_t vword = L.vsort.wide ? 8 : 4;
+    k2::relabel_hist_kernel<<<ngrid, 256, 0, s>>>(g->d_out, L.row_nent, N, L.vsort.hist, L.sort.hist,
+                                                  static_cast<uint32_t *>(L.vsort.status[0]),
+                                                  vtiles * os::RADIX * vword / 4);
+    count_launch();
+    os::launch_pass<uint32_t>(L.vsort, 0, 1, k2::VertexSrc{g->d_out}, k2::PermDst{g->perm, g->iperm}, nullptr, N, s,
+                              k2::VKEY_SHIFT);
+    if (M) {
         const uint64_t *n_dev = g->info + PP_INFO_NNZ0;
-        for (int p = 0; p < P; ++p) {
-            os::launch_pass<unsigned long long>(L.sort, p, P, k2::EntSrc{L.ent[p & 1]},
-                                                       k2::EntDst{L.ent[(p + 1) & 1]}, n_dev, M, s, 32);
+        const uint32_t umask = N - 1;
+        // entries into row-position order: one stable pass on the row bucket
+        os::launch_pass<unsigned long long>(L.sort, 0, P + 1, k2::RelabelSrc{L.ent[0], g->d_out, g->perm, umask},
+                                            k2::ClearDst{L.ent[1]}, n_dev, M, s, k2::EKEY_SHIFT);
+        // transpose: then stably by column, P passes over bits 32 .. 32+scale (pass p: shift 24 + 8p)
+        for (int p = 1; p <= P; ++p) {
+            os::launch_pass<unsigned long long>(L.sort, p, P + 1, k2::EntSrc{L.ent[p & 1]},
+                                                k2::EntDst{L.ent[(p + 1) & 1]}, n_dev, M, s, 24);
         }
-        sorted = L.ent[P & 1];
+        sorted = L.ent[(P + 1) & 1];
         const unsigned cgrid = (unsigned)std::min<uint64_t>(ceil_div(M, k2::CS_TILE), (uint64_t)sms * 8);
-        k2::colscan_kernel<<<cgrid, 256, 0, s>>>(sorted, g->info, scale, cmax, g->ovf_key, g->ovf_cnt, L.deg);
+        k2::colscan_kernel<<<cgrid, 256, 0, s>>>(sorted, g->info, scale, cmax, g->ovf_key, g->ovf_cnt, g->iperm,
+                                                 L.deg);
         count_launch();
     }
     k2::dmax_kernel<<<ngrid, 256, 0, s>>>(L.deg, N, g->d_in, L.dmaxkey);
@@ -614,8 +724,8 @@ extern "C" pp_status pp_build_filter_normalize(const uint32_t *us, const uint32_
     count_launch(2);
     if (M) {
         const unsigned pgrid = (unsigned)std::min<uint64_t>(ceil_div(M, 256 * k2::CP_ITEMS), (uint64_t)sms * 8);
-        k2::compact_kernel<<<pgrid, 256, 0, s>>>(sorted, g->info, scale, cmax, g->ovf_key, g->ovf_cnt, L.shift,
-                                                 g->rowc, g->d_out);
+        k2::compact_kernel<<<pgrid, 256, 0, s>>>(sorted, g->info, scale, cmax, g->ovf_key, g->ovf_cnt, g->iperm,
+                                                 L.shift, g->rowc, g->d_out);
         count_launch();
     }
     k2::finalize_kernel<<<ngrid, 256, 0, s>>>(g->d_out, N, g->inv_dout32, g->inv_dout64);

@@ -47,6 +47,7 @@ constexpr uint64_t F_AGG = 1ull << 62, F_INC = 2ull << 62;
 // One graph of the batch, as the kernels see it.
 struct BG {
     const uint32_t *colptr, *rowc;
+    const uint32_t *perm, *iperm;  // X row of vertex u is perm[u] (Kernel 2's row order)
     const uint64_t *ovf_key;
     const uint32_t *ovf_cnt;
     const uint64_t *info;
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(256) normalize_kernel(const __grid_constant__ 
             const uint64_t at = (G.row0 + i) * d.nrhs + lane;
             const float r = (float)(r0[at] / norm);
             fx_add(acc, r, 1);
-            w.x[0][at] = r * G.inv[i];
+            w.x[0][(G.row0 + __ldg(G.perm + i)) * d.nrhs + lane] = r * G.inv[i];
             if (d.iters == 0) r_out[at] = r;
         }
     }
@@ -349,11 +350,12 @@ __global__ void __launch_bounds__(THREADS) iterate_kernel(const __grid_constant_
         float *xo = x_out + G.row0 * nrhs;
         float *ro = r_out + G.row0 * nrhs;
         const uint32_t umask = (1u << G.scale) - 1u;
-        auto epi = [&](uint32_t col, float y, float invc) {
+        // column col is vertex col; its X row goes to position pos = perm[col]
+        auto epi = [&](uint32_t col, uint32_t pos, float y, float invc) {
             if (!active) return;
             const float r = cc * y + tele;
             if (LAST) ro[(uint64_t)col * nrhs + lane] = r;
-            st_hint(xo + (uint64_t)col * nrhs + lane, r * invc, keep);
+            st_hint(xo + (uint64_t)pos * nrhs + lane, r * invc, keep);
             fx_add(acc, r, E);
         };
         const uint32_t e0 = it.z;
@@ -379,14 +381,14 @@ __global__ void __launch_bounds__(THREADS) iterate_kernel(const __grid_constant_
                             uint32_t cf = wk[m] >> G.scale;
                             if (cf == G.cmax)
                                 cf = ovf_lookup(G.ovf_key, G.ovf_cnt, G.info[PP_INFO_NOVF],
-                                                ((uint64_t)(wk[m] & umask) << 32) | col);
+                                                ((uint64_t)__ldg(G.iperm + (wk[m] & umask)) << 32) | col);
                             y.add((float)cf * xv[m]);
                         }
                     }
                 }
             }
             if (nchunks == 1) {
-                epi(col, y.s, __ldg(G.inv + col));
+                epi(col, __ldg(G.perm + col), y.s, __ldg(G.inv + col));
             } else {
                 // the warp finishing the column's last chunk adds the chunk sums in order
                 if (active) w.chunk_sum[(uint64_t)item * nrhs + lane] = y.s;
@@ -401,7 +403,7 @@ __global__ void __launch_bounds__(THREADS) iterate_kernel(const __grid_constant_
                     if (active)
                         for (uint32_t q = 0; q < nchunks; ++q)
                             tot.add(__ldcg(w.chunk_sum + (uint64_t)(first + q) * nrhs + lane));
-                    epi(col, tot.s, __ldg(G.inv + col));
+                    epi(col, __ldg(G.perm + col), tot.s, __ldg(G.inv + col));
                 }
             }
         } else {
@@ -409,6 +411,7 @@ __global__ void __launch_bounds__(THREADS) iterate_kernel(const __grid_constant_
             if (lane < (int)ncol) cp[lane] = ld_stream_u32(G.colptr + c0 + lane, stream) - e0;
             if (lane == 0) cp[ncol] = nent;
             const float myinv = lane < (int)ncol ? __ldg(G.inv + c0 + lane) : 0.f;
+            const uint32_t mypos = lane < (int)ncol ? __ldg(G.perm + c0 + lane) : 0u;
             for (uint32_t k = lane; k < nent; k += 32) rowc_s[k] = ld_stream_u32(G.rowc + e0 + k, stream);
             __syncwarp();
             // entries in order; a column is finished when its last entry has been added
@@ -427,7 +430,8 @@ __global__ void __launch_bounds__(THREADS) iterate_kernel(const __grid_constant_
                 for (int m = 0; m < GATHERS; ++m) {
                     if (k + m < nent) {
                         while (k + m >= next_end) {
-                            epi(c0 + ci, y.s, __shfl_sync(0xffffffffu, myinv, ci));
+                            epi(c0 + ci, __shfl_sync(0xffffffffu, mypos, ci), y.s,
+                                __shfl_sync(0xffffffffu, myinv, ci));
                             y = KSum{0.f, 0.f};
                             ++ci;
                             next_end = cp[ci + 1];
@@ -435,13 +439,13 @@ __global__ void __launch_bounds__(THREADS) iterate_kernel(const __grid_constant_
                         uint32_t cf = wk[m] >> G.scale;
                         if (cf == G.cmax)
                             cf = ovf_lookup(G.ovf_key, G.ovf_cnt, G.info[PP_INFO_NOVF],
-                                            ((uint64_t)(wk[m] & umask) << 32) | (c0 + ci));
+                                            ((uint64_t)__ldg(G.iperm + (wk[m] & umask)) << 32) | (c0 + ci));
                         y.add((float)cf * xv[m]);
                     }
                 }
             }
             while (ci < ncol) {  // the last column, and empty columns at the end
-                epi(c0 + ci, y.s, __shfl_sync(0xffffffffu, myinv, ci));
+                epi(c0 + ci, __shfl_sync(0xffffffffu, mypos, ci), y.s, __shfl_sync(0xffffffffu, myinv, ci));
                 y = KSum{0.f, 0.f};
                 ++ci;
             }
@@ -513,7 +517,8 @@ using namespace pp;
 static bool batch_args_ok(const pp_graph *gs, uint32_t ng, uint32_t nrhs) {
     if (!gs || ng == 0 || ng > PP_BATCH_MAX_GRAPHS || nrhs == 0 || nrhs > PP_BATCH_MAX_RHS) return false;
     for (uint32_t g = 0; g < ng; ++g)
-        if (!gs[g].colptr || !gs[g].rowc || !gs[g].ovf_key || !gs[g].ovf_cnt || !gs[g].info || !gs[g].inv_dout32)
+        if (!gs[g].colptr || !gs[g].rowc || !gs[g].ovf_key || !gs[g].ovf_cnt || !gs[g].info || !gs[g].inv_dout32 ||
+            !gs[g].perm || !gs[g].iperm)
             return false;
     return true;
 }
@@ -547,6 +552,8 @@ extern "C" pp_status pp_pagerank_batched(const pp_graph *gs, uint32_t n_graphs, 
         k3b::BG &G = d.g[g];
         G.colptr = gs[g].colptr;
         G.rowc = gs[g].rowc;
+        G.perm = gs[g].perm;
+        G.iperm = gs[g].iperm;
         G.ovf_key = gs[g].ovf_key;
         G.ovf_cnt = gs[g].ovf_cnt;
         G.info = gs[g].info;

@@ -6,7 +6,9 @@
 // d_out(u), the sum over a column is sum_e count_e * x(u_e) for the vector
 // x = r .* (1/d_out), which each iteration writes for the next one: the row
 // normalisation is folded into the gathered vector and the matrix is read as
-// packed (row, count) words only.
+// packed (row position, count) words only.  x is stored in Kernel 2's row
+// order (x[perm[u]] for row u, rows grouped by degree), so the rows gathered
+// most often share cache lines; r stays in vertex order.
 //
 // Work split by column length (a degree-bucketed pull SpMV), one warp per
 // work item and no block-wide barriers, so each warp's gathers overlap other
@@ -72,6 +74,7 @@ struct Ctl {
 struct Args {
     uint32_t N, scale, cmax, iters;
     const uint32_t *colptr, *rowc;
+    const uint32_t *perm, *iperm;  // row u is stored at position perm[u]
     const uint64_t *ovf_key;
     const uint32_t *ovf_cnt;
     const uint64_t *info;
@@ -255,7 +258,7 @@ __global__ void __launch_bounds__(256) normalize_kernel(Args a, const double *r0
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += stride) {
         const TA r = (TA)(r0[i] / norm);
         fx_add(acc, r, 1);
-        x0[i] = from_acc<TS>(r * inv[i]);
+        x0[a.perm[i]] = from_acc<TS>(r * inv[i]);
         if (a.iters == 0) r_out[i] = (TO)r;
     }
     const Fx128 bt = fx_block_sum<256>(acc, s_fx);
@@ -287,10 +290,11 @@ struct Epilogue {
     TA cc, tele;
     uint64_t keep, stream;
     int E;
-    __device__ __forceinline__ void operator()(uint32_t col, TA y, TA inv_col, Fx128 &acc) const {
+    // column `col` of A is vertex col; its x goes to the row position pos = perm[col]
+    __device__ __forceinline__ void operator()(uint32_t col, uint32_t pos, TA y, TA inv_col, Fx128 &acc) const {
         const TA r = cc * y + tele;
         if (LAST) r_out[col] = (TO)r;
-        st_x(x_out + col, from_acc<TS>(r * inv_col), keep);
+        st_x(x_out + pos, from_acc<TS>(r * inv_col), keep);
         fx_add(acc, r, E);
     }
 };
@@ -302,7 +306,7 @@ __device__ __forceinline__ TA entry_product(uint32_t w, TA xv, uint32_t col, con
     uint32_t cf = w >> a.scale;
     if (cf == a.cmax) {
         const uint32_t u = w & ((1u << a.scale) - 1u);
-        cf = ovf_lookup(a.ovf_key, a.ovf_cnt, a.info[PP_INFO_NOVF], ((uint64_t)u << 32) | col);
+        cf = ovf_lookup(a.ovf_key, a.ovf_cnt, a.info[PP_INFO_NOVF], ((uint64_t)__ldg(a.iperm + u) << 32) | col);
     }
     return (TA)cf * xv;
 }
@@ -370,7 +374,7 @@ __global__ void __launch_bounds__(THREADS, MINB) iterate_kernel(Args a, const TA
             const TA y = warp_sum(part);
             if (lane == 0) {
                 if (nchunks == 1) {
-                    epi(col, y, ld_inv(inv + col, stream), acc);
+                    epi(col, __ldg(a.perm + col), y, ld_inv(inv + col, stream), acc);
                 } else {
                     // the warp finishing the column's last chunk adds the chunk sums in order
                     a.chunk_sum[item] = (double)y;
@@ -380,7 +384,7 @@ __global__ void __launch_bounds__(THREADS, MINB) iterate_kernel(Args a, const TA
                         __threadfence();
                         TA tot = TA(0);
                         for (uint32_t q = 0; q < nchunks; ++q) tot += (TA)__ldcg(a.chunk_sum + first + q);
-                        epi(col, tot, ld_inv(inv + col, stream), acc);
+                        epi(col, __ldg(a.perm + col), tot, ld_inv(inv + col, stream), acc);
                     }
                 }
             }
@@ -390,6 +394,7 @@ __global__ void __launch_bounds__(THREADS, MINB) iterate_kernel(Args a, const TA
             // column starts and 1/d_out of lane's column, in flight with the entries
             const uint32_t mycp = lane < (int)ncol ? ld_stream_u32(a.colptr + c0 + lane, stream) : 0u;
             const TA myinv = lane < (int)ncol ? ld_inv(inv + c0 + lane, stream) : TA(0);
+            const uint32_t mypos = lane < (int)ncol ? ld_stream_u32(a.perm + c0 + lane, stream) : 0u;
 #pragma unroll
             for (int g = 0; g < TILE_ENTRIES / 32; g += UNROLL) {
                 if ((uint32_t)(g * 32) >= nent) break;
@@ -443,7 +448,7 @@ __global__ void __launch_bounds__(THREADS, MINB) iterate_kernel(Args a, const TA
                 if (e - s <= a.lane_short) {
                     TA y = TA(0);
                     for (uint32_t k = s; k < e; ++k) y += prod[k];
-                    epi(c0 + lane, y, myinv, acc);
+                    epi(c0 + lane, mypos, y, myinv, acc);
                 } else {
                     medium = 1;
                 }
@@ -458,7 +463,8 @@ __global__ void __launch_bounds__(THREADS, MINB) iterate_kernel(Args a, const TA
                 for (uint32_t k = s + lane; k < e; k += 32) y += prod[k];
                 y = warp_sum(y);
                 const TA invj = __shfl_sync(0xffffffffu, myinv, j);
-                if (lane == 0) epi(c0 + j, y, invj, acc);
+                const uint32_t posj = __shfl_sync(0xffffffffu, mypos, j);
+                if (lane == 0) epi(c0 + j, posj, y, invj, acc);
             }
             __syncwarp();
         }
@@ -550,6 +556,8 @@ pp_status run_unroll(const pp_graph *g, const double *r0, uint32_t iters, double
     a.iters = iters;
     a.colptr = g->colptr;
     a.rowc = g->rowc;
+    a.perm = g->perm;
+    a.iperm = g->iperm;
     a.ovf_key = g->ovf_key;
     a.ovf_cnt = g->ovf_cnt;
     a.info = g->info;
@@ -635,7 +643,8 @@ extern "C" pp_status pp_pagerank(const pp_graph *g, const double *r0, uint32_t i
                                  void *r_out, double *r_l1, void *ws, size_t ws_bytes, void *stream) {
     if (!g || !r0 || !r_out || (int)dt < 0 || (int)dt > 2) return PP_ERR_INVALID_ARG;
     if (g->scale < 1 || g->scale > 27 || g->M > (1ull << 31) || !(c >= 0.0 && c <= 1.0)) return PP_ERR_INVALID_ARG;
-    if (!g->colptr || !g->rowc || !g->ovf_key || !g->ovf_cnt || !g->info) return PP_ERR_INVALID_ARG;
+    if (!g->colptr || !g->rowc || !g->ovf_key || !g->ovf_cnt || !g->info || !g->perm || !g->iperm)
+        return PP_ERR_INVALID_ARG;
     const k3::Layout need = k3::layout(nullptr, g->M, g->scale, iters, dt);
     pp_status st = check_ws(ws, ws_bytes, need.bytes);
     if (st != PP_OK) return st;

@@ -107,7 +107,7 @@ PipeLayout pipe_layout(void *ws, uint64_t M, uint32_t scale, uint32_t iters, pp_
     PipeLayout L;
     const uint64_t N = 1ull << scale;
     const uint64_t cap = M ? M : 1;
-    uint64_t len[9];
+    uint64_t len[PP_GRAPH_ARRAYS];
     pp_graph_lengths(M, scale, len);
     L.u = c.take<uint32_t>(cap);
     L.v = c.take<uint32_t>(cap);
@@ -125,6 +125,8 @@ PipeLayout pipe_layout(void *ws, uint64_t M, uint32_t scale, uint32_t iters, pp_
     L.g.inv_dout32 = c.take<float>(len[6]);
     L.g.inv_dout64 = c.take<double>(len[7]);
     L.g.info = c.take<uint64_t>(len[8]);
+    L.g.perm = c.take<uint32_t>(len[9]);
+    L.g.iperm = c.take<uint32_t>(len[10]);
     L.r0 = c.take<double>(N);
     L.r_out = c.take<char>(N * (dt == PP_FP64 ? 8 : 4));
     size_t b1 = 0, b2 = 0, b3 = 0;

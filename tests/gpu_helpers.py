@@ -16,14 +16,33 @@ def host_u32(t):
     return t.cpu().numpy().view(np.uint32)
 
 
+def row_buckets(u_sorted, N):
+    """Kernel 2's row order key: clz(d | 1) of each row's edge count d before
+    the filters (ascending key = descending floor(log2(d)))."""
+    d = np.bincount(u_sorted.astype(np.int64), minlength=N).astype(np.uint64)
+    return 31 - np.floor(np.log2(np.maximum(d, 1))).astype(np.int64)
+
+
+def check_row_order(g, u_sorted):
+    """perm / iperm are inverse permutations ordering the rows by bucket, then id."""
+    N = g.N
+    perm = host_u32(g.perm)[:N].astype(np.int64)
+    iperm = host_u32(g.iperm)[:N].astype(np.int64)
+    want = np.lexsort((np.arange(N), row_buckets(u_sorted, N)))
+    assert np.array_equal(iperm, want)
+    assert np.array_equal(perm[iperm], np.arange(N))
+
+
 def gpu_triples(g):
-    """(u, v, cnt) of the GPU's filtered A in (u, v) order, plus the CSC-order arrays."""
+    """(u, v, cnt) of the GPU's filtered A in (u, v) order, plus the CSC-order
+    arrays (row positions, columns, column pointers)."""
     info = g.info_dict()
     nnz, novf = info["nnz"], info["novf"]
     colptr = host_u32(g.colptr)[: g.N + 1].astype(np.int64)
     rowc = host_u32(g.rowc)[:nnz]
     assert colptr[0] == 0 and colptr[-1] == nnz and (np.diff(colptr) >= 0).all()
-    u = rowc & np.uint32((1 << g.scale) - 1)
+    pos = rowc & np.uint32((1 << g.scale) - 1)
+    u = host_u32(g.iperm)[: g.N][pos]
     cf = (rowc >> np.uint32(g.scale)).astype(np.uint64)
     v = np.repeat(np.arange(g.N, dtype=np.uint32), np.diff(colptr))
     cmax = (1 << (32 - g.scale)) - 1
@@ -36,7 +55,7 @@ def gpu_triples(g):
         assert (idx < novf).all() and (ovk[idx] == keys).all()
         cf[esc] = ovc[idx]
     order = np.lexsort((v, u))
-    return u[order], v[order], cf[order], (u, v, colptr)
+    return u[order], v[order], cf[order], (pos, v, colptr)
 
 
 def oracle_triples(R):

@@ -45,6 +45,7 @@ def test_workspace_queries_and_lengths():
     assert pp.workspace_bytes("pagerank", 16 << 10, 10, dtype="fp64") > pp.workspace_bytes("pagerank", 16 << 10, 10)
     lens = pp.graph_lengths(16 << 10, 10)
     assert lens[0] == 1025 and lens[1] == 16 << 10 and lens[4] == 1024 and lens[8] == pp.INFO_LEN
+    assert len(lens) == pp.GRAPH_ARRAYS and lens[9] == lens[10] == 1024
     # the overflow table bound: each overflow entry needs >= 2^(32-scale)-1 duplicate edges
     assert pp.graph_lengths(1 << 30, 26)[2] == (1 << 30) // 63 + 1
 
@@ -58,7 +59,7 @@ def test_host_side_argument_errors():
     assert L.pp_sort_edges_workspace(10, 28, ctypes.byref(n)) == pp.PP_ERR_INVALID_ARG
     assert L.pp_sort_edges_workspace((1 << 31) + 1, 20, ctypes.byref(n)) == pp.PP_ERR_INVALID_ARG
     assert L.pp_pagerank_workspace(10, 5, 20, 7, ctypes.byref(n)) == pp.PP_ERR_INVALID_ARG
-    out = (ctypes.c_uint64 * 9)()
+    out = (ctypes.c_uint64 * pp.GRAPH_ARRAYS)()
     assert L.pp_graph_lengths(10, 30, out) == pp.PP_ERR_INVALID_ARG
     # null pointers and missing workspace are rejected before anything is enqueued
     assert L.pp_sort_edges(None, None, 10, 5, None, None, None, 0, None) == pp.PP_ERR_INVALID_ARG

@@ -21,7 +21,7 @@ import os
 import numpy as np
 import pytest
 
-from gpu_helpers import host_u32, rank_errors
+from gpu_helpers import check_row_order, host_u32, rank_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -127,10 +127,13 @@ def test_k2_structure_bit_exact(fullsize):
     sel = keep[vs[starts]]
     want = _hashes(us[starts][sel], vs[starts][sel], runs[sel], S)
     del key, first, kept_edge, kept_entry, starts, runs, sel
-    gu, gv, gc, colptr_dev = _decode_csc(g)
+    gu, gv, gc, colptr_dev, gpos = _decode_csc(g)
     same_col = gv[1:] == gv[:-1]
-    assert bool((gu[1:][same_col] > gu[:-1][same_col]).all()), "rows not strictly ascending in a column"
+    assert bool((gpos[1:][same_col] > gpos[:-1][same_col]).all()), "row positions not ascending in a column"
     assert _hashes(gu, gv, gc, S) == want
+    del gu, gv, gc, gpos
+    # Kernel 2's row order: by bucket of the edge count before the filter, then id
+    check_row_order(g, us)
 
 
 def _decode_csc(g):
@@ -139,7 +142,8 @@ def _decode_csc(g):
     nnz, novf = info["nnz"], info["novf"]
     colptr = host_u32(g.colptr)[: g.N + 1].astype(np.int64)
     rowc = host_u32(g.rowc)[:nnz]
-    u = rowc & np.uint32(g.N - 1)
+    pos = rowc & np.uint32(g.N - 1)
+    u = host_u32(g.iperm)[: g.N][pos]
     cf = (rowc >> np.uint32(g.scale)).astype(np.uint32)
     v = np.repeat(np.arange(g.N, dtype=np.uint32), np.diff(colptr))
     esc = cf == np.uint32((1 << (32 - g.scale)) - 1)
@@ -150,7 +154,7 @@ def _decode_csc(g):
         i = np.searchsorted(ovk, k)
         assert (i < novf).all() and (ovk[i] == k).all()
         cf[esc] = ovc[i]
-    return u, v, cf, colptr
+    return u, v, cf, colptr, pos
 
 
 def test_k3_one_step_and_precisions(fullsize):
@@ -173,7 +177,7 @@ def test_k3_one_step_and_precisions(fullsize):
     assert abs(float(np.sum(r20)) - want_mass) <= 1e-12 * want_mass
 
     # Eq. 1 for sampled columns: the heaviest kept column, removed columns, random ones
-    u, v, cnt, _ = _decode_csc(g)
+    u, v, cnt, _, _ = _decode_csc(g)
     rng = np.random.default_rng(7)
     deg = np.diff(colptr)
     cols = np.unique(np.concatenate([[int(np.argmax(deg))], np.flatnonzero(deg == 0)[:50],

@@ -8,7 +8,7 @@ reported and only checked loosely (L1 <= 2e-2).
 import numpy as np
 import pytest
 
-from gpu_helpers import dev_u32, gpu_triples, host_u32, oracle_triples, rank_errors
+from gpu_helpers import check_row_order, dev_u32, gpu_triples, host_u32, oracle_triples, rank_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -46,7 +46,7 @@ def check_k2(pp, g, R):
     gu, gv, gc, (cu, cv, colptr) = gpu_triples(g)
     ou, ov, oc = oracle_triples(R)
     assert np.array_equal(gu, ou) and np.array_equal(gv, ov) and np.array_equal(gc, oc)
-    # rows strictly ascend inside each column (the compressed-column layout)
+    # row positions strictly ascend inside each column (the compressed-column layout)
     same_col = cv[1:] == cv[:-1]
     assert (cu[1:][same_col] > cu[:-1][same_col]).all()
     d = R["d_out"]
@@ -73,6 +73,7 @@ def test_pipeline_parity(pp, k0, oracle_mod, scale, M, seed):
         g = pp.build_filter_normalize(us, vs, scale, rule)
         R = oracle_mod.k2_filter(ous, ovs, N, rule)
         check_k2(pp, g, R)
+        check_row_order(g, ous)
         # Kernel 3
         want = oracle_mod.k3_pagerank(R, r0, 20, 0.85)
         for dt in ("fp64", "fp32", "bf16"):
