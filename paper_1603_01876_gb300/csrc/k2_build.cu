@@ -1,17 +1,19 @@
 // Kernel 2 (Sec. IV-C): build, filter and normalise the adjacency matrix.
 //
-//   unique_kernel    step 1: run-lengths of equal (u, v) in Kernel 1's sorted
-//                    output are the counts A(u,v); output offsets by a
-//                    decoupled look-back over tiles.  Each entry is written
-//                    as one 64-bit word (column << 32 | row | count << scale);
-//                    each row's counts (entries arrive in row order) go to
-//                    the row's out-degree before filtering, and the column
-//                    digits to the transpose's histograms.
-//   relabel          rows ordered by decreasing floor(log2(out-degree)) (a
-//                    one-pass radix sort of the vertices): perm / iperm; the
-//                    entry words take the row's position perm[u], and one
-//                    radix pass on the row's bucket puts them in position
-//                    order (the storage order Kernel 3 gathers from).
+//   stats_kernel     per row of Kernel 1's sorted output: its edges (the
+//                    out-degree before filtering) and its distinct (u, v)
+//                    pairs (entries).
+//   relabel          rows ordered by decreasing floor(log2(out-degree)),
+//                    vertex id breaking ties (a one-pass radix sort of the
+//                    vertices): perm / iperm, the storage order of the rows
+//                    that Kernel 3 gathers from; two scans give each row's
+//                    first entry in vertex order and in position order.
+//   unique_kernel    step 1: run-lengths of equal (u, v) are the counts
+//                    A(u,v); output offsets by a decoupled look-back over
+//                    tiles.  Each entry is written as one 64-bit word
+//                    (column << 32 | row position | count << scale) at its
+//                    place in row-position order, and its column digits go
+//                    to the transpose's histograms.
 //   transpose        stable LSD radix sort of the entry words by column (row
 //                    positions stay ascending inside a column).
 //   colscan_kernel   step 2: with the entries grouped by column, the entry
@@ -112,8 +114,9 @@ struct UniqueArgs {
     unsigned long long *ent;  // [nnz0] column << 32 | row | count field << scale
     uint64_t *ovf_key;
     uint32_t *ovf_cnt;
-    uint32_t *d_out;          // [N]: row sums before the filter
-    uint32_t *row_nent;       // [N]: entries per row before the filter
+    uint32_t n_vert;          // N
+    const uint32_t *delta;    // [N]: first entry of row u in position order minus in vertex order (mod 2^32)
+    const uint32_t *perm;     // [N]: row positions
     uint32_t *hist;           // [npasses * 256] column digits, for the transpose
     int npasses;
     int vec;                  // us and vs are 16-byte aligned: load 4 ids at a time
@@ -210,14 +213,24 @@ __global__ void __launch_bounds__(UQ_THREADS, 3) unique_kernel(UniqueArgs a) {
             }
         }
 
+        // Runs of an id >= N are not entries (reported; the stats pass skips them too,
+        // so row counts and entries agree and every write stays in bounds).
+        uint32_t valid = 0;
+#pragma unroll
+        for (int j = 0; j < UQ_ITEMS; ++j)
+            if ((tails >> j & 1u) && !((k[j] >> 32) >= (uint64_t)a.n_vert || (uint32_t)k[j] >= a.n_vert))
+                valid |= 1u << j;
+        if (valid != tails) pp_set_error(PP_DEV_RANGE);
         const uint64_t start0 = start;
         uint32_t nt = 0, ne = 0;
 #pragma unroll
         for (int j = 0; j < UQ_ITEMS; ++j) {
             if (tails >> j & 1u) {
-                ne += (uint32_t)(my0 + j - start + 1) >= a.cmax;
+                if (valid >> j & 1u) {
+                    ne += (uint32_t)(my0 + j - start + 1) >= a.cmax;
+                    ++nt;
+                }
                 start = my0 + j + 1;
-                ++nt;
             }
         }
         start = start0;
@@ -236,19 +249,14 @@ __global__ void __launch_bounds__(UQ_THREADS, 3) unique_kernel(UniqueArgs a) {
         const uint64_t gex = s_excl + texcl;
         uint32_t lpos = (uint32_t)texcl;  // place inside the tile's output
         uint64_t epos = (gex >> 32) & 0x3fffffffull;
-        uint32_t row = 0xffffffffu, rowsum = 0, rowent = 0;
+
 #pragma unroll
         for (int j = 0; j < UQ_ITEMS; ++j) {
             if (!(tails >> j & 1u)) continue;
-            uint32_t u = (uint32_t)(k[j] >> 32), v = (uint32_t)k[j];
-            if ((u | v) & ~umask) {
-                // an id >= N: report it and keep every later access in bounds
-                pp_set_error(PP_DEV_RANGE);
-                u &= umask;
-                v &= umask;
-            }
             const uint32_t c = (uint32_t)(my0 + j - start + 1);
             start = my0 + j + 1;
+            if (!(valid >> j & 1u)) continue;
+            const uint32_t u = (uint32_t)(k[j] >> 32), v = (uint32_t)k[j];
             const uint32_t field = c >= a.cmax ? a.cmax : c;
             s_out[lpos + lpos / 16] = ((unsigned long long)v << 32) | (u | (field << a.scale));
             if (c >= a.cmax) {
@@ -257,29 +265,19 @@ __global__ void __launch_bounds__(UQ_THREADS, 3) unique_kernel(UniqueArgs a) {
                 ++epos;
             }
             for (int p = 0; p < a.npasses; ++p) atomicAdd(&s_hist[p][(v >> (8 * p)) & (os::RADIX - 1)], 1u);
-            // this thread's entries ascend in u: add each row's run once
-            if (u != row) {
-                if (rowsum) {
-                    atomicAdd(&a.d_out[row], rowsum);
-                    atomicAdd(&a.row_nent[row], rowent);
-                }
-                row = u;
-                rowsum = 0;
-                rowent = 0;
-            }
-            rowsum += c;
-            ++rowent;
             ++lpos;
-        }
-        if (rowsum) {
-            atomicAdd(&a.d_out[row], rowsum);
-            atomicAdd(&a.row_nent[row], rowent);
         }
         __syncthreads();
         {
-            unsigned long long *dst = a.ent + (s_excl & 0xffffffffull);
+            // entry i of the tile (vertex order g = first + i) goes to g + delta[u]:
+            // a row's entries stay together, rows move to their positions
+            const uint32_t first = (uint32_t)(s_excl & 0xffffffffull);
             const uint32_t n_out = (uint32_t)total;
-            for (uint32_t i = tid; i < n_out; i += UQ_THREADS) dst[i] = s_out[i + i / 16];
+            for (uint32_t i = tid; i < n_out; i += UQ_THREADS) {
+                const unsigned long long w = s_out[i + i / 16];
+                const uint32_t u = (uint32_t)w & umask;
+                a.ent[first + i + __ldg(a.delta + u)] = (w & ~(unsigned long long)umask) | __ldg(a.perm + u);
+            }
         }
         __syncthreads();  // shared scratch is reused by the next tile
     }
@@ -287,6 +285,96 @@ __global__ void __launch_bounds__(UQ_THREADS, 3) unique_kernel(UniqueArgs a) {
     for (int i = tid; i < a.npasses * os::RADIX; i += UQ_THREADS) {
         const uint32_t c = (&s_hist[0][0])[i];
         if (c) atomicAdd(&a.hist[i], c);
+    }
+}
+
+// Edges (the out-degree before filtering) and entries (distinct (u, v)) of
+// every row, from Kernel 1's sorted output: each thread takes 16 consecutive
+// edges and adds each row's run with one atomic per array.
+__global__ void __launch_bounds__(256) stats_kernel(const uint32_t *us, const uint32_t *vs, uint64_t M,
+                                                    uint32_t umask, uint32_t *d_out, uint32_t *row_nent) {
+    constexpr int ITEMS = 16;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * ITEMS;
+    for (uint64_t i0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * ITEMS; i0 < M; i0 += stride) {
+        uint64_t k[ITEMS + 1];
+#pragma unroll
+        for (int j = 0; j <= ITEMS; ++j) k[j] = (i0 + j < M) ? edge_key(us, vs, i0 + j) : ~0ull;
+        uint32_t row = 0xffffffffu, edges = 0, entries = 0;
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            if (i0 + j >= M) break;
+            // an edge with an id >= N is no entry (the unique pass reports it)
+            if (((k[j] >> 32) | (k[j] & 0xffffffffull)) > (uint64_t)umask) continue;
+            const uint32_t u = (uint32_t)(k[j] >> 32);
+            if (u != row) {
+                if (edges) {
+                    atomicAdd(&d_out[row], edges);
+                    atomicAdd(&row_nent[row], entries);
+                }
+                row = u;
+                edges = entries = 0;
+            }
+            ++edges;
+            entries += k[j] != k[j + 1];  // a run of equal (u, v) ends here
+        }
+        if (edges) {
+            atomicAdd(&d_out[row], edges);
+            atomicAdd(&row_nent[row], entries);
+        }
+    }
+}
+
+// Exclusive scans of the rows' entry counts, in vertex order (uoff) and in
+// position order; delta[u] = (first entry of row u in position order) -
+// (first entry in vertex order), mod 2^32.  One look-back scan per kernel.
+struct OffArgs {
+    const uint32_t *row_nent;
+    const uint32_t *iperm;  // nullptr: vertex order
+    uint32_t N;
+    uint32_t *uoff;         // written in vertex order, read in position order
+    uint32_t *delta;
+    uint64_t *status;
+    uint32_t *tile_ctr;
+};
+
+__global__ void __launch_bounds__(SC_THREADS) offsets_kernel(OffArgs a) {
+    __shared__ uint32_t s_tile;
+    __shared__ uint64_t s_scan[40];
+    __shared__ uint64_t s_excl;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_tile = atomicAdd(a.tile_ctr, 1u);
+    __syncthreads();
+    const uint64_t tile = s_tile;
+    const uint64_t ntiles = (a.N + SC_TILE - 1) / SC_TILE;
+    if (tile >= ntiles) return;
+    const uint64_t p0 = tile * SC_TILE + (uint64_t)tid * SC_ITEMS;
+    uint32_t cnt[SC_ITEMS], who[SC_ITEMS];
+    uint64_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < SC_ITEMS; ++j) {
+        const uint64_t p = p0 + j;
+        who[j] = 0;
+        cnt[j] = 0;
+        if (p < a.N) {
+            who[j] = a.iperm ? a.iperm[p] : (uint32_t)p;
+            cnt[j] = a.row_nent[who[j]];
+        }
+        sum += cnt[j];
+    }
+    uint64_t total;
+    const uint64_t ex = block_exclusive_sum<uint64_t, SC_THREADS>(sum, s_scan, &total);
+    if (tid < 32) warp_tile_prefix(a.status, tile, total, &s_excl);
+    __syncthreads();
+    uint64_t run = s_excl + ex;
+#pragma unroll
+    for (int j = 0; j < SC_ITEMS; ++j) {
+        if (p0 + j < a.N) {
+            if (a.iperm)
+                a.delta[who[j]] = (uint32_t)run - a.uoff[who[j]];
+            else
+                a.uoff[who[j]] = (uint32_t)run;
+        }
+        run += cnt[j];
     }
 }
 
@@ -503,29 +591,19 @@ __global__ void __launch_bounds__(256) finalize_kernel(const uint32_t *d_out, ui
 __device__ __forceinline__ uint32_t row_bucket(uint32_t d) { return (uint32_t)__clz(d | 1u); }
 
 constexpr uint32_t VKEY_SHIFT = 27;  // vertex key: bucket << 27 | u (u < 2^27)
-constexpr uint32_t EKEY_SHIFT = 59;  // entry key: bucket in bits 63:59 above the column (< 2^27)
 
-// Histograms of the row buckets over the vertices (for the vertex pass) and
-// over the entries (for the entry pass), and pass 0's look-back words cleared.
-__global__ void __launch_bounds__(256) relabel_hist_kernel(const uint32_t *d_out, const uint32_t *row_nent,
-                                                           uint32_t N, uint32_t *vhist, uint32_t *ehist,
+// Histogram of the row buckets over the vertices (for the vertex pass), and
+// that pass's look-back words cleared.
+__global__ void __launch_bounds__(256) relabel_hist_kernel(const uint32_t *d_out, uint32_t N, uint32_t *vhist,
                                                            uint32_t *vstatus0, uint64_t vstatus_words) {
-    __shared__ uint32_t sv[32], se[32];
-    if (threadIdx.x < 32) sv[threadIdx.x] = se[threadIdx.x] = 0;
+    __shared__ uint32_t sv[32];
+    if (threadIdx.x < 32) sv[threadIdx.x] = 0;
     __syncthreads();
     const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < N; u += stride) {
-        const uint32_t b = row_bucket(d_out[u]);
-        atomicAdd(&sv[b], 1u);
-        const uint32_t ne = row_nent[u];
-        if (ne) atomicAdd(&se[b], ne);
-    }
+    for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < N; u += stride) atomicAdd(&sv[row_bucket(d_out[u])], 1u);
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < vstatus_words; i += stride) vstatus0[i] = 0;
     __syncthreads();
-    if (threadIdx.x < 32) {
-        if (sv[threadIdx.x]) atomicAdd(&vhist[threadIdx.x], sv[threadIdx.x]);
-        if (se[threadIdx.x]) atomicAdd(&ehist[threadIdx.x], se[threadIdx.x]);
-    }
+    if (threadIdx.x < 32 && sv[threadIdx.x]) atomicAdd(&vhist[threadIdx.x], sv[threadIdx.x]);
 }
 
 // Vertex keys for the relabel pass and the permutation it writes.
@@ -545,27 +623,7 @@ struct PermDst {
     }
 };
 
-// The entry words as the unique pass wrote them, with the row replaced by its
-// position and the row's bucket on top; the pass writes them back without it.
-struct RelabelSrc {
-    const unsigned long long *e;
-    const uint32_t *d_out, *perm;
-    uint32_t umask;
-    __device__ __forceinline__ bool load(uint64_t i, unsigned long long &k, uint32_t &) const {
-        const unsigned long long w = e[i];
-        const uint32_t u = (uint32_t)w & umask;
-        k = ((unsigned long long)row_bucket(d_out[u]) << EKEY_SHIFT) | (w & ~(unsigned long long)umask) | perm[u];
-        return true;
-    }
-};
-struct ClearDst {
-    unsigned long long *e;
-    __device__ __forceinline__ void store(uint64_t pos, unsigned long long k, uint32_t) const {
-        e[pos] = k & ((1ull << EKEY_SHIFT) - 1ull);
-    }
-};
-
-// The transpose sorts the 64-bit entry words by their column (bits 58:32).
+// The transpose sorts the 64-bit entry words by their column (bits 63:32).
 struct EntSrc {
     const unsigned long long *e;
     __device__ __forceinline__ bool load(uint64_t i, unsigned long long &k, uint32_t &) const {
@@ -583,8 +641,9 @@ struct Layout {
     unsigned long long *deg;
     uint32_t *shift;
     uint32_t *row_nent;
-    uint64_t *uq_status, *sc_status;
-    uint32_t *ctr;                // [0] unique tiles, [1] scan tiles
+    uint32_t *uoff, *delta;
+    uint64_t *uq_status, *sc_status, *off_status;
+    uint32_t *ctr;                // [0] unique tiles, [1] mask scan, [2] vertex-order scan, [3] position-order scan
     unsigned long long *dmaxkey;  // follows ctr in one control block
     os::SortWs sort;   // the entry words: bucket pass + column passes
     os::SortWs vsort;  // the vertices by bucket
@@ -592,6 +651,7 @@ struct Layout {
 };
 
 inline int num_passes(uint32_t scale) { return (int)ceil_div(scale, 8u); }
+constexpr int CTR_WORDS = 6;
 
 inline Layout layout(void *ws, uint64_t M, uint32_t scale) {
     Carver c(ws);
@@ -603,10 +663,13 @@ inline Layout layout(void *ws, uint64_t M, uint32_t scale) {
     L.deg = c.take<unsigned long long>(N);
     L.shift = c.take<uint32_t>(N);
     L.row_nent = c.take<uint32_t>(N);
+    L.uoff = c.take<uint32_t>(N);
+    L.delta = c.take<uint32_t>(N);
     L.uq_status = c.take<uint64_t>(ceil_div(cap, UQ_TILE));
     L.sc_status = c.take<uint64_t>(2 * ceil_div(N, SC_TILE));
-    L.ctr = c.take<uint32_t>(4);  // two counters + the 8-byte max key
-    L.dmaxkey = L.ctr ? reinterpret_cast<unsigned long long *>(L.ctr + 2) : nullptr;
+    L.off_status = c.take<uint64_t>(2 * ceil_div(N, SC_TILE));
+    L.ctr = c.take<uint32_t>(CTR_WORDS);  // four counters + the 8-byte max key
+    L.dmaxkey = L.ctr ? reinterpret_cast<unsigned long long *>(L.ctr + 4) : nullptr;
     L.sort = os::carve_sort_ws(c, cap);
     L.vsort = os::carve_sort_ws(c, N);
     L.bytes = c.size();
@@ -665,7 +728,7 @@ extern "C" pp_status pp_build_filter_normalize(const uint32_t *us, const uint32_
 
     const size_t word = L.sort.wide ? 8 : 4;
     cudaMemsetAsync(g->info, 0, PP_INFO_LEN * sizeof(uint64_t), s);
-    cudaMemsetAsync(L.ctr, 0, 4 * sizeof(uint32_t), s);
+    cudaMemsetAsync(L.ctr, 0, k2::CTR_WORDS * sizeof(uint32_t), s);
     cudaMemsetAsync(L.deg, 0, (size_t)N * sizeof(unsigned long long), s);
     cudaMemsetAsync(g->d_out, 0, (size_t)N * sizeof(uint32_t), s);
     cudaMemsetAsync(L.row_nent, 0, (size_t)N * sizeof(uint32_t), s);
@@ -673,11 +736,32 @@ extern "C" pp_status pp_build_filter_normalize(const uint32_t *us, const uint32_
     cudaMemsetAsync(L.vsort.hist, 0, os::kCtlBytes, s);
     cudaMemsetAsync(L.uq_status, 0, ceil_div(M ? M : 1, k2::UQ_TILE) * sizeof(uint64_t), s);
     cudaMemsetAsync(L.sc_status, 0, 2 * sc_tiles * sizeof(uint64_t), s);
+    cudaMemsetAsync(L.off_status, 0, 2 * sc_tiles * sizeof(uint64_t), s);
     cudaMemsetAsync(L.sort.status[0], 0, ceil_div(M ? M : 1, os::TILE) * os::RADIX * word, s);
 
     const unsigned ngrid = (unsigned)std::min<uint64_t>(ceil_div(N, 256), (uint64_t)sms * 8);
+    const uint32_t umask = N - 1;
     unsigned long long *sorted = L.ent[0];
     if (M) {
+        const unsigned sgrid = (unsigned)std::min<uint64_t>(ceil_div(M, 256 * 16), (uint64_t)sms * 8);
+        k2::stats_kernel<<<sgrid, 256, 0, s>>>(us, vs, M, umask, g->d_out, L.row_nent);
+        count_launch();
+    }
+    // relabel: the vertices by row bucket (one pass), giving perm and iperm
+    const uint64_t vtiles = ceil_div(N, os::TILE);
+    const size_t vword = L.vsort.wide ? 8 : 4;
+    k2::relabel_hist_kernel<<<ngrid, 256, 0, s>>>(g->d_out, N, L.vsort.hist, static_cast<uint32_t *>(L.vsort.status[0]),
+                                                  vtiles * os::RADIX * vword / 4);
+    count_launch();
+    os::launch_pass<uint32_t>(L.vsort, 0, 1, k2::VertexSrc{g->d_out}, k2::PermDst{g->perm, g->iperm}, nullptr, N, s,
+                              k2::VKEY_SHIFT);
+    if (M) {
+        // each row's first entry in vertex order, then in position order
+        k2::offsets_kernel<<<(unsigned)sc_tiles, k2::SC_THREADS, 0, s>>>(
+            k2::OffArgs{L.row_nent, nullptr, N, L.uoff, L.delta, L.off_status, L.ctr + 2});
+        k2::offsets_kernel<<<(unsigned)sc_tiles, k2::SC_THREADS, 0, s>>>(
+            k2::OffArgs{L.row_nent, g->iperm, N, L.uoff, L.delta, L.off_status + sc_tiles, L.ctr + 3});
+        count_launch(2);
         static int uq_occ = 0;
         if (!uq_occ) {
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&uq_occ, k2::unique_kernel, k2::UQ_THREADS, 0);
@@ -685,33 +769,18 @@ extern "C" pp_status pp_build_filter_normalize(const uint32_t *us, const uint32_
         }
         const unsigned ugrid = (unsigned)std::min<uint64_t>(ceil_div(M, k2::UQ_TILE), (uint64_t)sms * uq_occ);
         const int vec = (((uintptr_t)us | (uintptr_t)vs) & 15u) == 0;
-        // the column digits go to histogram slots 1..P (slot 0: the row buckets)
-        k2::UniqueArgs ua{us,       vs,         M,          scale,        cmax, L.ent[0], g->ovf_key, g->ovf_cnt,
-                          g->d_out, L.row_nent, L.sort.hist + os::RADIX, P, vec,  L.uq_status, L.ctr,     g->info};
+        k2::UniqueArgs ua{us,    vs,      M,       scale,       cmax, L.ent[0], g->ovf_key,  g->ovf_cnt,
+                          N,     L.delta, g->perm, L.sort.hist, P,    vec,      L.uq_status, L.ctr,
+                          g->info};
         k2::unique_kernel<<<ugrid, k2::UQ_THREADS, 0, s>>>(ua);
         count_launch();
-    }
-    // relabel: the vertices by row bucket (one pass), giving perm and iperm
-    const uint64_t vtiles = ceil_div(N, os::TILE);
-    const size_t vword = L.vsort.wide ? 8 : 4;
-    k2::relabel_hist_kernel<<<ngrid, 256, 0, s>>>(g->d_out, L.row_nent, N, L.vsort.hist, L.sort.hist,
-                                                  static_cast<uint32_t *>(L.vsort.status[0]),
-                                                  vtiles * os::RADIX * vword / 4);
-    count_launch();
-    os::launch_pass<uint32_t>(L.vsort, 0, 1, k2::VertexSrc{g->d_out}, k2::PermDst{g->perm, g->iperm}, nullptr, N, s,
-                              k2::VKEY_SHIFT);
-    if (M) {
+        // transpose: every entry sorted by column, P passes over bits 32 .. 32+scale
         const uint64_t *n_dev = g->info + PP_INFO_NNZ0;
-        const uint32_t umask = N - 1;
-        // entries into row-position order: one stable pass on the row bucket
-        os::launch_pass<unsigned long long>(L.sort, 0, P + 1, k2::RelabelSrc{L.ent[0], g->d_out, g->perm, umask},
-                                            k2::ClearDst{L.ent[1]}, n_dev, M, s, k2::EKEY_SHIFT);
-        // transpose: then stably by column, P passes over bits 32 .. 32+scale (pass p: shift 24 + 8p)
-        for (int p = 1; p <= P; ++p) {
-            os::launch_pass<unsigned long long>(L.sort, p, P + 1, k2::EntSrc{L.ent[p & 1]},
-                                                k2::EntDst{L.ent[(p + 1) & 1]}, n_dev, M, s, 24);
+        for (int p = 0; p < P; ++p) {
+            os::launch_pass<unsigned long long>(L.sort, p, P, k2::EntSrc{L.ent[p & 1]},
+                                                k2::EntDst{L.ent[(p + 1) & 1]}, n_dev, M, s, 32);
         }
-        sorted = L.ent[(P + 1) & 1];
+        sorted = L.ent[P & 1];
         const unsigned cgrid = (unsigned)std::min<uint64_t>(ceil_div(M, k2::CS_TILE), (uint64_t)sms * 8);
         k2::colscan_kernel<<<cgrid, 256, 0, s>>>(sorted, g->info, scale, cmax, g->ovf_key, g->ovf_cnt, g->iperm,
                                                  L.deg);
