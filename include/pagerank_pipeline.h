@@ -78,19 +78,20 @@ typedef enum {
  * pointers are device arrays allocated by the caller with the lengths that
  * pp_graph_lengths() returns.  Kernel 3 only reads it.
  *
- *   colptr[N+1]  column v holds entries colptr[v] .. colptr[v+1]-1;
- *                colptr[N] = nnz.
+ *   colptr[N+1]  the column of vertex v is at position p = perm[v] and holds
+ *                entries colptr[p] .. colptr[p+1]-1; colptr[N] = nnz.
  *   rowc[M]      entry e (e < nnz) packs the position perm[u] of its row u
  *                (= start vertex) in its low `scale` bits and the count
  *                A(u,v) in the high 32-scale bits; within a column the
  *                positions ascend.  A count >= 2^(32-scale)-1 is stored as the
  *                all-ones field and found in the overflow table.
- *   perm[N], iperm[N]  the order in which Kernel 3 stores the gathered
- *                vector x: rows by decreasing floor(log2(out-degree before
- *                the column filters)), ties by vertex id; perm[u] is the
- *                position of row u and iperm[p] the row at position p.  Rows
- *                gathered most often sit together, so a warp's gathers share
- *                cache lines.  (A storage order only: A, the degrees and the
+ *   perm[N], iperm[N]  the storage order of rows and columns: vertices by
+ *                decreasing floor(log2(out-degree before the column
+ *                filters)), ties by vertex id; perm[v] is the position of
+ *                vertex v and iperm[p] the vertex at position p.  Kernel 3
+ *                keeps x in this order, so the rows gathered most often sit
+ *                together and a warp's gathers share cache lines.  (A storage
+ *                order only: d_in, d_out, 1/d_out, the overflow keys and the
  *                ranks are indexed by vertex id.)
  *   ovf_key[n], ovf_cnt[n]  the overflow table: key (u << 32 | v) ascending,
  *                count; n = info[PP_INFO_NOVF] <= pp_graph_lengths()[2].

@@ -20,12 +20,15 @@
 //                    count and d_in = sum(A,1) of each column, one atomic per
 //                    run of a column inside a thread's stretch.
 //   dmax_kernel      d_in out; max(d_in) and its lowest column.
-//   mask_scan_kernel step 3: the supernode and leaf columns; two look-back
-//                    scans over the columns give the kept-entry column
-//                    pointer and the removed entries before each column.
-//   compact_kernel   step 4: kept entries move to their compacted place;
-//                    a removed entry's count comes off its row's out-degree
-//                    (d_out = sum(A,2) after the filter).
+//   mask_scan_kernel step 3: the supernode and leaf columns, and each
+//                    column's first entry in the sorted words (look-back scan).
+//   pos_scan_kernel  the column pointers of the kept entries with the
+//                    columns in storage order (vertex iperm[p] at position p;
+//                    look-back scan), so that Kernel 3 writes x in the order
+//                    it gathers it.
+//   compact_kernel   step 4: kept entries move to their column's place in
+//                    storage order; a removed entry's count comes off its
+//                    row's out-degree (d_out = sum(A,2) after the filter).
 //   finalize_kernel  1/d_out in binary32 and binary64.
 // Every pass after the unique pass streams the entries in column order, so
 // the per-column lookups are nearly sequential and no atomic is issued per
@@ -428,42 +431,44 @@ __global__ void __launch_bounds__(256) colscan_kernel(const unsigned long long *
 constexpr uint32_t KILL_BIT = 1u << 31;
 constexpr int CP_ITEMS = 4;
 
-// Step 4 over the column-sorted entries: kept entries move down by the
-// removed entries before their column; removed entries leave the out-degree.
-// shift[v] carries the removed-entry count and, in bit 31, the column's
-// removal flag.
+// Step 4 over the column-sorted entries.  vstart[v] is column v's first entry
+// in the sorted words, with the removal flag in bit 31; a kept entry moves to
+// colptr[perm[v]] + its place inside the column; a removed entry's count
+// leaves its row's out-degree.
 __global__ void __launch_bounds__(256) compact_kernel(const unsigned long long *ent, const uint64_t *info,
                                                       uint32_t scale, uint32_t cmax, const uint64_t *ovf_key,
-                                                      const uint32_t *ovf_cnt, const uint32_t *iperm,
-                                                      const uint32_t *shift, uint32_t *rowc, uint32_t *d_out) {
+                                                      const uint32_t *ovf_cnt, const uint32_t *perm,
+                                                      const uint32_t *iperm, const uint32_t *vstart,
+                                                      const uint32_t *colptr, uint32_t *rowc, uint32_t *d_out) {
     const uint64_t n = info[PP_INFO_NNZ0];
     const uint64_t novf = info[PP_INFO_NOVF];
     const uint32_t umask = (1u << scale) - 1u;
     const uint64_t step = (uint64_t)gridDim.x * 256 * CP_ITEMS;
     for (uint64_t b = (uint64_t)blockIdx.x * 256 * CP_ITEMS + threadIdx.x; b < n; b += step) {
         unsigned long long e[CP_ITEMS];
-        uint32_t sh[CP_ITEMS];
+        uint32_t sv[CP_ITEMS];
 #pragma unroll
         for (int q = 0; q < CP_ITEMS; ++q) e[q] = (b + 256 * q < n) ? ent[b + 256 * q] : 0ull;
 #pragma unroll
-        for (int q = 0; q < CP_ITEMS; ++q) sh[q] = (b + 256 * q < n) ? shift[(uint32_t)(e[q] >> 32)] : 0u;
+        for (int q = 0; q < CP_ITEMS; ++q) sv[q] = (b + 256 * q < n) ? vstart[(uint32_t)(e[q] >> 32)] : 0u;
 #pragma unroll
         for (int q = 0; q < CP_ITEMS; ++q) {
             const uint64_t i = b + 256 * q;
             if (i >= n) break;
             const uint32_t v = (uint32_t)(e[q] >> 32), w = (uint32_t)e[q];
-            if (sh[q] & KILL_BIT) {
+            if (sv[q] & KILL_BIT) {
                 const uint32_t u = iperm[w & umask];
                 uint32_t c = w >> scale;
                 if (c == cmax) c = ovf_lookup(ovf_key, ovf_cnt, novf, ((uint64_t)u << 32) | v);
                 atomicSub(&d_out[u], c);
             } else {
-                rowc[i - sh[q]] = w;
+                rowc[__ldg(colptr + __ldg(perm + v)) + ((uint32_t)i - sv[q])] = w;
             }
         }
     }
 }
 
+// d_in out; max(d_in) with the lowest vertex attaining it.
 __global__ void __launch_bounds__(256) dmax_kernel(const unsigned long long *deg, uint32_t N, uint32_t *d_in,
                                                    unsigned long long *dmaxkey) {
     unsigned long long best = 0;
@@ -482,13 +487,12 @@ __global__ void __launch_bounds__(256) dmax_kernel(const unsigned long long *deg
 }
 
 struct ScanArgs {
-    const unsigned long long *deg;
+    const unsigned long long *deg;  // entries << 32 | d_in, per vertex
     uint32_t N;
     int all_ties;
     const unsigned long long *dmaxkey;
-    uint32_t *colptr;
-    uint32_t *shift;  // removed entries in the columns before each column | KILL_BIT
-    uint64_t *status_kept, *status_gone;
+    uint32_t *vstart;  // first entry of each column in the sorted words | KILL_BIT
+    uint64_t *status;
     uint32_t *tile_ctr;
     uint64_t *info;
 };
@@ -496,9 +500,9 @@ struct ScanArgs {
 __global__ void __launch_bounds__(SC_THREADS) mask_scan_kernel(ScanArgs a) {
     __shared__ uint32_t s_tile;
     __shared__ uint64_t s_scan[40];
-    __shared__ uint64_t s_excl[2];
+    __shared__ uint64_t s_excl;
     __shared__ unsigned long long s_red[2][SC_THREADS / 32];
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x;
     if (tid == 0) s_tile = atomicAdd(a.tile_ctr, 1u);
     __syncthreads();
     const uint64_t tile = s_tile;
@@ -508,51 +512,38 @@ __global__ void __launch_bounds__(SC_THREADS) mask_scan_kernel(ScanArgs a) {
     const uint32_t dmax = (uint32_t)(key >> 32);
     const uint32_t vmax = ~(uint32_t)key;
     const uint64_t v0 = tile * SC_TILE + (uint64_t)tid * SC_ITEMS;
-    uint32_t kept[SC_ITEMS], gone[SC_ITEMS], killed = 0;
-    uint64_t sk = 0, sg = 0;
+    uint32_t ent[SC_ITEMS], killed = 0;
+    uint64_t sum = 0;
     unsigned long long ties = 0, sup = 0;
 #pragma unroll
     for (int j = 0; j < SC_ITEMS; ++j) {
         const uint64_t v = v0 + j;
-        kept[j] = gone[j] = 0;
+        ent[j] = 0;
         if (v < a.N) {
             const unsigned long long w = a.deg[v];
-            const uint32_t din = (uint32_t)w, entries = (uint32_t)(w >> 32);
+            const uint32_t din = (uint32_t)w;
+            ent[j] = (uint32_t)(w >> 32);
             const bool is_max = din == dmax && (a.all_ties || (uint32_t)v == vmax);
-            const bool kill = is_max || din == 1;
             ties += din == dmax;
             sup += is_max;
-            killed |= (uint32_t)kill << j;
-            kept[j] = kill ? 0u : entries;
-            gone[j] = kill ? entries : 0u;
-            sk += kept[j];
-            sg += gone[j];
+            killed |= (uint32_t)(is_max || din == 1) << j;
+            sum += ent[j];
         }
     }
-    uint64_t tk, tg;
-    const uint64_t ek = block_exclusive_sum<uint64_t, SC_THREADS>(sk, s_scan, &tk);
-    const uint64_t eg = block_exclusive_sum<uint64_t, SC_THREADS>(sg, s_scan, &tg);
-    // warp 0 looks back for the kept entries, warp 1 for the removed ones
-    if (warp == 0) warp_tile_prefix(a.status_kept, tile, tk, &s_excl[0]);
-    if (warp == 1) warp_tile_prefix(a.status_gone, tile, tg, &s_excl[1]);
+    uint64_t total;
+    const uint64_t ex = block_exclusive_sum<uint64_t, SC_THREADS>(sum, s_scan, &total);
+    if (tid < 32) warp_tile_prefix(a.status, tile, total, &s_excl);
     __syncthreads();
     if (tid == 0 && tile == ntiles - 1) {
-        a.colptr[a.N] = (uint32_t)(s_excl[0] + tk);
-        a.info[PP_INFO_NNZ] = s_excl[0] + tk;
         a.info[PP_INFO_DMAX] = dmax;
         a.info[PP_INFO_VMAX] = vmax;
     }
-    uint64_t rk = s_excl[0] + ek, rg = s_excl[1] + eg;
+    uint64_t run = s_excl + ex;
 #pragma unroll
     for (int j = 0; j < SC_ITEMS; ++j) {
-        const uint64_t v = v0 + j;
-        if (v < a.N) {
-            a.colptr[v] = (uint32_t)rk;
-            // a kept column with entries has fewer than 2^31 removed entries before it
-            a.shift[v] = (uint32_t)rg | ((killed >> j & 1u) ? KILL_BIT : 0u);
-        }
-        rk += kept[j];
-        rg += gone[j];
+        // every start is below nnz0 <= 2^31, so bit 31 is free for the flag
+        if (v0 + j < a.N) a.vstart[v0 + j] = (uint32_t)run | ((killed >> j & 1u) ? KILL_BIT : 0u);
+        run += ent[j];
     }
     // tie and supernode counts
 #pragma unroll
@@ -573,6 +564,55 @@ __global__ void __launch_bounds__(SC_THREADS) mask_scan_kernel(ScanArgs a) {
         }
         if (t) atomicAdd((unsigned long long *)&a.info[PP_INFO_TIES], t);
         if (s) atomicAdd((unsigned long long *)&a.info[PP_INFO_SUPERNODES], s);
+    }
+}
+
+// Column pointers of the kept entries, columns in storage order.
+struct PosArgs {
+    const unsigned long long *deg;
+    const uint32_t *iperm, *vstart;
+    uint32_t N;
+    uint32_t *colptr;
+    uint64_t *status;
+    uint32_t *tile_ctr;
+    uint64_t *info;
+};
+
+__global__ void __launch_bounds__(SC_THREADS) pos_scan_kernel(PosArgs a) {
+    __shared__ uint32_t s_tile;
+    __shared__ uint64_t s_scan[40];
+    __shared__ uint64_t s_excl;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_tile = atomicAdd(a.tile_ctr, 1u);
+    __syncthreads();
+    const uint64_t tile = s_tile;
+    const uint64_t ntiles = (a.N + SC_TILE - 1) / SC_TILE;
+    if (tile >= ntiles) return;
+    const uint64_t p0 = tile * SC_TILE + (uint64_t)tid * SC_ITEMS;
+    uint32_t kept[SC_ITEMS];
+    uint64_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < SC_ITEMS; ++j) {
+        kept[j] = 0;
+        if (p0 + j < a.N) {
+            const uint32_t v = a.iperm[p0 + j];
+            kept[j] = (a.vstart[v] & KILL_BIT) ? 0u : (uint32_t)(a.deg[v] >> 32);
+        }
+        sum += kept[j];
+    }
+    uint64_t total;
+    const uint64_t ex = block_exclusive_sum<uint64_t, SC_THREADS>(sum, s_scan, &total);
+    if (tid < 32) warp_tile_prefix(a.status, tile, total, &s_excl);
+    __syncthreads();
+    if (tid == 0 && tile == ntiles - 1) {
+        a.colptr[a.N] = (uint32_t)(s_excl + total);
+        a.info[PP_INFO_NNZ] = s_excl + total;
+    }
+    uint64_t run = s_excl + ex;
+#pragma unroll
+    for (int j = 0; j < SC_ITEMS; ++j) {
+        if (p0 + j < a.N) a.colptr[p0 + j] = (uint32_t)run;
+        run += kept[j];
     }
 }
 
@@ -639,11 +679,11 @@ struct EntDst {
 struct Layout {
     unsigned long long *ent[2];  // entry words, ping-pong
     unsigned long long *deg;
-    uint32_t *shift;
+    uint32_t *shift;  // vstart: each column's first entry in the sorted words | KILL_BIT
     uint32_t *row_nent;
     uint32_t *uoff, *delta;
     uint64_t *uq_status, *sc_status, *off_status;
-    uint32_t *ctr;                // [0] unique tiles, [1] mask scan, [2] vertex-order scan, [3] position-order scan
+    uint32_t *ctr;                // [0] unique, [1] mask scan, [2] vertex-order and [3] position-order offsets, [5] column pointers
     unsigned long long *dmaxkey;  // follows ctr in one control block
     os::SortWs sort;   // the entry words: bucket pass + column passes
     os::SortWs vsort;  // the vertices by bucket
@@ -651,7 +691,7 @@ struct Layout {
 };
 
 inline int num_passes(uint32_t scale) { return (int)ceil_div(scale, 8u); }
-constexpr int CTR_WORDS = 6;
+constexpr int CTR_WORDS = 8;  // tile counters [0..3], [5]; the 8-byte max key at [6..7]
 
 inline Layout layout(void *ws, uint64_t M, uint32_t scale) {
     Carver c(ws);
@@ -668,8 +708,8 @@ inline Layout layout(void *ws, uint64_t M, uint32_t scale) {
     L.uq_status = c.take<uint64_t>(ceil_div(cap, UQ_TILE));
     L.sc_status = c.take<uint64_t>(2 * ceil_div(N, SC_TILE));
     L.off_status = c.take<uint64_t>(2 * ceil_div(N, SC_TILE));
-    L.ctr = c.take<uint32_t>(CTR_WORDS);  // four counters + the 8-byte max key
-    L.dmaxkey = L.ctr ? reinterpret_cast<unsigned long long *>(L.ctr + 4) : nullptr;
+    L.ctr = c.take<uint32_t>(CTR_WORDS);
+    L.dmaxkey = L.ctr ? reinterpret_cast<unsigned long long *>(L.ctr + 6) : nullptr;
     L.sort = os::carve_sort_ws(c, cap);
     L.vsort = os::carve_sort_ws(c, N);
     L.bytes = c.size();
@@ -787,14 +827,15 @@ extern "C" pp_status pp_build_filter_normalize(const uint32_t *us, const uint32_
         count_launch();
     }
     k2::dmax_kernel<<<ngrid, 256, 0, s>>>(L.deg, N, g->d_in, L.dmaxkey);
-    k2::ScanArgs sa{L.deg, N, rule == PP_SUPERNODE_ALL_TIES, L.dmaxkey, g->colptr, L.shift,
-                    L.sc_status, L.sc_status + sc_tiles, L.ctr + 1, g->info};
+    k2::ScanArgs sa{L.deg, N, rule == PP_SUPERNODE_ALL_TIES, L.dmaxkey, L.shift, L.sc_status, L.ctr + 1, g->info};
     k2::mask_scan_kernel<<<(unsigned)sc_tiles, k2::SC_THREADS, 0, s>>>(sa);
-    count_launch(2);
+    k2::PosArgs pa{L.deg, g->iperm, L.shift, N, g->colptr, L.sc_status + sc_tiles, L.ctr + 5, g->info};
+    k2::pos_scan_kernel<<<(unsigned)sc_tiles, k2::SC_THREADS, 0, s>>>(pa);
+    count_launch(3);
     if (M) {
         const unsigned pgrid = (unsigned)std::min<uint64_t>(ceil_div(M, 256 * k2::CP_ITEMS), (uint64_t)sms * 8);
-        k2::compact_kernel<<<pgrid, 256, 0, s>>>(sorted, g->info, scale, cmax, g->ovf_key, g->ovf_cnt, g->iperm,
-                                                 L.shift, g->rowc, g->d_out);
+        k2::compact_kernel<<<pgrid, 256, 0, s>>>(sorted, g->info, scale, cmax, g->ovf_key, g->ovf_cnt, g->perm,
+                                                 g->iperm, L.shift, g->colptr, g->rowc, g->d_out);
         count_launch();
     }
     k2::finalize_kernel<<<ngrid, 256, 0, s>>>(g->d_out, N, g->inv_dout32, g->inv_dout64);

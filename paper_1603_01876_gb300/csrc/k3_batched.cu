@@ -47,7 +47,7 @@ constexpr uint64_t F_AGG = 1ull << 62, F_INC = 2ull << 62;
 // One graph of the batch, as the kernels see it.
 struct BG {
     const uint32_t *colptr, *rowc;
-    const uint32_t *perm, *iperm;  // X row of vertex u is perm[u] (Kernel 2's row order)
+    const uint32_t *iperm;  // vertex at storage position p (Kernel 2's order of rows and columns)
     const uint64_t *ovf_key;
     const uint32_t *ovf_cnt;
     const uint64_t *info;
@@ -67,7 +67,8 @@ struct Desc {
 };
 
 struct Ws {
-    float *x[2];               // [rows * nrhs]
+    float *x[2];               // [rows * nrhs], rows in storage order
+    float *invp;               // [rows] 1/d_out in storage order
     uint32_t *bound;           // [rows] global columns that start a work item
     uint32_t *bound_item;      // [rows] first work item of each
     uint4 *item;               // [max_items] (col | LONG_FLAG, first item, first entry, entries | chunks<<12)
@@ -171,11 +172,15 @@ __global__ void __launch_bounds__(256) normalize_kernel(const __grid_constant__ 
     Fx128 acc{0, 0};
     if (lane < (int)d.nrhs) {
         const double norm = w.norm[g * 32 + lane];
-        for (uint64_t i = r_begin + warp; i < r_end; i += WARPS) {
-            const uint64_t at = (G.row0 + i) * d.nrhs + lane;
+        for (uint64_t p = r_begin + warp; p < r_end; p += WARPS) {
+            // storage position p holds vertex v; r0 and r_out are in vertex order
+            const uint32_t v = __ldg(G.iperm + p);
+            const uint64_t at = (G.row0 + v) * d.nrhs + lane;
             const float r = (float)(r0[at] / norm);
             fx_add(acc, r, 1);
-            w.x[0][(G.row0 + __ldg(G.perm + i)) * d.nrhs + lane] = r * G.inv[i];
+            const float iv = G.inv[v];
+            if (lane == 0) w.invp[G.row0 + p] = iv;
+            w.x[0][(G.row0 + p) * d.nrhs + lane] = r * iv;
             if (d.iters == 0) r_out[at] = r;
         }
     }
@@ -350,12 +355,13 @@ __global__ void __launch_bounds__(THREADS) iterate_kernel(const __grid_constant_
         float *xo = x_out + G.row0 * nrhs;
         float *ro = r_out + G.row0 * nrhs;
         const uint32_t umask = (1u << G.scale) - 1u;
-        // column col is vertex col; its X row goes to position pos = perm[col]
-        auto epi = [&](uint32_t col, uint32_t pos, float y, float invc) {
+        const float *invp = w.invp + G.row0;
+        // col is a column position (vertex iperm[col]); r_out is in vertex order
+        auto epi = [&](uint32_t col, float y, float invc) {
             if (!active) return;
             const float r = cc * y + tele;
-            if (LAST) ro[(uint64_t)col * nrhs + lane] = r;
-            st_hint(xo + (uint64_t)pos * nrhs + lane, r * invc, keep);
+            if (LAST) ro[(uint64_t)__ldg(G.iperm + col) * nrhs + lane] = r;
+            st_hint(xo + (uint64_t)col * nrhs + lane, r * invc, keep);
             fx_add(acc, r, E);
         };
         const uint32_t e0 = it.z;
@@ -381,14 +387,15 @@ __global__ void __launch_bounds__(THREADS) iterate_kernel(const __grid_constant_
                             uint32_t cf = wk[m] >> G.scale;
                             if (cf == G.cmax)
                                 cf = ovf_lookup(G.ovf_key, G.ovf_cnt, G.info[PP_INFO_NOVF],
-                                                ((uint64_t)__ldg(G.iperm + (wk[m] & umask)) << 32) | col);
+                                                ((uint64_t)__ldg(G.iperm + (wk[m] & umask)) << 32) |
+                                                    __ldg(G.iperm + col));
                             y.add((float)cf * xv[m]);
                         }
                     }
                 }
             }
             if (nchunks == 1) {
-                epi(col, __ldg(G.perm + col), y.s, __ldg(G.inv + col));
+                epi(col, y.s, invp[col]);
             } else {
                 // the warp finishing the column's last chunk adds the chunk sums in order
                 if (active) w.chunk_sum[(uint64_t)item * nrhs + lane] = y.s;
@@ -403,15 +410,14 @@ __global__ void __launch_bounds__(THREADS) iterate_kernel(const __grid_constant_
                     if (active)
                         for (uint32_t q = 0; q < nchunks; ++q)
                             tot.add(__ldcg(w.chunk_sum + (uint64_t)(first + q) * nrhs + lane));
-                    epi(col, __ldg(G.perm + col), tot.s, __ldg(G.inv + col));
+                    epi(col, tot.s, invp[col]);
                 }
             }
         } else {
             const uint32_t c0 = it.x, ncol = it.y, nent = it.w;
             if (lane < (int)ncol) cp[lane] = ld_stream_u32(G.colptr + c0 + lane, stream) - e0;
             if (lane == 0) cp[ncol] = nent;
-            const float myinv = lane < (int)ncol ? __ldg(G.inv + c0 + lane) : 0.f;
-            const uint32_t mypos = lane < (int)ncol ? __ldg(G.perm + c0 + lane) : 0u;
+            const float myinv = lane < (int)ncol ? invp[c0 + lane] : 0.f;
             for (uint32_t k = lane; k < nent; k += 32) rowc_s[k] = ld_stream_u32(G.rowc + e0 + k, stream);
             __syncwarp();
             // entries in order; a column is finished when its last entry has been added
@@ -430,8 +436,7 @@ __global__ void __launch_bounds__(THREADS) iterate_kernel(const __grid_constant_
                 for (int m = 0; m < GATHERS; ++m) {
                     if (k + m < nent) {
                         while (k + m >= next_end) {
-                            epi(c0 + ci, __shfl_sync(0xffffffffu, mypos, ci), y.s,
-                                __shfl_sync(0xffffffffu, myinv, ci));
+                            epi(c0 + ci, y.s, __shfl_sync(0xffffffffu, myinv, ci));
                             y = KSum{0.f, 0.f};
                             ++ci;
                             next_end = cp[ci + 1];
@@ -439,13 +444,14 @@ __global__ void __launch_bounds__(THREADS) iterate_kernel(const __grid_constant_
                         uint32_t cf = wk[m] >> G.scale;
                         if (cf == G.cmax)
                             cf = ovf_lookup(G.ovf_key, G.ovf_cnt, G.info[PP_INFO_NOVF],
-                                            ((uint64_t)__ldg(G.iperm + (wk[m] & umask)) << 32) | (c0 + ci));
+                                            ((uint64_t)__ldg(G.iperm + (wk[m] & umask)) << 32) |
+                                                __ldg(G.iperm + c0 + ci));
                         y.add((float)cf * xv[m]);
                     }
                 }
             }
             while (ci < ncol) {  // the last column, and empty columns at the end
-                epi(c0 + ci, __shfl_sync(0xffffffffu, mypos, ci), y.s, __shfl_sync(0xffffffffu, myinv, ci));
+                epi(c0 + ci, y.s, __shfl_sync(0xffffffffu, myinv, ci));
                 y = KSum{0.f, 0.f};
                 ++ci;
             }
@@ -486,6 +492,7 @@ inline Layout layout(void *ws, uint32_t ng, uint64_t rows, uint64_t edges, uint3
     const uint64_t mi = max_items(ng, rows, edges);
     L.w.x[0] = c.take<float>(rows * nrhs);
     L.w.x[1] = c.take<float>(rows * nrhs);
+    L.w.invp = c.take<float>(rows);
     L.w.bound = c.take<uint32_t>(rows);
     L.w.bound_item = c.take<uint32_t>(rows);
     L.w.item = c.take<uint4>(mi);
@@ -552,7 +559,6 @@ extern "C" pp_status pp_pagerank_batched(const pp_graph *gs, uint32_t n_graphs, 
         k3b::BG &G = d.g[g];
         G.colptr = gs[g].colptr;
         G.rowc = gs[g].rowc;
-        G.perm = gs[g].perm;
         G.iperm = gs[g].iperm;
         G.ovf_key = gs[g].ovf_key;
         G.ovf_cnt = gs[g].ovf_cnt;

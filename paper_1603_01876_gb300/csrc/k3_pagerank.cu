@@ -6,9 +6,10 @@
 // d_out(u), the sum over a column is sum_e count_e * x(u_e) for the vector
 // x = r .* (1/d_out), which each iteration writes for the next one: the row
 // normalisation is folded into the gathered vector and the matrix is read as
-// packed (row position, count) words only.  x is stored in Kernel 2's row
-// order (x[perm[u]] for row u, rows grouped by degree), so the rows gathered
-// most often share cache lines; r stays in vertex order.
+// packed (row position, count) words only.  Rows and columns are in Kernel
+// 2's storage order (vertex iperm[p] at position p, grouped by degree), so x
+// is written in the order it is gathered and the rows gathered most often
+// share cache lines; r_out is written in vertex order.
 //
 // Work split by column length (a degree-bucketed pull SpMV), one warp per
 // work item and no block-wide barriers, so each warp's gathers overlap other
@@ -74,7 +75,7 @@ struct Ctl {
 struct Args {
     uint32_t N, scale, cmax, iters;
     const uint32_t *colptr, *rowc;
-    const uint32_t *perm, *iperm;  // row u is stored at position perm[u]
+    const uint32_t *iperm;  // vertex at position p
     const uint64_t *ovf_key;
     const uint32_t *ovf_cnt;
     const uint64_t *info;
@@ -242,7 +243,7 @@ __global__ void __launch_bounds__(256) setup_kernel(Args a, const double *r0) {
 // r = r0 / norm(r0,1) rounded to the working precision; x = r / d_out; and
 // sum(r) of that vector.  With iters == 0 the normalised r is the result.
 template <typename TS, typename TA, typename TO>
-__global__ void __launch_bounds__(256) normalize_kernel(Args a, const double *r0, const TA *inv, TS *x0,
+__global__ void __launch_bounds__(256) normalize_kernel(Args a, const double *r0, const TA *inv, TA *invp, TS *x0,
                                                         TO *r_out) {
     __shared__ double s_norm;
     __shared__ uint64_t s_fx[16];
@@ -255,11 +256,15 @@ __global__ void __launch_bounds__(256) normalize_kernel(Args a, const double *r0
     const double norm = s_norm;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     Fx128 acc{0, 0};
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += stride) {
-        const TA r = (TA)(r0[i] / norm);
+    // in storage order: position p holds vertex iperm[p]; 1/d_out is copied into that order too
+    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.N; p += stride) {
+        const uint32_t v = a.iperm[p];
+        const TA r = (TA)(r0[v] / norm);
         fx_add(acc, r, 1);
-        x0[a.perm[i]] = from_acc<TS>(r * inv[i]);
-        if (a.iters == 0) r_out[i] = (TO)r;
+        const TA iv = inv[v];
+        invp[p] = iv;
+        x0[p] = from_acc<TS>(r * iv);
+        if (a.iters == 0) r_out[v] = (TO)r;
     }
     const Fx128 bt = fx_block_sum<256>(acc, s_fx);
     if (threadIdx.x == 0 && (bt.hi | bt.lo)) fx_atomic_add(a.acc, bt);
@@ -290,11 +295,12 @@ struct Epilogue {
     TA cc, tele;
     uint64_t keep, stream;
     int E;
-    // column `col` of A is vertex col; its x goes to the row position pos = perm[col]
-    __device__ __forceinline__ void operator()(uint32_t col, uint32_t pos, TA y, TA inv_col, Fx128 &acc) const {
+    const uint32_t *iperm;
+    // col is a column position (vertex iperm[col])
+    __device__ __forceinline__ void operator()(uint32_t col, TA y, TA inv_col, Fx128 &acc) const {
         const TA r = cc * y + tele;
-        if (LAST) r_out[col] = (TO)r;
-        st_x(x_out + pos, from_acc<TS>(r * inv_col), keep);
+        if (LAST) r_out[__ldg(iperm + col)] = (TO)r;
+        st_x(x_out + col, from_acc<TS>(r * inv_col), keep);
         fx_add(acc, r, E);
     }
 };
@@ -306,7 +312,8 @@ __device__ __forceinline__ TA entry_product(uint32_t w, TA xv, uint32_t col, con
     uint32_t cf = w >> a.scale;
     if (cf == a.cmax) {
         const uint32_t u = w & ((1u << a.scale) - 1u);
-        cf = ovf_lookup(a.ovf_key, a.ovf_cnt, a.info[PP_INFO_NOVF], ((uint64_t)__ldg(a.iperm + u) << 32) | col);
+        cf = ovf_lookup(a.ovf_key, a.ovf_cnt, a.info[PP_INFO_NOVF],
+                        ((uint64_t)__ldg(a.iperm + u) << 32) | __ldg(a.iperm + col));
     }
     return (TA)cf * xv;
 }
@@ -333,8 +340,8 @@ __global__ void __launch_bounds__(THREADS, MINB) iterate_kernel(Args a, const TA
     if (blockIdx.x == 0 && threadIdx.x == 0) a.fx_exp[iter + 1] = E;
     const uint32_t umask = (1u << a.scale) - 1u;
     const uint64_t keep = policy_evict_last(), stream = policy_evict_first();
-    const Epilogue<TS, TA, TO, LAST> epi{inv, x_out, r_out, (TA)a.c, (TA)(((1.0 - a.c) / (double)a.N) * S),
-                                         keep, stream, E};
+    const Epilogue<TS, TA, TO, LAST> epi{inv,  x_out,  r_out, (TA)a.c, (TA)(((1.0 - a.c) / (double)a.N) * S),
+                                         keep, stream, E,     a.iperm};
     TA *prod = s_prod[warp];
     uint32_t *cp = s_cp[warp];
     Fx128 acc{0, 0};
@@ -374,7 +381,7 @@ __global__ void __launch_bounds__(THREADS, MINB) iterate_kernel(Args a, const TA
             const TA y = warp_sum(part);
             if (lane == 0) {
                 if (nchunks == 1) {
-                    epi(col, __ldg(a.perm + col), y, ld_inv(inv + col, stream), acc);
+                    epi(col, y, ld_inv(inv + col, stream), acc);
                 } else {
                     // the warp finishing the column's last chunk adds the chunk sums in order
                     a.chunk_sum[item] = (double)y;
@@ -384,7 +391,7 @@ __global__ void __launch_bounds__(THREADS, MINB) iterate_kernel(Args a, const TA
                         __threadfence();
                         TA tot = TA(0);
                         for (uint32_t q = 0; q < nchunks; ++q) tot += (TA)__ldcg(a.chunk_sum + first + q);
-                        epi(col, __ldg(a.perm + col), tot, ld_inv(inv + col, stream), acc);
+                        epi(col, tot, ld_inv(inv + col, stream), acc);
                     }
                 }
             }
@@ -394,7 +401,6 @@ __global__ void __launch_bounds__(THREADS, MINB) iterate_kernel(Args a, const TA
             // column starts and 1/d_out of lane's column, in flight with the entries
             const uint32_t mycp = lane < (int)ncol ? ld_stream_u32(a.colptr + c0 + lane, stream) : 0u;
             const TA myinv = lane < (int)ncol ? ld_inv(inv + c0 + lane, stream) : TA(0);
-            const uint32_t mypos = lane < (int)ncol ? ld_stream_u32(a.perm + c0 + lane, stream) : 0u;
 #pragma unroll
             for (int g = 0; g < TILE_ENTRIES / 32; g += UNROLL) {
                 if ((uint32_t)(g * 32) >= nent) break;
@@ -448,7 +454,7 @@ __global__ void __launch_bounds__(THREADS, MINB) iterate_kernel(Args a, const TA
                 if (e - s <= a.lane_short) {
                     TA y = TA(0);
                     for (uint32_t k = s; k < e; ++k) y += prod[k];
-                    epi(c0 + lane, mypos, y, myinv, acc);
+                    epi(c0 + lane, y, myinv, acc);
                 } else {
                     medium = 1;
                 }
@@ -463,8 +469,7 @@ __global__ void __launch_bounds__(THREADS, MINB) iterate_kernel(Args a, const TA
                 for (uint32_t k = s + lane; k < e; k += 32) y += prod[k];
                 y = warp_sum(y);
                 const TA invj = __shfl_sync(0xffffffffu, myinv, j);
-                const uint32_t posj = __shfl_sync(0xffffffffu, mypos, j);
-                if (lane == 0) epi(c0 + j, posj, y, invj, acc);
+                if (lane == 0) epi(c0 + j, y, invj, acc);
             }
             __syncwarp();
         }
@@ -502,6 +507,7 @@ __global__ void __launch_bounds__(256) l1_scale_kernel(const TO *r, uint32_t N, 
 
 struct Layout {
     void *x[2];
+    void *invp;  // 1/d_out in storage order (TA)
     uint32_t *bound, *bound_item;
     uint4 *item;
     double *chunk_sum;
@@ -523,6 +529,7 @@ inline Layout layout(void *ws, uint64_t M, uint32_t scale, uint32_t iters, pp_dt
     const size_t xs = dt == PP_FP64 ? 8 : (dt == PP_FP32 ? 4 : 2);
     L.x[0] = c.take<char>(N * xs);
     L.x[1] = c.take<char>(N * xs);
+    L.invp = c.take<char>(N * (dt == PP_FP64 ? 8 : 4));
     L.bound = c.take<uint32_t>(N);
     L.bound_item = c.take<uint32_t>(N);
     L.item = c.take<uint4>(max_items);
@@ -556,7 +563,6 @@ pp_status run_unroll(const pp_graph *g, const double *r0, uint32_t iters, double
     a.iters = iters;
     a.colptr = g->colptr;
     a.rowc = g->rowc;
-    a.perm = g->perm;
     a.iperm = g->iperm;
     a.ovf_key = g->ovf_key;
     a.ovf_cnt = g->ovf_cnt;
@@ -584,7 +590,8 @@ pp_status run_unroll(const pp_graph *g, const double *r0, uint32_t iters, double
     setup_kernel<<<SETUP_BLOCKS, 256, 0, s>>>(a, r0);
     plan_kernel<<<(unsigned)ceil_div(N, PLAN_TILE), PLAN_THREADS, 0, s>>>(a);
     plan_items_kernel<<<(unsigned)std::min<uint64_t>(ceil_div(N, 256), 4096), 256, 0, s>>>(a);
-    normalize_kernel<TS, TA, TO><<<SETUP_BLOCKS, 256, 0, s>>>(a, r0, inv, x0, r_out);
+    TA *invp = static_cast<TA *>(L.invp);  // 1/d_out in storage order
+    normalize_kernel<TS, TA, TO><<<SETUP_BLOCKS, 256, 0, s>>>(a, r0, inv, invp, x0, r_out);
     count_launch(4);
 
     static const int o_mid = occupancy(iterate_kernel<TS, TA, TO, false, UNROLL, MINB>);
@@ -594,11 +601,11 @@ pp_status run_unroll(const pp_graph *g, const double *r0, uint32_t iters, double
         const TS *xin = (it & 1) ? x1 : x0;
         TS *xout = (it & 1) ? x0 : x1;
         if (it + 1 == iters)
-            iterate_kernel<TS, TA, TO, true, UNROLL, MINB><<<sms * o_last, THREADS, 0, s>>>(a, inv, xin, xout, r_out,
-                                                                                         it);
+            iterate_kernel<TS, TA, TO, true, UNROLL, MINB><<<sms * o_last, THREADS, 0, s>>>(a, invp, xin, xout,
+                                                                                         r_out, it);
         else
-            iterate_kernel<TS, TA, TO, false, UNROLL, MINB><<<sms * o_mid, THREADS, 0, s>>>(a, inv, xin, xout, r_out,
-                                                                                          it);
+            iterate_kernel<TS, TA, TO, false, UNROLL, MINB><<<sms * o_mid, THREADS, 0, s>>>(a, invp, xin, xout,
+                                                                                          r_out, it);
         count_launch();
     }
     if (r_l1) {

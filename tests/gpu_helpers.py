@@ -35,16 +35,18 @@ def check_row_order(g, u_sorted):
 
 def gpu_triples(g):
     """(u, v, cnt) of the GPU's filtered A in (u, v) order, plus the CSC-order
-    arrays (row positions, columns, column pointers)."""
+    arrays (row positions, column positions, column pointers)."""
     info = g.info_dict()
     nnz, novf = info["nnz"], info["novf"]
     colptr = host_u32(g.colptr)[: g.N + 1].astype(np.int64)
     rowc = host_u32(g.rowc)[:nnz]
     assert colptr[0] == 0 and colptr[-1] == nnz and (np.diff(colptr) >= 0).all()
+    iperm = host_u32(g.iperm)[: g.N]
     pos = rowc & np.uint32((1 << g.scale) - 1)
-    u = host_u32(g.iperm)[: g.N][pos]
+    u = iperm[pos]
     cf = (rowc >> np.uint32(g.scale)).astype(np.uint64)
-    v = np.repeat(np.arange(g.N, dtype=np.uint32), np.diff(colptr))
+    cpos = np.repeat(np.arange(g.N, dtype=np.uint32), np.diff(colptr))  # column positions
+    v = iperm[cpos]
     cmax = (1 << (32 - g.scale)) - 1
     esc = cf == cmax
     if esc.any():
@@ -55,7 +57,7 @@ def gpu_triples(g):
         assert (idx < novf).all() and (ovk[idx] == keys).all()
         cf[esc] = ovc[idx]
     order = np.lexsort((v, u))
-    return u[order], v[order], cf[order], (pos, v, colptr)
+    return u[order], v[order], cf[order], (pos, cpos, colptr)
 
 
 def oracle_triples(R):

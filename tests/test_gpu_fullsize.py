@@ -118,8 +118,12 @@ def test_k2_structure_bit_exact(fullsize):
         inv64 = np.where(d_out > 0, 1.0 / d_out.astype(np.float64), 0.0)
     np.testing.assert_array_equal(g.inv_dout32.cpu().numpy()[:N].view(np.uint32), inv32.view(np.uint32))
     np.testing.assert_array_equal(g.inv_dout64.cpu().numpy()[:N].view(np.uint64), inv64.view(np.uint64))
-    colptr = np.concatenate([[0], np.cumsum(np.bincount(vs[kept_entry], minlength=N))])
-    np.testing.assert_array_equal(host_u32(g.colptr)[:N + 1].astype(np.int64), colptr)
+    # columns are stored in position order: vertex v at perm[v]
+    per_col = np.bincount(vs[kept_entry], minlength=N)
+    perm = host_u32(g.perm)[:N].astype(np.int64)
+    gcp = host_u32(g.colptr)[:N + 1].astype(np.int64)
+    assert gcp[0] == 0 and gcp[N] == info["nnz"]
+    np.testing.assert_array_equal(gcp[perm + 1] - gcp[perm], per_col)
 
     # the entry set, through hashes of (u, v) and of (u, v) weighted by the count
     starts = np.flatnonzero(first)
@@ -128,7 +132,7 @@ def test_k2_structure_bit_exact(fullsize):
     want = _hashes(us[starts][sel], vs[starts][sel], runs[sel], S)
     del key, first, kept_edge, kept_entry, starts, runs, sel
     gu, gv, gc, colptr_dev, gpos = _decode_csc(g)
-    same_col = gv[1:] == gv[:-1]
+    same_col = gv[1:] == gv[:-1]  # same vertex <=> same column position
     assert bool((gpos[1:][same_col] > gpos[:-1][same_col]).all()), "row positions not ascending in a column"
     assert _hashes(gu, gv, gc, S) == want
     del gu, gv, gc, gpos
@@ -137,15 +141,18 @@ def test_k2_structure_bit_exact(fullsize):
 
 
 def _decode_csc(g):
-    """(u, v, count) of every kept entry in column order (test-side decode)."""
+    """(u, v, count) of every kept entry in storage order, the column
+    pointers (by column position) and the row positions (test-side decode)."""
     info = g.info_dict()
     nnz, novf = info["nnz"], info["novf"]
     colptr = host_u32(g.colptr)[: g.N + 1].astype(np.int64)
     rowc = host_u32(g.rowc)[:nnz]
+    iperm = host_u32(g.iperm)[: g.N]
     pos = rowc & np.uint32(g.N - 1)
-    u = host_u32(g.iperm)[: g.N][pos]
+    u = iperm[pos]
     cf = (rowc >> np.uint32(g.scale)).astype(np.uint32)
-    v = np.repeat(np.arange(g.N, dtype=np.uint32), np.diff(colptr))
+    cpos = np.repeat(np.arange(g.N, dtype=np.uint32), np.diff(colptr))
+    v = iperm[cpos]
     esc = cf == np.uint32((1 << (32 - g.scale)) - 1)
     if esc.any():
         ovk = g.ovf_key.cpu().numpy().view(np.uint64)[:novf]
@@ -169,6 +176,7 @@ def test_k3_one_step_and_precisions(fullsize):
     assert pp.last_device_error() == 0
 
     colptr = host_u32(g.colptr)[:N + 1].astype(np.int64)
+    perm = host_u32(g.perm)[:N].astype(np.int64)
     d_out = host_u32(g.d_out)[:N]
     inv64 = g.inv_dout64.cpu().numpy()[:N]
     S19 = float(np.sum(r19))
@@ -179,13 +187,13 @@ def test_k3_one_step_and_precisions(fullsize):
     # Eq. 1 for sampled columns: the heaviest kept column, removed columns, random ones
     u, v, cnt, _, _ = _decode_csc(g)
     rng = np.random.default_rng(7)
-    deg = np.diff(colptr)
+    deg = (colptr[perm + 1] - colptr[perm])  # entries of each vertex's column
     cols = np.unique(np.concatenate([[int(np.argmax(deg))], np.flatnonzero(deg == 0)[:50],
                                      rng.integers(0, N, 4000)]))
     x = r19 * inv64
     tele = (1 - C) / N * S19
     for col in cols:
-        a, b = colptr[col], colptr[col + 1]
+        a, b = colptr[perm[col]], colptr[perm[col] + 1]
         y = float(np.dot(cnt[a:b].astype(np.float64), x[u[a:b]]))
         want = C * y + tele
         assert abs(r20[col] - want) <= 1e-12 * want, (int(col), r20[col], want)
