@@ -295,13 +295,28 @@ __global__ void __launch_bounds__(UQ_THREADS, 3) unique_kernel(UniqueArgs a) {
 // every row, from Kernel 1's sorted output: each thread takes 16 consecutive
 // edges and adds each row's run with one atomic per array.
 __global__ void __launch_bounds__(256) stats_kernel(const uint32_t *us, const uint32_t *vs, uint64_t M,
-                                                    uint32_t umask, uint32_t *d_out, uint32_t *row_nent) {
+                                                    uint32_t umask, int vec, uint32_t *d_out, uint32_t *row_nent) {
     constexpr int ITEMS = 16;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * ITEMS;
     for (uint64_t i0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * ITEMS; i0 < M; i0 += stride) {
         uint64_t k[ITEMS + 1];
+        if (vec && i0 + ITEMS <= M) {
+            // 16-byte loads (i0 is a multiple of 16 elements)
+            const uint4 *pu = reinterpret_cast<const uint4 *>(us + i0);
+            const uint4 *pv = reinterpret_cast<const uint4 *>(vs + i0);
 #pragma unroll
-        for (int j = 0; j <= ITEMS; ++j) k[j] = (i0 + j < M) ? edge_key(us, vs, i0 + j) : ~0ull;
+            for (int q = 0; q < ITEMS / 4; ++q) {
+                const uint4 x = __ldg(pu + q), y = __ldg(pv + q);
+                k[4 * q + 0] = ((uint64_t)x.x << 32) | y.x;
+                k[4 * q + 1] = ((uint64_t)x.y << 32) | y.y;
+                k[4 * q + 2] = ((uint64_t)x.z << 32) | y.z;
+                k[4 * q + 3] = ((uint64_t)x.w << 32) | y.w;
+            }
+            k[ITEMS] = (i0 + ITEMS < M) ? edge_key(us, vs, i0 + ITEMS) : ~0ull;
+        } else {
+#pragma unroll
+            for (int j = 0; j <= ITEMS; ++j) k[j] = (i0 + j < M) ? edge_key(us, vs, i0 + j) : ~0ull;
+        }
         uint32_t row = 0xffffffffu, edges = 0, entries = 0;
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
@@ -784,7 +799,8 @@ extern "C" pp_status pp_build_filter_normalize(const uint32_t *us, const uint32_
     unsigned long long *sorted = L.ent[0];
     if (M) {
         const unsigned sgrid = (unsigned)std::min<uint64_t>(ceil_div(M, 256 * 16), (uint64_t)sms * 8);
-        k2::stats_kernel<<<sgrid, 256, 0, s>>>(us, vs, M, umask, g->d_out, L.row_nent);
+        const int vec = (((uintptr_t)us | (uintptr_t)vs) & 15u) == 0;
+        k2::stats_kernel<<<sgrid, 256, 0, s>>>(us, vs, M, umask, vec, g->d_out, L.row_nent);
         count_launch();
     }
     // relabel: the vertices by row bucket (one pass), giving perm and iperm
