@@ -42,7 +42,7 @@ WORKLOAD = ("Kronecker graph, scale 24 (N=2^24, M=16N=268,435,456 edges, initiat
 # DRAM bytes (read + write) per launch of each stage's dominant kernel from
 # one ncu capture (profiles/), valid while its source file is unchanged.
 TRAFFIC = {
-    "k3_pagerank": {"source": "paper_1603_01876_gb300/csrc/k3_pagerank.cu", "sha": "45f2d61e62aa3802", "bytes_per_launch": 2086587000 + 80691712,
+    "k3_pagerank": {"source": "paper_1603_01876_gb300/csrc/k3_pagerank.cu", "sha": "bf061987f2519d59", "bytes_per_launch": 1398614000 + 20113152,
                     "dtype": "fp32", "scale": 24, "capture": "profiles/k3_iterate_fp32_scale24.md"},
 }
 
