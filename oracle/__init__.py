@@ -34,7 +34,9 @@ class Oracle:
         L.oracle_k1_sort.argtypes = [vp, vp, u64, vp, vp]
         L.oracle_k2_filter.argtypes = [vp, vp, u64, u32, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp]
         L.oracle_k3_pagerank.argtypes = [u32, vp, vp, vp, vp, u32, ctypes.c_double, vp, vp]
-        for f in (L.oracle_k1_sort, L.oracle_k2_filter, L.oracle_k3_pagerank):
+        L.oracle_k3_pagerank_ex.argtypes = [u32, vp, vp, vp, vp, u32, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                            vp, vp]
+        for f in (L.oracle_k1_sort, L.oracle_k2_filter, L.oracle_k3_pagerank, L.oracle_k3_pagerank_ex):
             f.restype = ctypes.c_int
         self.lib = L
 
@@ -91,6 +93,24 @@ class Oracle:
             raise MemoryError("oracle_k3_pagerank failed")
         return (r, sums) if want_sums else r
 
+    def k3_pagerank_ex(self, A, r0, iters=20, c=0.85, dangling=False, tol=0.0):
+        """Kernel 3 with the dangling-node term and/or the convergence test;
+        returns (r, iterations run)."""
+        N = A["N"]
+        r0 = np.ascontiguousarray(r0, dtype=np.float64)
+        assert len(r0) == N
+        rowptr = np.ascontiguousarray(A["rowptr"], dtype=np.uint64)
+        col = np.ascontiguousarray(A["col"], dtype=np.uint32)
+        val = np.ascontiguousarray(A["val"], dtype=np.float64)
+        r = np.empty(N, dtype=np.float64)
+        done = ctypes.c_uint32(0)
+        rc = self.lib.oracle_k3_pagerank_ex(N, rowptr.ctypes.data, col.ctypes.data if len(col) else None,
+                                            val.ctypes.data if len(val) else None, r0.ctypes.data, iters, c,
+                                            1 if dangling else 0, float(tol), r.ctypes.data, ctypes.byref(done))
+        if rc != 0:
+            raise MemoryError("oracle_k3_pagerank_ex failed")
+        return r, int(done.value)
+
     def pipeline(self, u, v, scale, r0, iters=20, c=0.85, rule="lowest"):
         """Kernels 1-3 in order, each finished before the next starts."""
         N = 1 << scale
@@ -120,6 +140,10 @@ def k2_filter(u, v, N, rule="lowest"):
 
 def k3_pagerank(A, r0, iters=20, c=0.85, want_sums=False):
     return default().k3_pagerank(A, r0, iters, c, want_sums)
+
+
+def k3_pagerank_ex(A, r0, iters=20, c=0.85, dangling=False, tol=0.0):
+    return default().k3_pagerank_ex(A, r0, iters, c, dangling, tol)
 
 
 def pipeline(u, v, scale, r0, iters=20, c=0.85, rule="lowest"):

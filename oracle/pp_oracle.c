@@ -21,6 +21,10 @@
  *  - Kernel 3 keeps the 1/N of the teleport term: the update is
  *    r <- (c r) A + ((1-c)/N) sum(r), as in its first form and the appendix;
  *    the "simplified" form printed without the /N is read as a misprint.
+ *  - The variants (oracle_k3_pagerank_ex): the dangling-node term the paper
+ *    omits spreads the mass of rows without entries evenly, scaled by c
+ *    (the usual uniform correction); the convergence test is the L1 norm of
+ *    the difference of consecutive iterates against an absolute tolerance.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -212,5 +216,63 @@ int oracle_k3_pagerank(uint32_t N, const uint64_t *rowptr, const uint32_t *col, 
     }
     if (sums) sums[iters] = sum_compensated(r, N);
     free(y);
+    return 0;
+}
+
+/* Kernel 3 variants beyond the paper's fixed iteration count (Sec. IV-D):
+ *   dangling != 0  the mass of the rows without entries (the dangling nodes
+ *                  Sec. IV-C and IV-D leave out) is spread evenly over all
+ *                  vertices: with D = sum of r over those rows,
+ *                  r' = c*(r*A) + c*D/N + (1-c)*sum(r)/N;
+ *   tol > 0        stop after the first iteration k with
+ *                  norm(r_k - r_(k-1), 1) < tol (the convergence test Sec.
+ *                  IV-D describes), running at most `iters` iterations.
+ * With dangling == 0 and tol <= 0 this is oracle_k3_pagerank.  *iters_done
+ * receives the number of iterations run. */
+int oracle_k3_pagerank_ex(uint32_t N, const uint64_t *rowptr, const uint32_t *col, const double *val,
+                          const double *r0, uint32_t iters, double c, int dangling, double tol, double *r_out,
+                          uint32_t *iters_done) {
+    if (N == 0 || !iters_done) return -1;
+    double *r = r_out;
+    double *y = (double *)malloc((size_t)N * sizeof(double));
+    double *tmp = (double *)malloc((size_t)N * sizeof(double));
+    if (!y || !tmp) {
+        free(y); free(tmp);
+        return -1;
+    }
+    for (uint32_t i = 0; i < N; ++i) tmp[i] = abs_d(r0[i]);
+    double norm1 = sum_compensated(tmp, N);
+    for (uint32_t i = 0; i < N; ++i) r[i] = r0[i] / norm1;
+
+    double a = (1.0 - c) / (double)N;
+    uint32_t done = iters;
+    for (uint32_t it = 0; it < iters; ++it) {
+        double s = sum_compensated(r, N);
+        double dmass = 0.0;
+        if (dangling) {
+            uint32_t n = 0;
+            for (uint32_t uu = 0; uu < N; ++uu)
+                if (rowptr[uu] == rowptr[uu + 1]) tmp[n++] = r[uu];
+            dmass = sum_compensated(tmp, n);
+        }
+        memset(y, 0, (size_t)N * sizeof(double));
+        for (uint32_t uu = 0; uu < N; ++uu) {
+            double cr = c * r[uu];
+            for (uint64_t e = rowptr[uu]; e < rowptr[uu + 1]; ++e) y[col[e]] += cr * val[e];
+        }
+        double spread = c * dmass / (double)N;
+        for (uint32_t vv = 0; vv < N; ++vv) {
+            double rn = y[vv] + spread + a * s;
+            tmp[vv] = abs_d(rn - r[vv]);
+            r[vv] = rn;
+        }
+        if (tol > 0.0 && sum_compensated(tmp, N) < tol) {
+            done = it + 1;
+            break;
+        }
+    }
+    *iters_done = done;
+    free(y);
+    free(tmp);
     return 0;
 }

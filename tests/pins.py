@@ -265,8 +265,94 @@ def check_k3_mass_balance(O, u, v, N, seed=0, iters=6, c=0.85):
         prev = r
 
 
+def google_dangling_matrix(A, c):
+    """Dense Google matrix with the dangling rows made uniform before damping:
+    G = c (A + d 1'/N)' + (1-c)/N, d the indicator of rows without entries.
+    Every column of G sums to 1 (a stochastic matrix)."""
+    N = A.shape[0]
+    S = A.copy()
+    S[A.sum(axis=1) == 0, :] = 1.0 / N
+    return c * S.T + (1.0 - c) / N * np.ones((N, N))
+
+
+def check_k3ex_dense_dangling(O, seed=0):
+    """The dangling-node variant against the dense stochastic Google matrix."""
+    for k, (N, M) in enumerate([(8, 6), (16, 20), (64, 120), (128, 300)]):
+        u, v = random_edges(N, M, seed + 17 * k, hub_bias=0.3)
+        R = O.k2_filter(u, v, N, "lowest")
+        A, _, _ = dense_kernel2(u, v, N, "lowest")
+        assert (A.sum(axis=1) == 0).sum() >= 2, "the case must have dangling rows"
+        r0 = np.random.default_rng(seed + k).random(N) + 0.01
+        for c in (0.85, 0.5):
+            G = google_dangling_matrix(A, c)
+            want = r0 / np.abs(r0).sum()
+            for _ in range(20):
+                want = G @ want
+            got, done = O.k3_pagerank_ex(R, r0, 20, c, dangling=True)
+            assert done == 20
+            assert np.abs(got - want).sum() <= 1e-13 * np.abs(want).sum()
+
+
+def check_k3ex_conservation(O, seed=0):
+    """With the dangling term every row of the update passes all its mass on,
+    so sum(r) stays 1 at every iteration, for every graph (also when columns
+    are removed: the removed columns' entries are gone before d_out is taken)."""
+    for k, (N, M) in enumerate([(32, 200), (256, 1500)]):
+        u, v = random_edges(N, M, seed + 7 * k, hub_bias=0.4)
+        for rule in ("lowest", "all_ties"):
+            R = O.k2_filter(u, v, N, rule)
+            r0 = np.random.default_rng(seed + k).random(N) + 0.01
+            for iters in (1, 5, 20):
+                r, _ = O.k3_pagerank_ex(R, r0, iters, 0.85, dangling=True)
+                assert abs(r.sum() - 1.0) <= 1e-14
+    # A = 0: every row dangles, so one step gives the uniform vector 1/N
+    z = load_golden("k2_all_columns_removed.json")
+    e = np.array(z["edges"], dtype=np.uint32)
+    N = 1 << z["scale"]
+    R = O.k2_filter(e[:, 0], e[:, 1], N, "lowest")
+    r, _ = O.k3_pagerank_ex(R, np.array([0.3, 0.1, 0.4, 0.2]), 3, 0.85, dangling=True)
+    assert np.allclose(r, 1.0 / N, rtol=1e-15, atol=0)
+
+
+def check_k3ex_convergence(O, seed=0):
+    """The convergence test stops at the first k with norm(r_k - r_(k-1), 1) < tol,
+    found independently by the dense iteration; the converged vector is the
+    Perron vector of the stochastic Google matrix (Sec. IV-D validation)."""
+    for k, (N, M) in enumerate([(24, 120), (96, 700)]):
+        u, v = random_edges(N, M, seed + 5 * k, hub_bias=0.3)
+        R = O.k2_filter(u, v, N, "lowest")
+        A, _, _ = dense_kernel2(u, v, N, "lowest")
+        r0 = np.random.default_rng(seed + 9 * k).random(N) + 0.01
+        for dangling in (False, True):
+            G = google_dangling_matrix(A, 0.85) if dangling else 0.85 * A.T + 0.15 / N * np.ones((N, N))
+            for tol in (1e-4, 1e-9):
+                r = r0 / np.abs(r0).sum()
+                first = None
+                for it in range(1, 400):
+                    nxt = G @ r
+                    if np.abs(nxt - r).sum() < tol:
+                        first, r = it, nxt
+                        break
+                    r = nxt
+                got, done = O.k3_pagerank_ex(R, r0, 400, 0.85, dangling=dangling, tol=tol)
+                assert done == first, (dangling, tol, done, first)
+                assert np.abs(got - r).sum() <= 1e-13 * np.abs(r).sum()
+            # tol = 0 runs every iteration
+            assert O.k3_pagerank_ex(R, r0, 7, 0.85, dangling=dangling, tol=0.0)[1] == 7
+        # converged to 1e-13, the dangling variant is the normalised Perron vector
+        G = google_dangling_matrix(A, 0.85)
+        w, V = np.linalg.eig(G)
+        p = np.real(V[:, int(np.argmax(np.abs(w)))])
+        p = p / p.sum()
+        got, _ = O.k3_pagerank_ex(R, r0, 1000, 0.85, dangling=True, tol=1e-13)
+        assert np.abs(got - p).sum() <= 1e-11
+
+
 ALL_CHECKS = [
     ("k1_brute_force", check_k1_brute_force),
+    ("k3ex_dense_dangling", check_k3ex_dense_dangling),
+    ("k3ex_conservation", check_k3ex_conservation),
+    ("k3ex_convergence", check_k3ex_convergence),
     ("k2_dense", check_k2_dense),
     ("k2_golden", check_k2_golden),
     ("k3_dense", check_k3_dense),

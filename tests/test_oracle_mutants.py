@@ -1,7 +1,8 @@
 """Plant plausible mistakes in copies of the oracle and require the pins to catch each one.
 
-Each mutant is the oracle's C source with one statement replaced, built with
-gcc into a temporary directory (CPU only).  A mutant that passes every pin
+Each mutant is the oracle's C source with one statement replaced (in every
+function that contains it), built with gcc into a temporary directory (CPU
+only).  A mutant that passes every pin
 would mean the pins cannot tell that mistake from the paper's method.
 """
 import os
@@ -31,6 +32,12 @@ MUTANTS = {
     "k3_stale_sum": ("double s = sum_compensated(r, N);", "double s = 1.0;"),
     "k3_teleport_sign": ("r[vv] = y[vv] + a * s;", "r[vv] = y[vv] - a * s;"),
     "k3_damping_not_applied": ("double cr = c * r[uu];", "double cr = r[uu];"),
+    # Kernel 3 variants (dangling-node term, convergence test)
+    "k3ex_dangling_without_damping": ("double spread = c * dmass / (double)N;", "double spread = dmass / (double)N;"),
+    "k3ex_dangling_not_over_N": ("double spread = c * dmass / (double)N;", "double spread = c * dmass;"),
+    "k3ex_dangling_takes_every_row": ("if (rowptr[uu] == rowptr[uu + 1]) tmp[n++] = r[uu];", "tmp[n++] = r[uu];"),
+    "k3ex_stops_one_early": ("done = it + 1;", "done = it;"),
+    "k3ex_never_stops": ("            done = it + 1;\n            break;", "            done = it + 1;"),
 }
 
 
@@ -61,7 +68,8 @@ def test_mutant_is_caught(mutant, tmp_path):
 
     old, new = MUTANTS[mutant]
     src = open(SRC).read()
-    assert src.count(old) == 1, "mutation anchor not found once in the oracle source: %s" % mutant
+    # a statement shared by the plain and the variant Kernel 3 is mutated in both
+    assert src.count(old) >= 1, "mutation anchor not found in the oracle source: %s" % mutant
     msrc = tmp_path / "pp_oracle.c"
     msrc.write_text(src.replace(old, new))
     out = str(tmp_path / "liboracle_mutant.so")
