@@ -204,6 +204,30 @@ pp_status pp_pagerank(const pp_graph *g, const double *r0, uint32_t iters, doubl
                       void *stream);
 
 /*
+ * Kernel 3 variants the paper describes but leaves out of the benchmark
+ * (Sec. IV-C and IV-D), as flags:
+ *   PP_K3_DANGLING  the rows without entries (dangling nodes) pass their mass
+ *                   on evenly: with D = sum of r over those rows, each
+ *                   iteration is r(v) = c*(sum_u r(u) A(u,v) + D/N) +
+ *                   ((1-c)/N)*sum(r), so sum(r) stays 1.
+ *   PP_K3_CONVERGE  stop after the first iteration k with
+ *                   norm(r_k - r_(k-1), 1) < tol (tol > 0 required), at
+ *                   most `iters` iterations.
+ * flags = 0 gives pp_pagerank's result up to rounding.  iters_done (device
+ * uint32, may be NULL) receives the number of iterations run.  D and the
+ * norms are reduced exactly (fixed point), so the stopping iteration does not
+ * depend on scheduling.  Workspace from pp_pagerank_ex_workspace (larger than
+ * pp_pagerank's: r itself is kept each iteration).  Other arguments and
+ * errors as pp_pagerank; unknown flags give PP_ERR_INVALID_ARG.
+ */
+#define PP_K3_DANGLING 1u
+#define PP_K3_CONVERGE 2u
+pp_status pp_pagerank_ex_workspace(uint64_t M, uint32_t scale, uint32_t iters, pp_dtype dtype, size_t *bytes);
+pp_status pp_pagerank_ex(const pp_graph *g, const double *r0, uint32_t iters, double c, pp_dtype dtype,
+                         uint32_t flags, double tol, void *r_out, double *r_l1, uint32_t *iters_done,
+                         void *workspace, size_t workspace_bytes, void *stream);
+
+/*
  * Kernel 3 for a batch of graphs with several start vectors each (a sparse
  * matrix times dense matrix product; every (graph, vector) pair is one run of
  * the iteration above, in binary32 with sum(r) reduced exactly).

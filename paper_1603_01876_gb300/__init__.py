@@ -71,6 +71,9 @@ def _lib():
             "pp_pagerank_batched_workspace": [ctypes.POINTER(CGraph), u32, u32, u32, sz],
             "pp_pagerank_batched": [ctypes.POINTER(CGraph), u32, vp, u32, u32, dbl, vp, vp, ctypes.c_size_t, vp],
             "pp_selftest_lookback_timeout": [u32, vp, ctypes.c_size_t, sz, vp],
+            "pp_pagerank_ex_workspace": [u64, u32, u32, i32, sz],
+            "pp_pagerank_ex": [ctypes.POINTER(CGraph), vp, u32, dbl, i32, u32, dbl, vp, vp, vp, vp, ctypes.c_size_t,
+                               vp],
             "pp_pagerank_batched_capture": [ctypes.POINTER(CGraph), u32, vp, u32, u32, dbl, vp, vp, ctypes.c_size_t,
                                             vp, ctypes.POINTER(vp)],
             "pp_exec_launch": [vp, vp],
@@ -167,6 +170,8 @@ def workspace_bytes(kind, M, scale, iters=20, dtype="fp32"):
         st = L.pp_build_filter_normalize_workspace(M, scale, ctypes.byref(n))
     elif kind == "pagerank":
         st = L.pp_pagerank_workspace(M, scale, iters, DTYPES[dtype], ctypes.byref(n))
+    elif kind == "pagerank_ex":
+        st = L.pp_pagerank_ex_workspace(M, scale, iters, DTYPES[dtype], ctypes.byref(n))
     elif kind == "pipeline":
         st = L.pp_pipeline_workspace(M, scale, iters, DTYPES[dtype], ctypes.byref(n))
     else:
@@ -245,6 +250,29 @@ def pagerank(graph, r0, iters=20, c=0.85, dtype="fp32", out=None, want_l1=False,
 
 
 BATCH_MAX_GRAPHS, BATCH_MAX_RHS = 128, 32
+
+
+K3_DANGLING = 1
+K3_CONVERGE = 2
+
+
+def pagerank_ex(graph, r0, iters=20, c=0.85, dtype="fp32", dangling=False, tol=0.0, out=None, want_l1=False,
+                workspace=None, stream=None):
+    """Kernel 3 variants (pp_pagerank_ex): the dangling-node term and/or the
+    convergence test norm(r_k - r_(k-1), 1) < tol.  Returns (r, iterations
+    run as a device uint32 tensor[, r / norm(r,1)])."""
+    dev = r0.device
+    if out is None:
+        out = torch.empty(graph.N, dtype=torch.float64 if dtype == "fp64" else torch.float32, device=dev)
+    l1 = torch.empty(graph.N, dtype=torch.float64, device=dev) if want_l1 else None
+    done = torch.zeros(1, dtype=torch.int32, device=dev)
+    flags = (K3_DANGLING if dangling else 0) | (K3_CONVERGE if tol > 0 else 0)
+    need = workspace_bytes("pagerank_ex", graph.M, graph.scale, iters, dtype)
+    ws = workspace if workspace is not None and workspace.numel() >= need else _workspace(need, dev)
+    st = _lib().pp_pagerank_ex(ctypes.byref(graph.c), _ptr(r0), iters, c, DTYPES[dtype], flags, float(tol),
+                               _ptr(out), _ptr(l1), _ptr(done), _ptr(ws), ws.numel(), _stream(stream, dev))
+    _check("pp_pagerank_ex", st)
+    return (out, done, l1) if want_l1 else (out, done)
 
 
 def pagerank_batched(graphs, r0, nrhs, iters=20, c=0.85, out=None, workspace=None, stream=None):

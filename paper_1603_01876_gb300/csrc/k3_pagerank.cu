@@ -94,6 +94,12 @@ struct Args {
     uint32_t shortmax;    // columns longer than this are cut into chunks (power of two)
     uint32_t chunk;       // entries of a long column per work item
     uint32_t lane_short;  // tile columns up to this long are summed by one lane
+    // variants (pp_pagerank_ex); zero / null for the plain iteration
+    uint32_t flags;                  // PP_K3_DANGLING | PP_K3_CONVERGE
+    double tol;                      // convergence threshold on norm(r_k - r_(k-1), 1)
+    unsigned long long *dmass;       // [2 * (iters + 1)] sum of r over dangling rows, per iterate
+    unsigned long long *delta;       // [2 * (iters + 1)] norm(r_k - r_(k-1), 1), per iterate
+    uint32_t *state;                 // [0] converged, [1] iterations run
 };
 
 __device__ __forceinline__ uint32_t ovf_lookup(const uint64_t *keys, const uint32_t *cnts, uint64_t n,
@@ -231,7 +237,12 @@ __global__ void __launch_bounds__(256) setup_kernel(Args a, const double *r0) {
     const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     if (gtid == 0) a.ctr[0] = 0;
-    for (uint64_t i = gtid; i < 2ull * (a.iters + 1); i += stride) a.acc[i] = 0;
+    for (uint64_t i = gtid; i < 2ull * (a.iters + 1); i += stride) {
+        a.acc[i] = 0;
+        if (a.dmass) a.dmass[i] = 0;
+        if (a.delta) a.delta[i] = 0;
+    }
+    if (gtid < 2 && a.state) a.state[gtid] = 0;
     for (uint64_t i = gtid; i < (a.N + PLAN_TILE - 1) / PLAN_TILE; i += stride) a.plan_status[i] = 0;
     if (gtid == 0) a.fx_exp[0] = 1;  // the normalised start vector has every entry <= 1 < 2^1
     double acc = 0.0;
@@ -244,7 +255,7 @@ __global__ void __launch_bounds__(256) setup_kernel(Args a, const double *r0) {
 // sum(r) of that vector.  With iters == 0 the normalised r is the result.
 template <typename TS, typename TA, typename TO>
 __global__ void __launch_bounds__(256) normalize_kernel(Args a, const double *r0, const TA *inv, TA *invp, TS *x0,
-                                                        TO *r_out) {
+                                                        TO *r_out, TA *rb0) {
     __shared__ double s_norm;
     __shared__ uint64_t s_fx[16];
     if (threadIdx.x == 0) {
@@ -255,7 +266,7 @@ __global__ void __launch_bounds__(256) normalize_kernel(Args a, const double *r0
     __syncthreads();
     const double norm = s_norm;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    Fx128 acc{0, 0};
+    Fx128 acc{0, 0}, dm{0, 0};
     // in storage order: position p holds vertex iperm[p]; 1/d_out is copied into that order too
     for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.N; p += stride) {
         const uint32_t v = a.iperm[p];
@@ -265,9 +276,16 @@ __global__ void __launch_bounds__(256) normalize_kernel(Args a, const double *r0
         invp[p] = iv;
         x0[p] = from_acc<TS>(r * iv);
         if (a.iters == 0) r_out[v] = (TO)r;
+        if (rb0) rb0[p] = r;
+        if ((a.flags & PP_K3_DANGLING) && iv == TA(0)) fx_add(dm, r, 1);
     }
     const Fx128 bt = fx_block_sum<256>(acc, s_fx);
     if (threadIdx.x == 0 && (bt.hi | bt.lo)) fx_atomic_add(a.acc, bt);
+    if (a.flags & PP_K3_DANGLING) {
+        __syncthreads();
+        const Fx128 bd = fx_block_sum<256>(dm, s_fx);
+        if (threadIdx.x == 0 && (bd.hi | bd.lo)) fx_atomic_add(a.dmass, bd);
+    }
 }
 
 // ------------------------------------------------------------- the iteration
@@ -286,8 +304,16 @@ __device__ __forceinline__ void st_x(__nv_bfloat16 *p, __nv_bfloat16 v, uint64_t
 __device__ __forceinline__ float ld_inv(const float *p, uint64_t pol) { return ld_hint(p, pol); }
 __device__ __forceinline__ double ld_inv(const double *p, uint64_t pol) { return ld_hint(p, pol); }
 
+// Per-thread exact accumulators: sum(r'), and for the variants the mass of
+// the dangling rows and norm(r' - r, 1).
+struct Sums {
+    Fx128 s, dm, df;
+};
+
 // Finishes column `col` from its sum y: r = c*y + teleport, x' = r / d_out.
-template <typename TS, typename TA, typename TO, bool LAST>
+// EXT (the variants) also keeps r itself (rb_out) for the convergence test
+// and the final result.
+template <typename TS, typename TA, typename TO, bool LAST, bool EXT>
 struct Epilogue {
     const TA *inv;
     TS *x_out;
@@ -296,12 +322,23 @@ struct Epilogue {
     uint64_t keep, stream;
     int E;
     const uint32_t *iperm;
+    const TA *rb_in;
+    TA *rb_out;
+    uint32_t flags;
     // col is a column position (vertex iperm[col])
-    __device__ __forceinline__ void operator()(uint32_t col, TA y, TA inv_col, Fx128 &acc) const {
+    __device__ __forceinline__ void operator()(uint32_t col, TA y, TA inv_col, Sums &acc) const {
         const TA r = cc * y + tele;
-        if (LAST) r_out[__ldg(iperm + col)] = (TO)r;
+        if (LAST && !EXT) r_out[__ldg(iperm + col)] = (TO)r;
         st_x(x_out + col, from_acc<TS>(r * inv_col), keep);
-        fx_add(acc, r, E);
+        fx_add(acc.s, r, E);
+        if (EXT) {
+            if (flags & PP_K3_CONVERGE) {
+                const TA d = r - rb_in[col];
+                fx_add(acc.df, d < TA(0) ? -d : d, E);
+            }
+            rb_out[col] = r;
+            if ((flags & PP_K3_DANGLING) && inv_col == TA(0)) fx_add(acc.dm, r, E);
+        }
     }
 };
 
@@ -325,26 +362,52 @@ __device__ __forceinline__ TA warp_sum(TA y) {
     return y;  // in lane 0
 }
 
-template <typename TS, typename TA, typename TO, bool LAST, int UNROLL, int MINB>
+template <typename TS, typename TA, typename TO, bool LAST, int UNROLL, int MINB, bool EXT>
 __global__ void __launch_bounds__(THREADS, MINB) iterate_kernel(Args a, const TA *inv, const TS *__restrict__ x_in,
-                                                          TS *__restrict__ x_out, TO *r_out, uint32_t iter) {
+                                                          TS *__restrict__ x_out, TO *r_out, uint32_t iter,
+                                                          const TA *rb_in, TA *rb_out) {
     static_assert(TILE_ENTRIES % (32 * UNROLL) == 0, "unroll must divide the work");
     __shared__ TA s_prod[WARPS][TILE_ENTRIES];
     __shared__ uint32_t s_cp[WARPS][TILE_COLS + 1];
     __shared__ uint64_t s_fx[2 * WARPS];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double tele_extra = 0.0;
+    if (EXT) {
+        // the variants: stop once converged; the dangling rows' mass is spread evenly
+        if (ld_relaxed_u32(a.state)) return;
+        if ((a.flags & PP_K3_CONVERGE) && iter >= 1 &&
+            fx_value(a.delta[2 * iter], a.delta[2 * iter + 1], a.fx_exp[iter]) < a.tol) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                a.state[1] = iter;
+                st_relaxed_u32(a.state, 1u);
+            }
+            return;
+        }
+        if (a.flags & PP_K3_DANGLING)
+            tele_extra = a.c / (double)a.N * fx_value(a.dmass[2 * iter], a.dmass[2 * iter + 1], a.fx_exp[iter]);
+    }
     const uint32_t n_items = a.ctl->n_items;
     const double S = fx_value(a.acc[2 * iter], a.acc[2 * iter + 1], a.fx_exp[iter]);
     const int E = fx_exponent(S);
     if (blockIdx.x == 0 && threadIdx.x == 0) a.fx_exp[iter + 1] = E;
     const uint32_t umask = (1u << a.scale) - 1u;
     const uint64_t keep = policy_evict_last(), stream = policy_evict_first();
-    const Epilogue<TS, TA, TO, LAST> epi{inv,  x_out,  r_out, (TA)a.c, (TA)(((1.0 - a.c) / (double)a.N) * S),
-                                         keep, stream, E,     a.iperm};
+    const Epilogue<TS, TA, TO, LAST, EXT> epi{inv,
+                                              x_out,
+                                              r_out,
+                                              (TA)a.c,
+                                              (TA)(((1.0 - a.c) / (double)a.N) * S + tele_extra),
+                                              keep,
+                                              stream,
+                                              E,
+                                              a.iperm,
+                                              rb_in,
+                                              rb_out,
+                                              a.flags};
     TA *prod = s_prod[warp];
     uint32_t *cp = s_cp[warp];
-    Fx128 acc{0, 0};
+    Sums acc{{0, 0}, {0, 0}, {0, 0}};
     const uint32_t nwarps = gridDim.x * WARPS;
 
     uint32_t item = blockIdx.x * WARPS + warp;
@@ -476,8 +539,30 @@ __global__ void __launch_bounds__(THREADS, MINB) iterate_kernel(Args a, const TA
         item = next;
         it = nit;
     }
-    const Fx128 bt = fx_block_sum<THREADS>(acc, s_fx);
+    const Fx128 bt = fx_block_sum<THREADS>(acc.s, s_fx);
     if (threadIdx.x == 0 && (bt.hi | bt.lo)) fx_atomic_add(a.acc + 2 * (iter + 1), bt);
+    if (EXT && (a.flags & PP_K3_DANGLING)) {
+        __syncthreads();
+        const Fx128 bd = fx_block_sum<THREADS>(acc.dm, s_fx);
+        if (threadIdx.x == 0 && (bd.hi | bd.lo)) fx_atomic_add(a.dmass + 2 * (iter + 1), bd);
+    }
+    if (EXT && (a.flags & PP_K3_CONVERGE)) {
+        __syncthreads();
+        const Fx128 bf = fx_block_sum<THREADS>(acc.df, s_fx);
+        if (threadIdx.x == 0 && (bf.hi | bf.lo)) fx_atomic_add(a.delta + 2 * (iter + 1), bf);
+    }
+}
+
+// The variants: r after the iterations that ran (storage order) into r_out
+// (vertex order), and the number of iterations.
+template <typename TA, typename TO>
+__global__ void __launch_bounds__(256) finish_kernel(Args a, const TA *rb0, const TA *rb1, TO *r_out,
+                                                     uint32_t *iters_done) {
+    const uint32_t k = ld_relaxed_u32(a.state) ? a.state[1] : a.iters;
+    const TA *rb = (k & 1) ? rb1 : rb0;
+    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.N; p += (uint64_t)gridDim.x * blockDim.x)
+        r_out[a.iperm[p]] = (TO)rb[p];
+    if (iters_done && blockIdx.x == 0 && threadIdx.x == 0) *iters_done = k;
 }
 
 // r_l1 = r / norm(r,1) in binary64: sum, then scale.
@@ -518,10 +603,14 @@ struct Layout {
     double *ipart;
     Ctl *ctl;
     uint32_t *ctr;
+    // the variants only
+    void *rb[2];  // r in storage order (TA), ping-pong
+    unsigned long long *dmass, *delta;
+    uint32_t *state;
     size_t bytes;
 };
 
-inline Layout layout(void *ws, uint64_t M, uint32_t scale, uint32_t iters, pp_dtype dt) {
+inline Layout layout(void *ws, uint64_t M, uint32_t scale, uint32_t iters, pp_dtype dt, bool ext = false) {
     Carver c(ws);
     Layout L;
     const uint64_t N = 1ull << scale;
@@ -541,6 +630,17 @@ inline Layout layout(void *ws, uint64_t M, uint32_t scale, uint32_t iters, pp_dt
     L.ipart = c.take<double>(SETUP_BLOCKS);
     L.ctl = c.take<Ctl>(1);
     L.ctr = c.take<uint32_t>(1);
+    L.rb[0] = L.rb[1] = nullptr;
+    L.dmass = L.delta = nullptr;
+    L.state = nullptr;
+    if (ext) {
+        const size_t ta = dt == PP_FP64 ? 8 : 4;
+        L.rb[0] = c.take<char>(N * ta);
+        L.rb[1] = c.take<char>(N * ta);
+        L.dmass = c.take<unsigned long long>(2ull * (iters + 1));
+        L.delta = c.take<unsigned long long>(2ull * (iters + 1));
+        L.state = c.take<uint32_t>(2);
+    }
     L.bytes = c.size();
     return L;
 }
@@ -552,9 +652,16 @@ inline int occupancy(K kernel) {
     return o > 0 ? o : 1;
 }
 
-template <typename TS, typename TA, typename TO, int UNROLL, int MINB>
+// Variant options of pp_pagerank_ex (EXT kernels only).
+struct Variant {
+    uint32_t flags;
+    double tol;
+    uint32_t *iters_done;
+};
+
+template <typename TS, typename TA, typename TO, int UNROLL, int MINB, bool EXT>
 pp_status run_unroll(const pp_graph *g, const double *r0, uint32_t iters, double c, pp_dtype dt, TO *r_out,
-                     double *r_l1, const Layout &L, cudaStream_t s) {
+                     double *r_l1, const Layout &L, cudaStream_t s, const Variant &var) {
     const uint32_t N = 1u << g->scale;
     Args a;
     a.N = N;
@@ -582,6 +689,12 @@ pp_status run_unroll(const pp_graph *g, const double *r0, uint32_t iters, double
     a.shortmax = (uint32_t)tuning("k3_shortmax");
     a.chunk = (uint32_t)tuning("k3_chunk");
     a.lane_short = (uint32_t)tuning("k3_lane_short");
+    a.flags = EXT ? var.flags : 0u;
+    a.tol = var.tol;
+    a.dmass = L.dmass;
+    a.delta = L.delta;
+    a.state = L.state;
+    TA *rb0 = static_cast<TA *>(L.rb[0]), *rb1 = static_cast<TA *>(L.rb[1]);
     const TA *inv = dt == PP_FP64 ? reinterpret_cast<const TA *>(g->inv_dout64)
                                   : reinterpret_cast<const TA *>(g->inv_dout32);
     if (!inv) return PP_ERR_INVALID_ARG;
@@ -591,21 +704,28 @@ pp_status run_unroll(const pp_graph *g, const double *r0, uint32_t iters, double
     plan_kernel<<<(unsigned)ceil_div(N, PLAN_TILE), PLAN_THREADS, 0, s>>>(a);
     plan_items_kernel<<<(unsigned)std::min<uint64_t>(ceil_div(N, 256), 4096), 256, 0, s>>>(a);
     TA *invp = static_cast<TA *>(L.invp);  // 1/d_out in storage order
-    normalize_kernel<TS, TA, TO><<<SETUP_BLOCKS, 256, 0, s>>>(a, r0, inv, invp, x0, r_out);
+    normalize_kernel<TS, TA, TO><<<SETUP_BLOCKS, 256, 0, s>>>(a, r0, inv, invp, x0, r_out, EXT ? rb0 : nullptr);
     count_launch(4);
 
-    static const int o_mid = occupancy(iterate_kernel<TS, TA, TO, false, UNROLL, MINB>);
-    static const int o_last = occupancy(iterate_kernel<TS, TA, TO, true, UNROLL, MINB>);
+    static const int o_mid = occupancy(iterate_kernel<TS, TA, TO, false, UNROLL, MINB, EXT>);
+    static const int o_last = occupancy(iterate_kernel<TS, TA, TO, !EXT, UNROLL, MINB, EXT>);
     const int sms = sm_count();
     for (uint32_t it = 0; it < iters; ++it) {
         const TS *xin = (it & 1) ? x1 : x0;
         TS *xout = (it & 1) ? x0 : x1;
-        if (it + 1 == iters)
-            iterate_kernel<TS, TA, TO, true, UNROLL, MINB><<<sms * o_last, THREADS, 0, s>>>(a, invp, xin, xout,
-                                                                                         r_out, it);
+        const TA *rin = (it & 1) ? rb1 : rb0;
+        TA *rout = (it & 1) ? rb0 : rb1;
+        // the variants write r every iteration and finish_kernel picks the last one
+        if (it + 1 == iters && !EXT)
+            iterate_kernel<TS, TA, TO, !EXT, UNROLL, MINB, EXT><<<sms * o_last, THREADS, 0, s>>>(a, invp, xin, xout,
+                                                                                              r_out, it, rin, rout);
         else
-            iterate_kernel<TS, TA, TO, false, UNROLL, MINB><<<sms * o_mid, THREADS, 0, s>>>(a, invp, xin, xout,
-                                                                                          r_out, it);
+            iterate_kernel<TS, TA, TO, false, UNROLL, MINB, EXT><<<sms * o_mid, THREADS, 0, s>>>(a, invp, xin, xout,
+                                                                                               r_out, it, rin, rout);
+        count_launch();
+    }
+    if (EXT) {
+        finish_kernel<TA, TO><<<SETUP_BLOCKS, 256, 0, s>>>(a, rb0, rb1, r_out, var.iters_done);
         count_launch();
     }
     if (r_l1) {
@@ -619,18 +739,26 @@ pp_status run_unroll(const pp_graph *g, const double *r0, uint32_t iters, double
 template <typename TS, typename TA, typename TO>
 pp_status run(const pp_graph *g, const double *r0, uint32_t iters, double c, pp_dtype dt, TO *r_out,
               double *r_l1, const Layout &L, cudaStream_t s) {
+    const Variant none{0u, 0.0, nullptr};
     const bool u4 = tuning(sizeof(TA) == 8 ? "k3_unroll_f64" : "k3_unroll_f32") == 4;
     switch (tuning("k3_minblocks")) {
         case 5:
-            return u4 ? run_unroll<TS, TA, TO, 4, 5>(g, r0, iters, c, dt, r_out, r_l1, L, s)
-                      : run_unroll<TS, TA, TO, 8, 5>(g, r0, iters, c, dt, r_out, r_l1, L, s);
+            return u4 ? run_unroll<TS, TA, TO, 4, 5, false>(g, r0, iters, c, dt, r_out, r_l1, L, s, none)
+                      : run_unroll<TS, TA, TO, 8, 5, false>(g, r0, iters, c, dt, r_out, r_l1, L, s, none);
         case 6:
-            return u4 ? run_unroll<TS, TA, TO, 4, 6>(g, r0, iters, c, dt, r_out, r_l1, L, s)
-                      : run_unroll<TS, TA, TO, 8, 6>(g, r0, iters, c, dt, r_out, r_l1, L, s);
+            return u4 ? run_unroll<TS, TA, TO, 4, 6, false>(g, r0, iters, c, dt, r_out, r_l1, L, s, none)
+                      : run_unroll<TS, TA, TO, 8, 6, false>(g, r0, iters, c, dt, r_out, r_l1, L, s, none);
         default:
-            return u4 ? run_unroll<TS, TA, TO, 4, 4>(g, r0, iters, c, dt, r_out, r_l1, L, s)
-                      : run_unroll<TS, TA, TO, 8, 4>(g, r0, iters, c, dt, r_out, r_l1, L, s);
+            return u4 ? run_unroll<TS, TA, TO, 4, 4, false>(g, r0, iters, c, dt, r_out, r_l1, L, s, none)
+                      : run_unroll<TS, TA, TO, 8, 4, false>(g, r0, iters, c, dt, r_out, r_l1, L, s, none);
     }
+}
+
+// The variants run one instantiation (unroll 4, 4 blocks per SM).
+template <typename TS, typename TA, typename TO>
+pp_status run_ext(const pp_graph *g, const double *r0, uint32_t iters, double c, pp_dtype dt, TO *r_out,
+                  double *r_l1, const Layout &L, cudaStream_t s, const Variant &var) {
+    return run_unroll<TS, TA, TO, 4, 4, true>(g, r0, iters, c, dt, r_out, r_l1, L, s, var);
 }
 
 }  // namespace k3
@@ -665,5 +793,40 @@ extern "C" pp_status pp_pagerank(const pp_graph *g, const double *r0, uint32_t i
         default:
             return k3::run<__nv_bfloat16, float, float>(g, r0, iters, c, dt, static_cast<float *>(r_out), r_l1, L,
                                                         s);
+    }
+}
+
+extern "C" pp_status pp_pagerank_ex_workspace(uint64_t M, uint32_t scale, uint32_t iters, pp_dtype dt,
+                                              size_t *bytes) {
+    if (!bytes || scale < 1 || scale > 27 || M > (1ull << 31) || (int)dt < 0 || (int)dt > 2)
+        return PP_ERR_INVALID_ARG;
+    *bytes = k3::layout(nullptr, M, scale, iters, dt, true).bytes;
+    return PP_OK;
+}
+
+extern "C" pp_status pp_pagerank_ex(const pp_graph *g, const double *r0, uint32_t iters, double c, pp_dtype dt,
+                                    uint32_t flags, double tol, void *r_out, double *r_l1, uint32_t *iters_done,
+                                    void *ws, size_t ws_bytes, void *stream) {
+    if (!g || !r0 || !r_out || (int)dt < 0 || (int)dt > 2) return PP_ERR_INVALID_ARG;
+    if (g->scale < 1 || g->scale > 27 || g->M > (1ull << 31) || !(c >= 0.0 && c <= 1.0)) return PP_ERR_INVALID_ARG;
+    if (flags & ~(uint32_t)(PP_K3_DANGLING | PP_K3_CONVERGE)) return PP_ERR_INVALID_ARG;
+    if ((flags & PP_K3_CONVERGE) && !(tol > 0.0)) return PP_ERR_INVALID_ARG;
+    if (!g->colptr || !g->rowc || !g->ovf_key || !g->ovf_cnt || !g->info || !g->perm || !g->iperm)
+        return PP_ERR_INVALID_ARG;
+    const k3::Layout need = k3::layout(nullptr, g->M, g->scale, iters, dt, true);
+    pp_status st = check_ws(ws, ws_bytes, need.bytes);
+    if (st != PP_OK) return st;
+    const k3::Layout L = k3::layout(ws, g->M, g->scale, iters, dt, true);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const k3::Variant var{flags, (flags & PP_K3_CONVERGE) ? tol : 0.0, iters_done};
+    switch (dt) {
+        case PP_FP64:
+            return k3::run_ext<double, double, double>(g, r0, iters, c, dt, static_cast<double *>(r_out), r_l1, L, s,
+                                                       var);
+        case PP_FP32:
+            return k3::run_ext<float, float, float>(g, r0, iters, c, dt, static_cast<float *>(r_out), r_l1, L, s, var);
+        default:
+            return k3::run_ext<__nv_bfloat16, float, float>(g, r0, iters, c, dt, static_cast<float *>(r_out), r_l1, L,
+                                                            s, var);
     }
 }
