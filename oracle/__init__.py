@@ -36,7 +36,11 @@ class Oracle:
         L.oracle_k3_pagerank.argtypes = [u32, vp, vp, vp, vp, u32, ctypes.c_double, vp, vp]
         L.oracle_k3_pagerank_ex.argtypes = [u32, vp, vp, vp, vp, u32, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                             vp, vp]
-        for f in (L.oracle_k1_sort, L.oracle_k2_filter, L.oracle_k3_pagerank, L.oracle_k3_pagerank_ex):
+        L.oracle_format_tsv.argtypes = [vp, vp, u64, vp, u64]
+        L.oracle_format_tsv.restype = ctypes.c_int64
+        L.oracle_parse_tsv.argtypes = [vp, u64, vp, vp, u64, vp, vp]
+        for f in (L.oracle_k1_sort, L.oracle_k2_filter, L.oracle_k3_pagerank, L.oracle_k3_pagerank_ex,
+                  L.oracle_parse_tsv):
             f.restype = ctypes.c_int
         self.lib = L
 
@@ -111,6 +115,30 @@ class Oracle:
             raise MemoryError("oracle_k3_pagerank_ex failed")
         return r, int(done.value)
 
+    def format_tsv(self, u, v):
+        """The edge file text of (u, v): one "u\\tv\\n" line per edge."""
+        u = np.ascontiguousarray(u, dtype=np.uint32)
+        v = np.ascontiguousarray(v, dtype=np.uint32)
+        cap = 22 * len(u)
+        out = np.empty(max(cap, 1), dtype=np.uint8)
+        n = self.lib.oracle_format_tsv(u.ctypes.data, v.ctypes.data, len(u), out.ctypes.data, cap)
+        if n < 0:
+            raise MemoryError("oracle_format_tsv failed")
+        return out[:n].tobytes()
+
+    def parse_tsv(self, text, cap=None):
+        """(u, v, lines, malformed) read from edge file text."""
+        buf = np.frombuffer(bytes(text), dtype=np.uint8)
+        cap = len(buf) // 4 + 1 if cap is None else cap
+        u = np.zeros(max(cap, 1), dtype=np.uint32)
+        v = np.zeros(max(cap, 1), dtype=np.uint32)
+        m = ctypes.c_uint64(0)
+        bad = ctypes.c_int(0)
+        self.lib.oracle_parse_tsv(buf.ctypes.data if len(buf) else None, len(buf), u.ctypes.data, v.ctypes.data, cap,
+                                  ctypes.byref(m), ctypes.byref(bad))
+        k = min(m.value, cap)
+        return u[:k], v[:k], int(m.value), bool(bad.value)
+
     def pipeline(self, u, v, scale, r0, iters=20, c=0.85, rule="lowest"):
         """Kernels 1-3 in order, each finished before the next starts."""
         N = 1 << scale
@@ -144,6 +172,14 @@ def k3_pagerank(A, r0, iters=20, c=0.85, want_sums=False):
 
 def k3_pagerank_ex(A, r0, iters=20, c=0.85, dangling=False, tol=0.0):
     return default().k3_pagerank_ex(A, r0, iters, c, dangling, tol)
+
+
+def format_tsv(u, v):
+    return default().format_tsv(u, v)
+
+
+def parse_tsv(text, cap=None):
+    return default().parse_tsv(text, cap)
 
 
 def pipeline(u, v, scale, r0, iters=20, c=0.85, rule="lowest"):

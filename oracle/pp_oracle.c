@@ -21,12 +21,15 @@
  *  - Kernel 3 keeps the 1/N of the teleport term: the update is
  *    r <- (c r) A + ((1-c)/N) sum(r), as in its first form and the appendix;
  *    the "simplified" form printed without the /N is read as a misprint.
+ *  - The edge files (Sec. IV-A, IV-B) hold 0-based ids as decimal strings,
+ *    "u\tv\n" per edge (the paper's Matlab files count from 1).
  *  - The variants (oracle_k3_pagerank_ex): the dangling-node term the paper
  *    omits spreads the mass of rows without entries evenly, scaled by c
  *    (the usual uniform correction); the convergence test is the L1 norm of
  *    the difference of consecutive iterates against an absolute tolerance.
  */
 #include <stdint.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -274,5 +277,66 @@ int oracle_k3_pagerank_ex(uint32_t N, const uint64_t *rowptr, const uint32_t *co
     *iters_done = done;
     free(y);
     free(tmp);
+    return 0;
+}
+
+/* The edge files of Kernels 0-2 (Sec. IV-A, IV-B): one edge per line, start
+ * and end vertex in decimal separated by a tab, "u\tv\n".  Formats M edges
+ * into out (room for cap bytes); returns the length, or -1 if out is too
+ * small. */
+int64_t oracle_format_tsv(const uint32_t *u, const uint32_t *v, uint64_t M, char *out, uint64_t cap) {
+    uint64_t n = 0;
+    char line[32];
+    for (uint64_t i = 0; i < M; ++i) {
+        int k = snprintf(line, sizeof line, "%u\t%u\n", (unsigned)u[i], (unsigned)v[i]);
+        if (k < 0 || n + (uint64_t)k > cap) return -1;
+        memcpy(out + n, line, (size_t)k);
+        n += (uint64_t)k;
+    }
+    return (int64_t)n;
+}
+
+/* One field: 1 to 10 decimal digits, value below 2^32. */
+static int parse_field(const char *p, const char *end, uint32_t *out) {
+    uint64_t x = 0;
+    if (p == end || end - p > 10) return 0;
+    for (; p < end; ++p) {
+        if (*p < '0' || *p > '9') return 0;
+        x = x * 10 + (uint64_t)(*p - '0');
+    }
+    if (x > 0xffffffffull) return 0;
+    *out = (uint32_t)x;
+    return 1;
+}
+
+/* Parses text[0 .. len) line by line.  Stores at most cap edges, the number
+ * of lines in *m, and 1 in *bad if any line is malformed (not "digits\tdigits",
+ * a field of more than 10 digits or above 2^32-1, longer than 22 bytes), if
+ * the text does not end with a newline, or if there are more than cap lines;
+ * a malformed line is stored as (0, 0). */
+int oracle_parse_tsv(const char *text, uint64_t len, uint32_t *u, uint32_t *v, uint64_t cap, uint64_t *m, int *bad) {
+    uint64_t line = 0, start = 0;
+    *bad = 0;
+    for (uint64_t i = 0; i < len; ++i) {
+        if (text[i] != '\n') continue;
+        const char *s = text + start, *e = text + i;
+        const char *tab = memchr(s, '\t', (size_t)(e - s));
+        uint32_t a = 0, b = 0;
+        int ok = tab != NULL && (e - s) + 1 <= 22 && memchr(tab + 1, '\t', (size_t)(e - tab - 1)) == NULL &&
+                 parse_field(s, tab, &a) && parse_field(tab + 1, e, &b);
+        if (!ok) {
+            *bad = 1;
+            a = b = 0;
+        }
+        if (line < cap) {
+            u[line] = a;
+            v[line] = b;
+        }
+        ++line;
+        start = i + 1;
+    }
+    if (start != len) *bad = 1; /* text after the last newline */
+    if (line > cap) *bad = 1;
+    *m = line;
     return 0;
 }

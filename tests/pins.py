@@ -348,11 +348,39 @@ def check_k3ex_convergence(O, seed=0):
         assert np.abs(got - p).sum() <= 1e-11
 
 
+def check_tsv_golden(O):
+    """The edge-file text of Sec. IV-A/B against a hand-written fixture, and
+    hand-written malformed lines that must be flagged."""
+    g = load_golden("edges_tsv_small.json")
+    text = g["text"].encode()
+    assert O.format_tsv(np.array(g["u"], dtype=np.uint32), np.array(g["v"], dtype=np.uint32)) == text
+    u, v, m, bad = O.parse_tsv(text)
+    assert not bad and m == len(g["u"]) and u.tolist() == g["u"] and v.tolist() == g["v"]
+    for t, why in g["malformed"]:
+        assert O.parse_tsv(t.encode())[3], why
+    # more lines than the room given
+    assert O.parse_tsv(text, cap=2)[3]
+
+
+def check_tsv_round_trip(O, seed=0):
+    """Formatting agrees with Python's own decimal formatting; parsing inverts it."""
+    rng = np.random.default_rng(seed)
+    for n in (0, 1, 7, 1000):
+        u = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32)
+        v = (rng.integers(0, 1 << 12, n)).astype(np.uint32)
+        text = O.format_tsv(u, v)
+        assert text == "".join("%d\t%d\n" % (a, b) for a, b in zip(u.tolist(), v.tolist())).encode()
+        pu, pv, m, bad = O.parse_tsv(text)
+        assert not bad and m == n and np.array_equal(pu, u) and np.array_equal(pv, v)
+
+
 ALL_CHECKS = [
     ("k1_brute_force", check_k1_brute_force),
     ("k3ex_dense_dangling", check_k3ex_dense_dangling),
     ("k3ex_conservation", check_k3ex_conservation),
     ("k3ex_convergence", check_k3ex_convergence),
+    ("tsv_golden", check_tsv_golden),
+    ("tsv_round_trip", check_tsv_round_trip),
     ("k2_dense", check_k2_dense),
     ("k2_golden", check_k2_golden),
     ("k3_dense", check_k3_dense),

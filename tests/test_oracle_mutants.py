@@ -38,6 +38,11 @@ MUTANTS = {
     "k3ex_dangling_takes_every_row": ("if (rowptr[uu] == rowptr[uu + 1]) tmp[n++] = r[uu];", "tmp[n++] = r[uu];"),
     "k3ex_stops_one_early": ("done = it + 1;", "done = it;"),
     "k3ex_never_stops": ("            done = it + 1;\n            break;", "            done = it + 1;"),
+    # edge files
+    "tsv_eleven_digits": ("if (p == end || end - p > 10) return 0;", "if (p == end || end - p > 11) return 0;"),
+    "tsv_trailing_text_accepted": ("if (start != len) *bad = 1;", ""),
+    "tsv_overflow_accepted": ("if (x > 0xffffffffull) return 0;", ""),
+    "tsv_end_vertex_dropped": ("\"%u\\t%u\\n\", (unsigned)u[i], (unsigned)v[i]", "\"%u\\t%u\\n\", (unsigned)u[i], 0u"),
 }
 
 
