@@ -61,6 +61,7 @@ typedef enum {
 /* Device error word bits (pp_last_device_error). */
 #define PP_DEV_RANGE 1u   /* an input vertex id was >= N */
 #define PP_DEV_TIMEOUT 2u /* a bounded cross-block wait expired; outputs are invalid */
+#define PP_DEV_PARSE 4u   /* edge-file text was malformed (pp_parse_tsv) */
 
 /* Slots of pp_graph.info (device uint64[PP_INFO_LEN]), written by Kernel 2. */
 #define PP_INFO_NNZ0 0       /* nonzeros of A before the column filters */
@@ -267,6 +268,32 @@ pp_status pp_pagerank_batched_capture(const pp_graph *gs, uint32_t n_graphs, con
                                       size_t workspace_bytes, void *stream, pp_exec **exec);
 pp_status pp_exec_launch(pp_exec *exec, void *stream);
 pp_status pp_exec_destroy(pp_exec *exec);
+
+/*
+ * The edge files of Kernels 0-2 (Sec. IV-A, IV-B): one edge per line, the
+ * start and end vertex in decimal separated by a tab and ended by a newline,
+ * "u\tv\n" (0-based ids, no signs or spaces; at most PP_TSV_MAX_LINE bytes
+ * a line).  The text is formatted and parsed on the device; reading and
+ * writing the files (and the host/device copies) is the caller's.
+ *
+ * pp_format_tsv writes the M edges (u[i], v[i]) as text[0 .. *text_len)
+ * (text_len: device uint64); text_cap must be at least
+ * M * PP_TSV_MAX_LINE, else PP_ERR_INVALID_ARG.
+ *
+ * pp_parse_tsv reads text[0 .. text_len) (device) into u[], v[] (device, room
+ * for m_cap edges) and stores the number of lines in *m_out (device uint64).
+ * Malformed text (a field that is not 1..10 digits or exceeds 2^32-1, not
+ * exactly one tab, an empty or over-long line, no newline at the end) or more
+ * than m_cap lines sets PP_DEV_PARSE in the device error word; a malformed
+ * line is stored as (0, 0) and lines beyond m_cap are dropped.
+ */
+#define PP_TSV_MAX_LINE 22
+pp_status pp_format_tsv_workspace(uint64_t M, size_t *bytes);
+pp_status pp_format_tsv(const uint32_t *u, const uint32_t *v, uint64_t M, char *text, uint64_t text_cap,
+                        uint64_t *text_len, void *workspace, size_t workspace_bytes, void *stream);
+pp_status pp_parse_tsv_workspace(uint64_t text_len, size_t *bytes);
+pp_status pp_parse_tsv(const char *text, uint64_t text_len, uint32_t *u, uint32_t *v, uint64_t m_cap,
+                       uint64_t *m_out, void *workspace, size_t workspace_bytes, void *stream);
 
 /*
  * Kernels 1-3 back to back from HOST buffers: copies u_host, v_host (M ids

@@ -72,6 +72,10 @@ def _lib():
             "pp_pagerank_batched": [ctypes.POINTER(CGraph), u32, vp, u32, u32, dbl, vp, vp, ctypes.c_size_t, vp],
             "pp_selftest_lookback_timeout": [u32, vp, ctypes.c_size_t, sz, vp],
             "pp_pagerank_ex_workspace": [u64, u32, u32, i32, sz],
+            "pp_format_tsv_workspace": [u64, sz],
+            "pp_format_tsv": [vp, vp, u64, vp, u64, vp, vp, ctypes.c_size_t, vp],
+            "pp_parse_tsv_workspace": [u64, sz],
+            "pp_parse_tsv": [vp, u64, vp, vp, u64, vp, vp, ctypes.c_size_t, vp],
             "pp_pagerank_ex": [ctypes.POINTER(CGraph), vp, u32, dbl, i32, u32, dbl, vp, vp, vp, vp, ctypes.c_size_t,
                                vp],
             "pp_pagerank_batched_capture": [ctypes.POINTER(CGraph), u32, vp, u32, u32, dbl, vp, vp, ctypes.c_size_t,
@@ -250,6 +254,45 @@ def pagerank(graph, r0, iters=20, c=0.85, dtype="fp32", out=None, want_l1=False,
 
 
 BATCH_MAX_GRAPHS, BATCH_MAX_RHS = 128, 32
+
+
+TSV_MAX_LINE = 22
+
+
+def format_tsv(u, v, out=None, stream=None):
+    """The edge-file text of (u, v) ("u\\tv\\n" per edge), formatted on the device.
+    Returns (text uint8 tensor with room for M * TSV_MAX_LINE bytes, length as a
+    device int64 tensor)."""
+    M = u.numel()
+    dev = u.device
+    if out is None:
+        out = torch.empty(max(1, M * TSV_MAX_LINE), dtype=torch.uint8, device=dev)
+    n = torch.zeros(1, dtype=torch.int64, device=dev)
+    need = ctypes.c_size_t(0)
+    _check("pp_format_tsv_workspace", _lib().pp_format_tsv_workspace(M, ctypes.byref(need)))
+    ws = _workspace(need.value, dev)
+    st = _lib().pp_format_tsv(_ptr(u), _ptr(v), M, _ptr(out), out.numel(), _ptr(n), _ptr(ws), ws.numel(),
+                              _stream(stream, dev))
+    _check("pp_format_tsv", st)
+    return out, n
+
+
+def parse_tsv(text, length, m_cap, out=None, stream=None):
+    """Edges (u, v) from edge-file text (device uint8 tensor, `length` bytes);
+    returns (u, v, number of lines as a device int64 tensor).  Malformed text
+    sets PP_DEV_PARSE (see last_device_error)."""
+    dev = text.device
+    if out is None:
+        out = (torch.empty(max(1, m_cap), dtype=torch.int32, device=dev),
+               torch.empty(max(1, m_cap), dtype=torch.int32, device=dev))
+    m = torch.zeros(1, dtype=torch.int64, device=dev)
+    need = ctypes.c_size_t(0)
+    _check("pp_parse_tsv_workspace", _lib().pp_parse_tsv_workspace(length, ctypes.byref(need)))
+    ws = _workspace(need.value, dev)
+    st = _lib().pp_parse_tsv(_ptr(text), length, _ptr(out[0]), _ptr(out[1]), m_cap, _ptr(m), _ptr(ws), ws.numel(),
+                             _stream(stream, dev))
+    _check("pp_parse_tsv", st)
+    return out[0], out[1], m
 
 
 K3_DANGLING = 1
