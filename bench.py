@@ -274,6 +274,57 @@ def run_ours(args):
                           "sum_r": float(rv.double().sum())}
     del ws_ex
 
+    # Kernel 1 with its files (Sec. IV-B): the edge-file text sits in pinned
+    # host memory (standing in for storage); copied in, parsed, sorted,
+    # formatted and copied out on the GPU
+    files = {}
+    if not args.no_files:
+        text, n = pp.format_tsv(u, v)  # Kernel 0's file (untimed)
+        tlen = int(n.item())
+        host_in = text[:tlen].cpu().pin_memory()
+        del text
+        torch.cuda.empty_cache()
+        dev_in = torch.empty(tlen, dtype=torch.uint8, device=dev)
+        dev_out = torch.empty(M * pp.TSV_MAX_LINE, dtype=torch.uint8, device=dev)
+        host_out = torch.empty(tlen, dtype=torch.uint8).pin_memory()
+        pu, pv = torch.empty_like(u), torch.empty_like(v)
+        su, sv = torch.empty_like(u), torch.empty_like(v)
+
+        def k1_files(ev=None):
+            if ev:
+                ev[0].record(stream)
+            dev_in.copy_(host_in, non_blocking=True)
+            if ev:
+                ev[1].record(stream)
+            pp.parse_tsv(dev_in, tlen, M, out=(pu, pv))
+            if ev:
+                ev[2].record(stream)
+            pp.sort_edges(pu, pv, scale, out=(su, sv), workspace=ws)
+            if ev:
+                ev[3].record(stream)
+            pp.format_tsv(su, sv, out=dev_out)
+            if ev:
+                ev[4].record(stream)
+            host_out.copy_(dev_out[:tlen], non_blocking=True)
+            if ev:
+                ev[5].record(stream)
+
+        k1_files()
+        torch.cuda.synchronize()
+        if pp.last_device_error():
+            raise RuntimeError("device error in the edge-file path")
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        k1_files(ev)
+        torch.cuda.synchronize()
+        t = [ev[i].elapsed_time(ev[i + 1]) for i in range(5)]
+        total_f = sum(t)
+        files = {"text_bytes": tlen, "h2d_ms": t[0], "parse_ms": t[1], "sort_ms": t[2], "format_ms": t[3],
+                 "d2h_ms": t[4], "k1_with_files_ms": total_f, "k1_with_files_edges_per_s": M / (total_f * 1e-3),
+                 "parse_gbs": tlen / t[1] / 1e6, "format_gbs": tlen / t[3] / 1e6,
+                 "storage": "pinned host memory (no disk)"}
+        del dev_in, dev_out, host_in, host_out, pu, pv, su, sv
+        torch.cuda.empty_cache()
+
     # end to end through the host-buffer entry point
     uh = u.cpu().pin_memory()
     vh = v.cpu().pin_memory()
@@ -354,6 +405,7 @@ def run_ours(args):
             "k3_iteration": {"ms": iter_ms, "setup_ms": k3_setup},
         },
         "k3_variants": variants,
+        "k1_files": files,
         "accuracy": {"fp32_vs_gpu_fp64_l1": l1_fp32, "fp32_vs_gpu_fp64_max_rel": maxrel_fp32,
                      "bf16_vs_gpu_fp64_l1": l1_bf, "bf16_vs_gpu_fp64_max_rel": maxrel_bf},
         "roofline": {"bound": "hbm", "kernel": kname, "stage": dom, "launches_per_step": launches_per_stage,
@@ -564,6 +616,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-batched", action="store_true", help="skip the batched Kernel 3 section")
+    ap.add_argument("--no-files", action="store_true", help="skip the edge-file (Kernel 1 with files) section")
     ap.add_argument("--tune", action="append", default=[], metavar="KEY=VALUE",
                     help="set a library tuning knob before running (repeatable)")
     ap.add_argument("--stage", choices=["all", "k3", "batched"], default="all",
