@@ -37,10 +37,9 @@ SEED = 1
 WORKLOAD = ("Kronecker graph, scale 24 (N=2^24, M=16N=268,435,456 edges, initiator A/B/C/D=0.57/0.19/0.19/0.05, "
             "seeded Philox), Kernel 1 sort + Kernel 2 filter/normalise + Kernel 3 20 damped iterations (c=0.85)")
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch from an ncu capture
-# (profiles/), valid only while the kernel's source file is unchanged.
-# DRAM bytes (read + write) per launch of each stage's dominant kernel from
-# one ncu capture (profiles/), valid while its source file is unchanged.
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
+# each stage's dominant kernel from one ncu capture (profiles/), valid while
+# its source file is unchanged.
 TRAFFIC = {
     "k3_pagerank": {"source": "paper_1603_01876_gb300/csrc/k3_pagerank.cu", "sha": "bf061987f2519d59", "bytes_per_launch": 1398614000 + 20113152,
                     "dtype": "fp32", "scale": 24, "capture": "profiles/k3_iterate_fp32_scale24.md"},

@@ -19,17 +19,20 @@ namespace {
 struct Knob {
     const char *key;
     std::atomic<int64_t> value;
-    int64_t allowed[4];
+    int n_allowed;
+    int64_t allowed[5];
 };
 Knob g_knobs[] = {
-    {"k3_unroll_f32", {8}, {4, 8, 0, 0}},
-    {"k3_unroll_f64", {8}, {4, 8, 0, 0}},
-    {"k3_minblocks", {4}, {4, 5, 6, 0}},
-    {"k3_shortmax", {256}, {64, 128, 256, 0}},
-    {"k3_chunk", {2048}, {2048, 4096, 0, 0}},
-    {"k3_lane_short", {16}, {8, 16, 32, 0}},
-    {"k3b_shortmax", {256}, {128, 256, 0, 0}},
-    {"k3b_chunk", {512}, {256, 512, 1024, 0}},
+    {"k3_unroll_f32", {8}, 2, {4, 8}},
+    {"k3_unroll_f64", {8}, 2, {4, 8}},
+    {"k3_minblocks", {4}, 3, {4, 5, 6}},
+    {"k3_shortmax", {256}, 3, {64, 128, 256}},
+    {"k3_chunk", {2048}, 2, {2048, 4096}},
+    {"k3_lane_short", {16}, 3, {8, 16, 32}},
+    {"k3_l1bytes", {0}, 4, {0, 65536, 131072, 196608}},
+    {"k3_hot_kb", {0}, 5, {0, 132, 164, 196, 228}},
+    {"k3b_shortmax", {256}, 2, {128, 256}},
+    {"k3b_chunk", {512}, 3, {256, 512, 1024}},
 };
 Knob *find_knob(const char *key) {
     if (!key) return nullptr;
@@ -50,8 +53,8 @@ using namespace pp;
 extern "C" pp_status pp_set_tuning(const char *key, int64_t value) {
     Knob *k = find_knob(key);
     if (!k) return PP_ERR_INVALID_ARG;
-    for (int64_t a : k->allowed)
-        if (a && a == value) {
+    for (int i = 0; i < k->n_allowed; ++i)
+        if (k->allowed[i] == value) {
             k->value.store(value);
             return PP_OK;
         }
