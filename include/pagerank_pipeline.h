@@ -343,7 +343,9 @@ uint64_t pp_launch_count(void);
  *                    many KB of the SM's shared-memory / L1 array and fills
  *                    what its slabs leave with the first rows of the gathered
  *                    vector, read from there: 0, 132, 164, 196 or 228
- *                    (default 0)
+ *                    (default 0).  Used from scale 21 (binary32 ranks), 23
+ *                    (binary64) and 24 (bfloat16 x) on; smaller graphs keep
+ *                    the four-block kernel.
  *   "k3_l1bytes"     the next this-many bytes of the vector are gathered
  *                    through L1, the rest around it: 65536, 131072 or 196608;
  *                    0 = every row through L1 (default 0)

@@ -39,6 +39,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "fixedpoint.cuh"
 #include "pp_common.cuh"
@@ -51,6 +52,15 @@ namespace k3 {
 constexpr int THREADS = 256;
 constexpr int WARPS = THREADS / 32;
 constexpr int HOT_THREADS = 1024;  // one block per SM when x's first rows sit in shared memory
+// The hot kernel (k3_hot_kb) serves large graphs only: it trades L1 for
+// the shared-memory rows, and below these scales (measured on GB300: where
+// the two kernels cross, per precision, whose slabs take different shares
+// of the array) the L1 it gives up is worth more than the rows it holds.
+template <typename TS, typename TA>
+inline bool use_hot(uint32_t scale) {
+    const uint32_t min_scale = sizeof(TA) == 8 ? 23u : (sizeof(TS) == 2 ? 24u : 21u);
+    return tuning("k3_hot_kb") != 0 && scale >= min_scale;
+}
 constexpr int TILE_COLS = 32;      // one lane per column in a tile
 constexpr int SHORTMAX_MAX = 256;  // largest long-column threshold (k3_shortmax)
 constexpr int TILE_ENTRIES = 2 * SHORTMAX_MAX;
@@ -801,9 +811,17 @@ pp_status run_unroll(const pp_graph *g, const double *r0, uint32_t iters, double
     auto *k_last = iterate_kernel<TS, TA, TO, !EXT, UNROLL, MINB, EXT, HOT>;
     constexpr int NT = HOT ? HOT_THREADS : THREADS;
     const size_t smem = Smem<TA>::hot(NT / 32) + (size_t)a.hot * sizeof(TS);
-    set_smem(k_mid, HOT ? 1 : MINB, smem);
-    set_smem(k_last, HOT ? 1 : MINB, smem);
-    const int o_mid = occupancy(k_mid, NT, smem), o_last = occupancy(k_last, NT, smem);
+    // the attributes and the occupancy only change with the shared-memory size
+    static std::atomic<uint64_t> cached{0};  // smem << 32 | o_mid << 16 | o_last, per instantiation
+    uint64_t cv = cached.load();
+    if (cv == 0 || (cv >> 32) != smem) {
+        set_smem(k_mid, HOT ? 1 : MINB, smem);
+        set_smem(k_last, HOT ? 1 : MINB, smem);
+        cv = ((uint64_t)smem << 32) | ((uint64_t)occupancy(k_mid, NT, smem) << 16) |
+             (uint64_t)occupancy(k_last, NT, smem);
+        cached.store(cv);
+    }
+    const int o_mid = (int)((cv >> 16) & 0xffff), o_last = (int)(cv & 0xffff);
     const int sms = sm_count();
     for (uint32_t it = 0; it < iters; ++it) {
         const TS *xin = (it & 1) ? x1 : x0;
@@ -834,7 +852,7 @@ pp_status run(const pp_graph *g, const double *r0, uint32_t iters, double c, pp_
               double *r_l1, const Layout &L, cudaStream_t s) {
     const Variant none{0u, 0.0, nullptr};
     const bool u4 = tuning(sizeof(TA) == 8 ? "k3_unroll_f64" : "k3_unroll_f32") == 4;
-    if (tuning("k3_hot_kb"))
+    if (use_hot<TS, TA>(g->scale))
         return u4 ? run_unroll<TS, TA, TO, 4, 1, false, true>(g, r0, iters, c, dt, r_out, r_l1, L, s, none)
                   : run_unroll<TS, TA, TO, 8, 1, false, true>(g, r0, iters, c, dt, r_out, r_l1, L, s, none);
     switch (tuning("k3_minblocks")) {
@@ -854,7 +872,7 @@ pp_status run(const pp_graph *g, const double *r0, uint32_t iters, double c, pp_
 template <typename TS, typename TA, typename TO>
 pp_status run_ext(const pp_graph *g, const double *r0, uint32_t iters, double c, pp_dtype dt, TO *r_out,
                   double *r_l1, const Layout &L, cudaStream_t s, const Variant &var) {
-    if (tuning("k3_hot_kb"))
+    if (use_hot<TS, TA>(g->scale))
         return run_unroll<TS, TA, TO, 4, 1, true, true>(g, r0, iters, c, dt, r_out, r_l1, L, s, var);
     return run_unroll<TS, TA, TO, 4, 4, true, false>(g, r0, iters, c, dt, r_out, r_l1, L, s, var);
 }

@@ -1,4 +1,5 @@
-"""Parity at full size, in the configuration the benchmark times.
+"""Parity at full size, in the configuration the benchmark times (the
+stored tuning for this GPU applied, as bench.py does).
 
 The oracle cannot rerun a 2^28-edge pipeline within a test, so the checks at
 scale 24 (and 26, when PP_FULLSIZE_26=1) are the definitions evaluated
@@ -61,6 +62,11 @@ def fullsize(request):
     scale = request.param
     if scale == 26 and os.environ.get("PP_FULLSIZE_26") != "1":
         pytest.skip("scale 26 runs with PP_FULLSIZE_26=1 (about 40 GB of host memory)")
+    # the benchmark's launch configuration: the stored tuning for this GPU
+    from paper_1603_01876_gb300 import tune
+
+    saved = {k: pp.get_tuning(k) for k in list(tune.SINGLE_KNOBS) + list(tune.BATCH_KNOBS) + ["k3_unroll_f64"]}
+    tuned = tune.apply()
     N, M = 1 << scale, 16 << scale
     dev = torch.device("cuda", 0)
     u, v = kernel0.edges_device(scale, SEED, device=dev)
@@ -73,7 +79,9 @@ def fullsize(request):
     pp.build_filter_normalize(us, vs, scale, "lowest", graph=g, workspace=ws)
     torch.cuda.synchronize()
     assert pp.last_device_error() == 0
-    return dict(pp=pp, scale=scale, N=N, M=M, u=u, v=v, us=us, vs=vs, g=g, r0=r0, ws=ws)
+    yield dict(pp=pp, scale=scale, N=N, M=M, u=u, v=v, us=us, vs=vs, g=g, r0=r0, ws=ws, tuned=tuned)
+    for k, val in saved.items():
+        pp.set_tuning(k, val)
 
 
 def test_k1_ordered_permutation(fullsize):
