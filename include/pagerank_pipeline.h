@@ -352,6 +352,11 @@ uint64_t pp_launch_count(void);
  *   "k3b_shortmax"   the long-column threshold of the batched Kernel 3:
  *                    128 or 256 (default 256)
  *   "k3b_chunk"      its entries per chunk: 256, 512 or 1024 (default 512)
+ *   "k3b_vec"        1: with 32 start vectors, 8 lanes of the batched Kernel
+ *                    3 share an entry, 4 vectors each (4 entries per warp
+ *                    step); 0: one entry per warp step, a vector per lane
+ *                    (default 1).  The two sum each column in a different
+ *                    (fixed) order.
  * pp_set_tuning returns PP_ERR_INVALID_ARG for an unknown key or value.
  * The autotuner (paper_1603_01876_gb300/tune.py) measures the choices and
  * stores the fastest per device and scale.

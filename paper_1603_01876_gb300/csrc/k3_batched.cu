@@ -17,6 +17,13 @@
 // warp that finishes it), and sum(r) of every (graph, vector) pair is
 // accumulated exactly in 128-bit fixed point, so results do not depend on
 // which warp took which item.
+//
+// With 32 start vectors (k3b_vec), 8 lanes share an entry, each with 4
+// vectors (one 16-byte piece of the gathered row), so a warp takes 4
+// entries per step and the per-entry work (the packed word, the row
+// address, the count) is shared by 4 times as many products.  Entry k of a
+// column goes to slot k mod 4; each slot keeps a compensated sum per vector
+// and the 4 slot sums are added in a fixed shuffle tree.
 #include <algorithm>
 #include <cstring>
 
@@ -461,6 +468,164 @@ __global__ void __launch_bounds__(THREADS) iterate_kernel(const __grid_constant_
     if (cur >= 0 && active && (acc.hi | acc.lo)) fx_atomic_add(acc_next + 2 * (cur * 32 + lane), acc);
 }
 
+// ------------------------------------------------ iteration, 32 start vectors
+
+constexpr int VEC_UNROLL = 2;  // steps of 4 entries in flight per warp
+
+// Compensated sums of the 4 vectors of one lane, for one slot of a column.
+struct KSum4 {
+    KSum v[4];
+    __device__ __forceinline__ void add(float cf, float4 x) {
+        v[0].add(cf * x.x);
+        v[1].add(cf * x.y);
+        v[2].add(cf * x.z);
+        v[3].add(cf * x.w);
+    }
+};
+
+// The slot sums of entries [lo, hi) of the staged words ws (a column's
+// entries, or a chunk of one), slot = entry index mod 4 counted from lo.
+// `col` is the column position, for a count that did not fit inline.
+__device__ __forceinline__ void vec_accumulate(const BG &G, const uint32_t *ws, uint32_t lo, uint32_t hi,
+                                               const float *xg, uint32_t col, int slot, int quad, uint64_t keep,
+                                               KSum4 &ks) {
+    const uint32_t umask = (1u << G.scale) - 1u;
+    for (uint32_t k = lo + slot; k < hi; k += 4 * VEC_UNROLL) {
+        uint32_t wk[VEC_UNROLL];
+        float4 xv[VEC_UNROLL];
+#pragma unroll
+        for (int m = 0; m < VEC_UNROLL; ++m) {
+            const uint32_t kk = k + 4 * m;
+            wk[m] = kk < hi ? ws[kk] : 0u;
+            xv[m] = kk < hi ? ld_hint4(xg + (uint64_t)(wk[m] & umask) * 32u + 4 * quad, keep)
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int m = 0; m < VEC_UNROLL; ++m) {
+            if (k + 4 * m < hi) {
+                uint32_t cf = wk[m] >> G.scale;
+                if (cf == G.cmax)
+                    cf = ovf_lookup(G.ovf_key, G.ovf_cnt, G.info[PP_INFO_NOVF],
+                                    ((uint64_t)__ldg(G.iperm + (wk[m] & umask)) << 32) | __ldg(G.iperm + col));
+                ks.add((float)cf, xv[m]);
+            }
+        }
+    }
+}
+
+// The column total of vector `lane` from the slot sums: the 4 slots added in
+// a fixed tree (all lanes of a quad then hold its 4 totals), then each lane
+// takes its own vector from the quad that holds it.
+__device__ __forceinline__ float vec_total(const KSum4 &ks, int lane) {
+    float t[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        t[j] = ks.v[j].s;
+        t[j] += __shfl_xor_sync(0xffffffffu, t[j], 8);
+        t[j] += __shfl_xor_sync(0xffffffffu, t[j], 16);
+    }
+    const int src = lane >> 2;  // slot 0, quad lane / 4
+    const float y0 = __shfl_sync(0xffffffffu, t[0], src), y1 = __shfl_sync(0xffffffffu, t[1], src);
+    const float y2 = __shfl_sync(0xffffffffu, t[2], src), y3 = __shfl_sync(0xffffffffu, t[3], src);
+    const int j = lane & 3;
+    return j == 0 ? y0 : (j == 1 ? y1 : (j == 2 ? y2 : y3));
+}
+
+template <bool LAST>
+__global__ void __launch_bounds__(THREADS) iterate_vec_kernel(const __grid_constant__ Desc d, Ws w,
+                                                              const float *x_in, float *x_out, float *r_out,
+                                                              uint32_t iter) {
+    __shared__ uint32_t s_rowc[WARPS][TILE_ENTRIES];
+    __shared__ uint32_t s_cp[WARPS][TILE_COLS + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int quad = lane & 7, slot = lane >> 3;
+    const uint32_t n_items = w.ctl[0];
+    const uint32_t nwarps = gridDim.x * WARPS;
+    const float cc = (float)d.c;
+    const uint64_t keep = policy_evict_last(), stream = policy_evict_first();
+    uint32_t *rowc_s = s_rowc[warp];
+    uint32_t *cp = s_cp[warp];
+    unsigned long long *acc_now = w.acc + 2ull * iter * d.ng * 32;
+    unsigned long long *acc_next = w.acc + 2ull * (iter + 1) * d.ng * 32;
+
+    int cur = -1;
+    Fx128 acc{0, 0};
+    float tele = 0.f;
+    int E = 1;
+    for (uint32_t item = blockIdx.x * WARPS + warp; item < n_items; item += nwarps) {
+        const uint4 it = __ldg(w.item + item);
+        const int g = __ldg(w.item_g + item);
+        if (g != cur) {
+            if (cur >= 0 && (acc.hi | acc.lo)) fx_atomic_add(acc_next + 2 * (cur * 32 + lane), acc);
+            acc = Fx128{0, 0};
+            cur = g;
+            const int sl = g * 32 + lane;
+            const double S = fx_value(acc_now[2 * sl], acc_now[2 * sl + 1], w.fx_exp[iter * d.ng * 32 + sl]);
+            E = fx_exponent(S);
+            tele = (float)(((1.0 - d.c) / (double)d.g[g].N) * S);
+            if (item == w.first_item[g]) w.fx_exp[(iter + 1) * d.ng * 32 + sl] = E;
+        }
+        const BG &G = d.g[g];
+        const float *xg = x_in + G.row0 * 32u;
+        float *xo = x_out + G.row0 * 32u;
+        float *ro = r_out + G.row0 * 32u;
+        const float *invp = w.invp + G.row0;
+        // col is a column position (vertex iperm[col]); r_out is in vertex order; lane = vector
+        auto epi = [&](uint32_t col, float y, float invc) {
+            const float r = cc * y + tele;
+            if (LAST) ro[(uint64_t)__ldg(G.iperm + col) * 32u + lane] = r;
+            st_hint(xo + (uint64_t)col * 32u + lane, r * invc, keep);
+            fx_add(acc, r, E);
+        };
+        const uint32_t e0 = it.z;
+        if (it.x & LONG_FLAG) {
+            const uint32_t col = it.x & ~LONG_FLAG, first = it.y;
+            const uint32_t nent = it.w & 0xfffu, nchunks = it.w >> 12;
+            KSum4 ks{};
+            for (uint32_t b = 0; b < nent; b += TILE_ENTRIES) {
+                const uint32_t n = min((uint32_t)TILE_ENTRIES, nent - b);
+                for (uint32_t k = lane; k < n; k += 32) rowc_s[k] = ld_stream_u32(G.rowc + e0 + b + k, stream);
+                __syncwarp();
+                vec_accumulate(G, rowc_s, 0, n, xg, col, slot, quad, keep, ks);
+                __syncwarp();
+            }
+            const float y = vec_total(ks, lane);
+            if (nchunks == 1) {
+                epi(col, y, invp[col]);
+            } else {
+                // the warp finishing the column's last chunk adds the chunk sums in order
+                w.chunk_sum[(uint64_t)item * 32u + lane] = y;
+                __threadfence();
+                __syncwarp();
+                uint32_t t = 0;
+                if (lane == 0) t = atomicAdd(w.ticket + first, 1u);
+                t = __shfl_sync(0xffffffffu, t, 0);
+                if ((t + 1) % nchunks == 0) {
+                    __threadfence();
+                    KSum tot{0.f, 0.f};
+                    for (uint32_t q = 0; q < nchunks; ++q)
+                        tot.add(__ldcg(w.chunk_sum + (uint64_t)(first + q) * 32u + lane));
+                    epi(col, tot.s, invp[col]);
+                }
+            }
+        } else {
+            const uint32_t c0 = it.x, ncol = it.y, nent = it.w;
+            if (lane < (int)ncol) cp[lane] = ld_stream_u32(G.colptr + c0 + lane, stream) - e0;
+            if (lane == 0) cp[ncol] = nent;
+            const float myinv = lane < (int)ncol ? invp[c0 + lane] : 0.f;
+            for (uint32_t k = lane; k < nent; k += 32) rowc_s[k] = ld_stream_u32(G.rowc + e0 + k, stream);
+            __syncwarp();
+            for (uint32_t ci = 0; ci < ncol; ++ci) {
+                KSum4 ks{};
+                vec_accumulate(G, rowc_s, cp[ci], cp[ci + 1], xg, c0 + ci, slot, quad, keep, ks);
+                epi(c0 + ci, vec_total(ks, lane), __shfl_sync(0xffffffffu, myinv, ci));
+            }
+            __syncwarp();
+        }
+    }
+    if (cur >= 0 && (acc.hi | acc.lo)) fx_atomic_add(acc_next + 2 * (cur * 32 + lane), acc);
+}
+
 // ------------------------------------------------------------------- host
 
 struct Layout {
@@ -589,18 +754,29 @@ extern "C" pp_status pp_pagerank_batched(const pp_graph *gs, uint32_t n_graphs, 
     k3b::plan_kernel<<<(unsigned)ceil_div(rows, k3b::PLAN_TILE), k3b::PLAN_THREADS, 0, s>>>(d, w);
     k3b::plan_items_kernel<<<(unsigned)std::min<uint64_t>(ceil_div(rows, 256), 4096), 256, 0, s>>>(d, w);
     count_launch(6);
-    static int o_mid = 0, o_last = 0;
+    static int o_mid = 0, o_last = 0, v_mid = 0, v_last = 0;
     if (!o_mid) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o_mid, k3b::iterate_kernel<false>, k3b::THREADS, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o_last, k3b::iterate_kernel<true>, k3b::THREADS, 0);
-        o_mid = o_mid > 0 ? o_mid : 1;
-        o_last = o_last > 0 ? o_last : 1;
+        auto occ = [](auto kernel) {
+            int o = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kernel, k3b::THREADS, 0);
+            return o > 0 ? o : 1;
+        };
+        o_mid = occ(k3b::iterate_kernel<false>);
+        o_last = occ(k3b::iterate_kernel<true>);
+        v_mid = occ(k3b::iterate_vec_kernel<false>);
+        v_last = occ(k3b::iterate_vec_kernel<true>);
     }
+    const bool vec = nrhs == 32 && tuning("k3b_vec") != 0;
     const int sms = sm_count();
     for (uint32_t it = 0; it < iters; ++it) {
         const float *xin = w.x[it & 1];
         float *xout = w.x[(it + 1) & 1];
-        if (it + 1 == iters)
+        const bool last = it + 1 == iters;
+        if (vec && last)
+            k3b::iterate_vec_kernel<true><<<sms * v_last, k3b::THREADS, 0, s>>>(d, w, xin, xout, r_out, it);
+        else if (vec)
+            k3b::iterate_vec_kernel<false><<<sms * v_mid, k3b::THREADS, 0, s>>>(d, w, xin, xout, r_out, it);
+        else if (last)
             k3b::iterate_kernel<true><<<sms * o_last, k3b::THREADS, 0, s>>>(d, w, xin, xout, r_out, it);
         else
             k3b::iterate_kernel<false><<<sms * o_mid, k3b::THREADS, 0, s>>>(d, w, xin, xout, r_out, it);

@@ -33,6 +33,7 @@ Knob g_knobs[] = {
     {"k3_hot_kb", {0}, 5, {0, 132, 164, 196, 228}},
     {"k3b_shortmax", {256}, 2, {128, 256}},
     {"k3b_chunk", {512}, 3, {256, 512, 1024}},
+    {"k3b_vec", {1}, 2, {0, 1}},
 };
 Knob *find_knob(const char *key) {
     if (!key) return nullptr;

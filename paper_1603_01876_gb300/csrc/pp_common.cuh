@@ -119,6 +119,13 @@ __device__ __forceinline__ double ld_hint(const double *ptr, uint64_t pol) {
     asm volatile("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(ptr), "l"(pol));
     return v;
 }
+__device__ __forceinline__ float4 ld_hint4(const float *ptr, uint64_t pol) {  // 16-byte aligned
+    float4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(ptr), "l"(pol));
+    return v;
+}
 // The same loads without allocating in L1 (the line goes to the register file
 // from L2 and does not displace lines other warps will reuse).
 __device__ __forceinline__ float ld_hint_na(const float *ptr, uint64_t pol) {

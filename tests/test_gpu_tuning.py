@@ -21,7 +21,8 @@ SINGLE = [
     {"k3_hot_kb": 164, "k3_l1bytes": 65536},
     {"k3_hot_kb": 228, "k3_unroll_f32": 4, "k3_unroll_f64": 4},
 ]
-BATCHED = [{"k3b_shortmax": 128, "k3b_chunk": 256}, {"k3b_chunk": 1024}]
+BATCHED = [{"k3b_shortmax": 128, "k3b_chunk": 256}, {"k3b_chunk": 1024}, {"k3b_vec": 0},
+           {"k3b_vec": 0, "k3b_chunk": 256}]
 
 
 @pytest.fixture(scope="module")
@@ -77,7 +78,7 @@ def test_batched_knobs(k0, oracle_mod, knobs):
         us, vs = pp.sort_edges(u, v, s)
         graphs.append(pp.build_filter_normalize(us, vs, s))
         edges.append((host_u32(us), host_u32(vs)))
-    nrhs = 3
+    nrhs = 32  # both batched layouts (k3b_vec) apply
     r0 = np.concatenate([np.stack([k0.r0_host(1 << s, 31, graph=i, rhs=j) for j in range(nrhs)], axis=1)
                          for i, s in enumerate(scales)])
     got = _with(pp, knobs, lambda: pp.pagerank_batched(graphs, torch.from_numpy(r0).cuda(), nrhs).cpu().numpy())
