@@ -29,6 +29,7 @@ SINGLE_KNOBS = {
     "k3_unroll_f32": [4, 8],
 }
 BATCH_KNOBS = {
+    "k3b_vec": [1, 0],
     "k3b_shortmax": [128, 256],
     "k3b_chunk": [256, 512, 1024],
 }
