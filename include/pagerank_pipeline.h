@@ -324,8 +324,8 @@ const char *pp_status_string(pp_status status);
 uint64_t pp_launch_count(void);
 
 /*
- * Tuning knobs (process-wide, read when a call is made).  The unroll,
- * block, hot-row and L1 knobs change speed only; the thresholds also
+ * Tuning knobs (process-wide, read when a call is made).  The unroll
+ * and block knobs change speed only; the thresholds also
  * change the order in which some column sums are added, so results move
  * within rounding (every setting meets the stated tolerances, and one
  * setting always gives the same bits):
@@ -339,16 +339,6 @@ uint64_t pp_launch_count(void);
  *   "k3_chunk"       entries per chunk of a long column: 2048 or 4096 (default 2048)
  *   "k3_lane_short"  tile columns up to this long are summed by one lane,
  *                    longer ones by the whole warp: 8, 16 or 32 (default 16)
- *   "k3_hot_kb"      nonzero: one 1024-thread Kernel 3 block per SM takes this
- *                    many KB of the SM's shared-memory / L1 array and fills
- *                    what its slabs leave with the first rows of the gathered
- *                    vector, read from there: 0, 132, 164, 196 or 228
- *                    (default 0).  Used from scale 21 (binary32 ranks), 23
- *                    (binary64) and 24 (bfloat16 x) on; smaller graphs keep
- *                    the four-block kernel.
- *   "k3_l1bytes"     the next this-many bytes of the vector are gathered
- *                    through L1, the rest around it: 65536, 131072 or 196608;
- *                    0 = every row through L1 (default 0)
  *   "k3b_shortmax"   the long-column threshold of the batched Kernel 3:
  *                    128 or 256 (default 256)
  *   "k3b_chunk"      its entries per chunk: 256, 512 or 1024 (default 512)

@@ -25,14 +25,8 @@
 //     medium column (lanes stride, fixed shuffle tree).
 // shortmax, chunk and lane_short are tuning knobs (k3_shortmax, k3_chunk,
 // k3_lane_short); for one setting every run gives the same bits.
-// The storage order puts the rows gathered most often first, so a row's
-// position tells how often its line will be reused.  With k3_hot_kb set, one
-// 1024-thread block per SM takes that much of the SM's shared-memory / L1
-// array, fills what its slabs leave with the first rows of x and reads those
-// rows from there (a warp's 32 gathers then cost a few bank cycles instead
-// of up to 32 L1 lookups); the next k3_l1bytes of x are gathered through
-// L1, and the rest with L1::no_allocate so they do not evict reused lines.
-// Blocks reserve no more shared memory than they use; the rest is L1.
+// Blocks reserve no more shared memory than they use; the rest of the SM's
+// shared-memory / L1 array is L1.
 // Items are dealt to warps round-robin.  Every column sum has a fixed order
 // and sum(r) is accumulated exactly in 128-bit fixed point, so results are
 // bitwise reproducible whichever warp takes which item.
@@ -51,16 +45,6 @@ namespace k3 {
 
 constexpr int THREADS = 256;
 constexpr int WARPS = THREADS / 32;
-constexpr int HOT_THREADS = 1024;  // one block per SM when x's first rows sit in shared memory
-// The hot kernel (k3_hot_kb) serves large graphs only: it trades L1 for
-// the shared-memory rows, and below these scales (measured on GB300: where
-// the two kernels cross, per precision, whose slabs take different shares
-// of the array) the L1 it gives up is worth more than the rows it holds.
-template <typename TS, typename TA>
-inline bool use_hot(uint32_t scale) {
-    const uint32_t min_scale = sizeof(TA) == 8 ? 23u : (sizeof(TS) == 2 ? 24u : 21u);
-    return tuning("k3_hot_kb") != 0 && scale >= min_scale;
-}
 constexpr int TILE_COLS = 32;      // one lane per column in a tile
 constexpr int SHORTMAX_MAX = 256;  // largest long-column threshold (k3_shortmax)
 constexpr int TILE_ENTRIES = 2 * SHORTMAX_MAX;
@@ -113,8 +97,6 @@ struct Args {
     uint32_t shortmax;    // columns longer than this are cut into chunks (power of two)
     uint32_t chunk;       // entries of a long column per work item
     uint32_t lane_short;  // tile columns up to this long are summed by one lane
-    uint32_t l1rows;      // rows of x below this position are gathered through L1
-    uint32_t hot;         // rows [0, hot) of x are read from shared memory (hot kernels only)
     // variants (pp_pagerank_ex); zero / null for the plain iteration
     uint32_t flags;                  // PP_K3_DANGLING | PP_K3_CONVERGE
     double tol;                      // convergence threshold on norm(r_k - r_(k-1), 1)
@@ -317,16 +299,6 @@ __device__ __forceinline__ double ld_x(const double *p, uint64_t pol) { return l
 __device__ __forceinline__ __nv_bfloat16 ld_x(const __nv_bfloat16 *p, uint64_t pol) {
     return __ushort_as_bfloat16(ld_hint_b16(p, pol));
 }
-__device__ __forceinline__ float ld_x_na(const float *p, uint64_t pol) { return ld_hint_na(p, pol); }
-__device__ __forceinline__ double ld_x_na(const double *p, uint64_t pol) { return ld_hint_na(p, pol); }
-__device__ __forceinline__ __nv_bfloat16 ld_x_na(const __nv_bfloat16 *p, uint64_t pol) {
-    return __ushort_as_bfloat16(ld_hint_na_b16(p, pol));
-}
-// x(p): through L1 for the hot rows, around it for the others
-template <typename TS>
-__device__ __forceinline__ TS gather_x(const TS *x, uint32_t p, uint32_t l1rows, uint64_t pol) {
-    return p < l1rows ? ld_x(x + p, pol) : ld_x_na(x + p, pol);
-}
 __device__ __forceinline__ void st_x(float *p, float v, uint64_t pol) { st_hint(p, v, pol); }
 __device__ __forceinline__ void st_x(double *p, double v, uint64_t pol) { st_hint(p, v, pol); }
 __device__ __forceinline__ void st_x(__nv_bfloat16 *p, __nv_bfloat16 v, uint64_t pol) {
@@ -394,20 +366,20 @@ __device__ __forceinline__ TA warp_sum(TA y) {
 }
 
 // Dynamic shared memory of iterate_kernel: the per-warp product slabs and
-// column starts, the block-sum scratch, then (hot kernels) x's first rows.
+// column starts, then the block-sum scratch.
 template <typename TA>
 struct Smem {
     static constexpr size_t cp(int nw) { return (size_t)nw * TILE_ENTRIES * sizeof(TA); }
     static constexpr size_t fx(int nw) { return (cp(nw) + (size_t)nw * (TILE_COLS + 1) * 4 + 15) & ~(size_t)15; }
-    static constexpr size_t hot(int nw) { return fx(nw) + (size_t)nw * 2 * 8; }
+    static constexpr size_t total(int nw) { return fx(nw) + (size_t)nw * 2 * 8; }
 };
 
-template <typename TS, typename TA, typename TO, bool LAST, int UNROLL, int MINB, bool EXT, bool HOT>
-__global__ void __launch_bounds__(HOT ? HOT_THREADS : THREADS, HOT ? 1 : MINB)
+template <typename TS, typename TA, typename TO, bool LAST, int UNROLL, int MINB, bool EXT>
+__global__ void __launch_bounds__(THREADS, MINB)
     iterate_kernel(Args a, const TA *inv, const TS *__restrict__ x_in, TS *__restrict__ x_out, TO *r_out,
                    uint32_t iter, const TA *rb_in, TA *rb_out) {
     static_assert(TILE_ENTRIES % (32 * UNROLL) == 0, "unroll must divide the work");
-    constexpr int NT = HOT ? HOT_THREADS : THREADS, NW = NT / 32;
+    constexpr int NT = THREADS, NW = WARPS;
     extern __shared__ __align__(16) unsigned char k3_smem[];
     uint64_t *s_fx = reinterpret_cast<uint64_t *>(k3_smem + Smem<TA>::fx(NW));
 
@@ -431,7 +403,7 @@ __global__ void __launch_bounds__(HOT ? HOT_THREADS : THREADS, HOT ? 1 : MINB)
     const double S = fx_value(a.acc[2 * iter], a.acc[2 * iter + 1], a.fx_exp[iter]);
     const int E = fx_exponent(S);
     if (blockIdx.x == 0 && threadIdx.x == 0) a.fx_exp[iter + 1] = E;
-    const uint32_t umask = (1u << a.scale) - 1u, l1rows = a.l1rows;
+    const uint32_t umask = (1u << a.scale) - 1u;
     const uint64_t keep = policy_evict_last(), stream = policy_evict_first();
     const Epilogue<TS, TA, TO, LAST, EXT> epi{inv,
                                               x_out,
@@ -447,17 +419,6 @@ __global__ void __launch_bounds__(HOT ? HOT_THREADS : THREADS, HOT ? 1 : MINB)
                                               a.flags};
     TA *prod = reinterpret_cast<TA *>(k3_smem) + warp * TILE_ENTRIES;
     uint32_t *cp = reinterpret_cast<uint32_t *>(k3_smem + Smem<TA>::cp(NW)) + warp * (TILE_COLS + 1);
-    TS *s_x = reinterpret_cast<TS *>(k3_smem + Smem<TA>::hot(NW));
-    const uint32_t hot = HOT ? a.hot : 0u;
-    if (HOT) {
-        // x's first `hot` rows into shared memory (16-byte pieces, then the tail)
-        const uint32_t nvec = (uint32_t)((uint64_t)hot * sizeof(TS) / 16);
-        const uint4 *src = reinterpret_cast<const uint4 *>(x_in);
-        uint4 *dst = reinterpret_cast<uint4 *>(s_x);
-        for (uint32_t i = threadIdx.x; i < nvec; i += NT) dst[i] = __ldg(src + i);
-        for (uint32_t i = nvec * (uint32_t)(16 / sizeof(TS)) + threadIdx.x; i < hot; i += NT) s_x[i] = x_in[i];
-        __syncthreads();
-    }
     Sums acc{{0, 0}, {0, 0}, {0, 0}};
     const uint32_t nwarps = gridDim.x * NW;
 
@@ -484,9 +445,7 @@ __global__ void __launch_bounds__(HOT ? HOT_THREADS : THREADS, HOT ? 1 : MINB)
 #pragma unroll
                 for (int m = 0; m < UNROLL; ++m) {
                     const uint32_t k = base + (uint32_t)(m * 32 + lane);
-                    const uint32_t p = w[m] & umask;
-                    xv[m] = k < nent ? (HOT && p < hot ? to_acc(s_x[p]) : to_acc(gather_x(x_in, p, l1rows, keep)))
-                                     : TA(0);
+                    xv[m] = k < nent ? to_acc(ld_x(x_in + (w[m] & umask), keep)) : TA(0);
                 }
 #pragma unroll
                 for (int m = 0; m < UNROLL; ++m) {
@@ -530,9 +489,7 @@ __global__ void __launch_bounds__(HOT ? HOT_THREADS : THREADS, HOT ? 1 : MINB)
 #pragma unroll
                 for (int m = 0; m < UNROLL; ++m) {
                     const uint32_t k = (uint32_t)((g + m) * 32 + lane);
-                    const uint32_t p = w[m] & umask;
-                    xv[m] = k < nent ? (HOT && p < hot ? to_acc(s_x[p]) : to_acc(gather_x(x_in, p, l1rows, keep)))
-                                     : TA(0);
+                    xv[m] = k < nent ? to_acc(ld_x(x_in + (w[m] & umask), keep)) : TA(0);
                 }
                 if (g == 0) {
                     if (lane < (int)ncol) cp[lane] = mycp - e0;
@@ -720,8 +677,7 @@ inline int device_attr(cudaDeviceAttr attr) {
 // `blocks` blocks plus the 1 KB the system keeps per block.  The hint is a
 // whole percentage of the largest size, which the driver rounds up to a
 // supported size, so it is rounded down here: a percentage rounded up could
-// land just past the wanted size and take the next one.  Hot kernels also
-// raise their dynamic limit.
+// land just past the wanted size and take the next one.
 template <typename K>
 inline void set_smem(K kernel, int blocks, size_t smem) {
     static const long kSizesKB[] = {0, 8, 16, 32, 64, 100, 132, 164, 196, 228};
@@ -737,18 +693,6 @@ inline void set_smem(K kernel, int blocks, size_t smem) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
 }
 
-// Rows of x a hot block holds: what its slabs leave of `kb` KB of shared
-// memory (less the 1 KB the system keeps, and never above the per-block
-// limit), a multiple of 32, at most N.
-template <typename TS, typename TA>
-inline uint32_t hot_rows(int64_t kb, uint32_t N) {
-    const int64_t fixed = (int64_t)Smem<TA>::hot(HOT_THREADS / 32);
-    const int64_t limit = device_attr(cudaDevAttrMaxSharedMemoryPerBlockOptin);
-    const int64_t room = std::min<int64_t>(kb * 1024 - 1024, limit) - fixed;
-    if (room <= 0) return 0;
-    return (uint32_t)std::min<uint64_t>(((uint64_t)room / sizeof(TS)) & ~31ull, N);
-}
-
 // Variant options of pp_pagerank_ex (EXT kernels only).
 struct Variant {
     uint32_t flags;
@@ -756,7 +700,7 @@ struct Variant {
     uint32_t *iters_done;
 };
 
-template <typename TS, typename TA, typename TO, int UNROLL, int MINB, bool EXT, bool HOT>
+template <typename TS, typename TA, typename TO, int UNROLL, int MINB, bool EXT>
 pp_status run_unroll(const pp_graph *g, const double *r0, uint32_t iters, double c, pp_dtype dt, TO *r_out,
                      double *r_l1, const Layout &L, cudaStream_t s, const Variant &var) {
     const uint32_t N = 1u << g->scale;
@@ -786,9 +730,6 @@ pp_status run_unroll(const pp_graph *g, const double *r0, uint32_t iters, double
     a.shortmax = (uint32_t)tuning("k3_shortmax");
     a.chunk = (uint32_t)tuning("k3_chunk");
     a.lane_short = (uint32_t)tuning("k3_lane_short");
-    a.hot = HOT ? hot_rows<TS, TA>(tuning("k3_hot_kb"), N) : 0u;
-    const int64_t l1bytes = tuning("k3_l1bytes");  // rows past the hot ones
-    a.l1rows = l1bytes ? (uint32_t)std::min<int64_t>(a.hot + l1bytes / (int64_t)sizeof(TS), N) : N;
     a.flags = EXT ? var.flags : 0u;
     a.tol = var.tol;
     a.dmass = L.dmass;
@@ -807,21 +748,20 @@ pp_status run_unroll(const pp_graph *g, const double *r0, uint32_t iters, double
     normalize_kernel<TS, TA, TO><<<SETUP_BLOCKS, 256, 0, s>>>(a, r0, inv, invp, x0, r_out, EXT ? rb0 : nullptr);
     count_launch(4);
 
-    auto *k_mid = iterate_kernel<TS, TA, TO, false, UNROLL, MINB, EXT, HOT>;
-    auto *k_last = iterate_kernel<TS, TA, TO, !EXT, UNROLL, MINB, EXT, HOT>;
-    constexpr int NT = HOT ? HOT_THREADS : THREADS;
-    const size_t smem = Smem<TA>::hot(NT / 32) + (size_t)a.hot * sizeof(TS);
-    // the attributes and the occupancy only change with the shared-memory size
-    static std::atomic<uint64_t> cached{0};  // smem << 32 | o_mid << 16 | o_last, per instantiation
-    uint64_t cv = cached.load();
-    if (cv == 0 || (cv >> 32) != smem) {
-        set_smem(k_mid, HOT ? 1 : MINB, smem);
-        set_smem(k_last, HOT ? 1 : MINB, smem);
-        cv = ((uint64_t)smem << 32) | ((uint64_t)occupancy(k_mid, NT, smem) << 16) |
-             (uint64_t)occupancy(k_last, NT, smem);
+    auto *k_mid = iterate_kernel<TS, TA, TO, false, UNROLL, MINB, EXT>;
+    auto *k_last = iterate_kernel<TS, TA, TO, !EXT, UNROLL, MINB, EXT>;
+    constexpr int NT = THREADS;
+    constexpr size_t smem = Smem<TA>::total(WARPS);
+    // the carveout attributes and the occupancy, once per instantiation
+    static std::atomic<uint32_t> cached{0};  // o_mid << 16 | o_last
+    uint32_t cv = cached.load();
+    if (cv == 0) {
+        set_smem(k_mid, MINB, smem);
+        set_smem(k_last, MINB, smem);
+        cv = ((uint32_t)occupancy(k_mid, NT, smem) << 16) | (uint32_t)occupancy(k_last, NT, smem);
         cached.store(cv);
     }
-    const int o_mid = (int)((cv >> 16) & 0xffff), o_last = (int)(cv & 0xffff);
+    const int o_mid = (int)(cv >> 16), o_last = (int)(cv & 0xffff);
     const int sms = sm_count();
     for (uint32_t it = 0; it < iters; ++it) {
         const TS *xin = (it & 1) ? x1 : x0;
@@ -852,29 +792,24 @@ pp_status run(const pp_graph *g, const double *r0, uint32_t iters, double c, pp_
               double *r_l1, const Layout &L, cudaStream_t s) {
     const Variant none{0u, 0.0, nullptr};
     const bool u4 = tuning(sizeof(TA) == 8 ? "k3_unroll_f64" : "k3_unroll_f32") == 4;
-    if (use_hot<TS, TA>(g->scale))
-        return u4 ? run_unroll<TS, TA, TO, 4, 1, false, true>(g, r0, iters, c, dt, r_out, r_l1, L, s, none)
-                  : run_unroll<TS, TA, TO, 8, 1, false, true>(g, r0, iters, c, dt, r_out, r_l1, L, s, none);
     switch (tuning("k3_minblocks")) {
         case 5:
-            return u4 ? run_unroll<TS, TA, TO, 4, 5, false, false>(g, r0, iters, c, dt, r_out, r_l1, L, s, none)
-                      : run_unroll<TS, TA, TO, 8, 5, false, false>(g, r0, iters, c, dt, r_out, r_l1, L, s, none);
+            return u4 ? run_unroll<TS, TA, TO, 4, 5, false>(g, r0, iters, c, dt, r_out, r_l1, L, s, none)
+                      : run_unroll<TS, TA, TO, 8, 5, false>(g, r0, iters, c, dt, r_out, r_l1, L, s, none);
         case 6:
-            return u4 ? run_unroll<TS, TA, TO, 4, 6, false, false>(g, r0, iters, c, dt, r_out, r_l1, L, s, none)
-                      : run_unroll<TS, TA, TO, 8, 6, false, false>(g, r0, iters, c, dt, r_out, r_l1, L, s, none);
+            return u4 ? run_unroll<TS, TA, TO, 4, 6, false>(g, r0, iters, c, dt, r_out, r_l1, L, s, none)
+                      : run_unroll<TS, TA, TO, 8, 6, false>(g, r0, iters, c, dt, r_out, r_l1, L, s, none);
         default:
-            return u4 ? run_unroll<TS, TA, TO, 4, 4, false, false>(g, r0, iters, c, dt, r_out, r_l1, L, s, none)
-                      : run_unroll<TS, TA, TO, 8, 4, false, false>(g, r0, iters, c, dt, r_out, r_l1, L, s, none);
+            return u4 ? run_unroll<TS, TA, TO, 4, 4, false>(g, r0, iters, c, dt, r_out, r_l1, L, s, none)
+                      : run_unroll<TS, TA, TO, 8, 4, false>(g, r0, iters, c, dt, r_out, r_l1, L, s, none);
     }
 }
 
-// The variants run unroll 4: four blocks per SM, or one hot block.
+// The variants run one instantiation (unroll 4, 4 blocks per SM).
 template <typename TS, typename TA, typename TO>
 pp_status run_ext(const pp_graph *g, const double *r0, uint32_t iters, double c, pp_dtype dt, TO *r_out,
                   double *r_l1, const Layout &L, cudaStream_t s, const Variant &var) {
-    if (use_hot<TS, TA>(g->scale))
-        return run_unroll<TS, TA, TO, 4, 1, true, true>(g, r0, iters, c, dt, r_out, r_l1, L, s, var);
-    return run_unroll<TS, TA, TO, 4, 4, true, false>(g, r0, iters, c, dt, r_out, r_l1, L, s, var);
+    return run_unroll<TS, TA, TO, 4, 4, true>(g, r0, iters, c, dt, r_out, r_l1, L, s, var);
 }
 
 }  // namespace k3

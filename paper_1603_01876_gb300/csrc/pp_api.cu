@@ -29,8 +29,6 @@ Knob g_knobs[] = {
     {"k3_shortmax", {256}, 3, {64, 128, 256}},
     {"k3_chunk", {2048}, 2, {2048, 4096}},
     {"k3_lane_short", {16}, 3, {8, 16, 32}},
-    {"k3_l1bytes", {0}, 4, {0, 65536, 131072, 196608}},
-    {"k3_hot_kb", {0}, 5, {0, 132, 164, 196, 228}},
     {"k3b_shortmax", {256}, 2, {128, 256}},
     {"k3b_chunk", {512}, 3, {256, 512, 1024}},
     {"k3b_vec", {1}, 2, {0, 1}},

@@ -126,23 +126,6 @@ __device__ __forceinline__ float4 ld_hint4(const float *ptr, uint64_t pol) {  //
                  : "l"(ptr), "l"(pol));
     return v;
 }
-// The same loads without allocating in L1 (the line goes to the register file
-// from L2 and does not displace lines other warps will reuse).
-__device__ __forceinline__ float ld_hint_na(const float *ptr, uint64_t pol) {
-    float v;
-    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(ptr), "l"(pol));
-    return v;
-}
-__device__ __forceinline__ double ld_hint_na(const double *ptr, uint64_t pol) {
-    double v;
-    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(ptr), "l"(pol));
-    return v;
-}
-__device__ __forceinline__ unsigned short ld_hint_na_b16(const void *ptr, uint64_t pol) {
-    unsigned short v;
-    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(v) : "l"(ptr), "l"(pol));
-    return v;
-}
 __device__ __forceinline__ unsigned short ld_hint_b16(const void *ptr, uint64_t pol) {
     unsigned short v;
     asm volatile("ld.global.nc.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(v) : "l"(ptr), "l"(pol));

@@ -1,9 +1,8 @@
 """Autotuner for Kernel 3's work split (the knobs of pp_set_tuning).
 
 The thresholds that decide which columns are cut into chunks, how long a
-chunk is, which tile columns one lane sums, plus the unroll depth, the
-register budget, the shared memory given to the most-gathered rows and the
-rows gathered through L1, are measured on the GPU at hand: each setting runs the
+chunk is, which tile columns one lane sums, plus the unroll depth and the
+register budget, are measured on the GPU at hand: each setting runs the
 20-iteration Kernel 3 on a graph of the requested scale (CUDA events, after
 warm-up) and the fastest setting is kept.  The single-vector search is a
 coordinate descent over the knobs (two rounds), the batched one a full grid.
@@ -20,8 +19,6 @@ import os
 import time
 
 SINGLE_KNOBS = {
-    "k3_hot_kb": [0, 164, 196],
-    "k3_l1bytes": [0, 65536, 131072],
     "k3_shortmax": [64, 128, 256],
     "k3_lane_short": [8, 16, 32],
     "k3_chunk": [2048, 4096],

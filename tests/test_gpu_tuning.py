@@ -16,10 +16,6 @@ SINGLE = [
     {"k3_chunk": 4096, "k3_lane_short": 32},
     {"k3_shortmax": 128, "k3_minblocks": 6, "k3_unroll_f32": 4, "k3_unroll_f64": 4},
     {"k3_minblocks": 5, "k3_chunk": 4096, "k3_shortmax": 64},
-    {"k3_l1bytes": 65536},
-    {"k3_l1bytes": 196608, "k3_unroll_f32": 4, "k3_minblocks": 6},
-    {"k3_hot_kb": 164, "k3_l1bytes": 65536},
-    {"k3_hot_kb": 228, "k3_unroll_f32": 4, "k3_unroll_f64": 4},
 ]
 BATCHED = [{"k3b_shortmax": 128, "k3b_chunk": 256}, {"k3b_chunk": 1024}, {"k3b_vec": 0},
            {"k3b_vec": 0, "k3b_chunk": 256}]
@@ -90,36 +86,3 @@ def test_batched_knobs(k0, oracle_mod, knobs):
             want = oracle_mod.k3_pagerank(R, r0[row[i]:row[i + 1], j], 20, 0.85)
             e = rank_errors(got[row[i]:row[i + 1], j], want)
             assert e["l1"] <= 1e-6 and e["max_rel"] <= 1e-4, (knobs, i, j, e)
-
-
-@pytest.mark.parametrize("scale", [1, 3, 10, 18, 21, 24])
-def test_cache_knobs_bit_identical(k0, scale):
-    """The cache knobs (rows copied to shared memory, rows gathered through L1)
-    change where the same values come from, not what is summed: the results
-    are the same bits.  The hot kernel runs from scale 21 (binary32), 23
-    (binary64) and 24 (bfloat16) on; smaller graphs keep the four-block
-    kernel whatever k3_hot_kb says."""
-    import torch
-
-    import paper_1603_01876_gb300 as pp
-
-    u, v = k0.edges_device(scale, 41)
-    us, vs = pp.sort_edges(u, v, scale)
-    g = pp.build_filter_normalize(us, vs, scale)
-    r0 = torch.from_numpy(k0.r0_host(1 << scale, 41)).cuda()
-    for dtype in ("fp64", "fp32", "bf16"):
-        for unroll in (4, 8):
-            base = {"k3_l1bytes": 0, "k3_hot_kb": 0, "k3_unroll_f32": unroll, "k3_unroll_f64": unroll}
-            want = _with(pp, base, lambda: pp.pagerank(g, r0, 20, 0.85, dtype).cpu().numpy())
-            for hk, l1 in ((0, 65536), (0, 196608), (132, 0), (164, 65536), (228, 131072)):
-                knobs = dict(base, k3_hot_kb=hk, k3_l1bytes=l1)
-                got = _with(pp, knobs, lambda: pp.pagerank(g, r0, 20, 0.85, dtype).cpu().numpy())
-                assert pp.last_device_error() == 0
-                assert np.array_equal(got, want), (scale, dtype, knobs)
-    kw = dict(dangling=True, tol=1e-9)
-    for dtype in ("fp64", "fp32"):
-        a = _with(pp, {"k3_l1bytes": 0, "k3_hot_kb": 0}, lambda: pp.pagerank_ex(g, r0, 60, 0.85, dtype, **kw))
-        for hk in (0, 164):
-            b = _with(pp, {"k3_l1bytes": 65536, "k3_hot_kb": hk}, lambda: pp.pagerank_ex(g, r0, 60, 0.85, dtype, **kw))
-            assert pp.last_device_error() == 0
-            assert np.array_equal(a[0].cpu().numpy(), b[0].cpu().numpy()) and int(a[1]) == int(b[1]), (dtype, hk)
