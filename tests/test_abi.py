@@ -98,3 +98,31 @@ def test_tuning_knobs():
             pp.set_tuning("no_such_knob", 1)
     finally:
         pp.set_tuning("k3_unroll_f32", old)
+
+
+def test_stored_tuning_file_is_accepted():
+    """Every knob the stored GB300 tuning file sets (what bench.py and the
+    full-size tests apply) is a knob the library knows, with an allowed value;
+    the autotuner searches only allowed values."""
+    import json
+
+    import paper_1603_01876_gb300 as pp
+    from paper_1603_01876_gb300 import tune
+
+    with open(tune.DEFAULT_PATH) as f:
+        data = json.load(f)
+    knobs = {}
+    for part in ("single", "batched"):
+        knobs.update(data[part]["knobs"])
+    searched = dict(tune.SINGLE_KNOBS, **tune.BATCH_KNOBS, k3_unroll_f64=[4, 8])
+    assert set(knobs) <= set(searched), set(knobs) - set(searched)
+    for k, values in searched.items():
+        old = pp.get_tuning(k)
+        try:
+            for v in values:
+                pp.set_tuning(k, v)
+            if k in knobs:
+                pp.set_tuning(k, knobs[k])
+                assert pp.get_tuning(k) == knobs[k]
+        finally:
+            pp.set_tuning(k, old)
