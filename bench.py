@@ -124,6 +124,28 @@ def dist_env():
     return world, rank, local
 
 
+def rank_seed(rank):
+    """Each rank generates its own graph and start vector (weak scaling)."""
+    return SEED + rank
+
+
+def max_over_ranks(x, world, device="cpu"):
+    """The largest x over all ranks (the slowest rank's time); x itself on one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, ms):
+    """Whole-job throughput: the units every rank processed over the slowest rank's time (ms)."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 def k3_bytes_per_iter(nnz, N, dtype):
     """Algorithmic bytes of one Kernel 3 iteration: packed entries, column ends,
     one read of each gathered x, 1/d_out, the new x."""
@@ -162,7 +184,7 @@ def run_ours(args):
     scale, iters = args.scale, ITERS
     N = 1 << scale
     M = 16 * N
-    seed = SEED + rank
+    seed = rank_seed(rank)
     u, v = kernel0.edges_device(scale, seed, device=dev)
     r0h = kernel0.r0_host(N, seed)
     r0 = torch.from_numpy(r0h).to(dev)
@@ -210,11 +232,8 @@ def run_ours(args):
         t1.record(stream)
         torch.cuda.synchronize()
     launches = pp.launch_count() - launches0
-    total_ms = t0.elapsed_time(t1)
+    total_ms = max_over_ranks(t0.elapsed_time(t1), world, dev)
     if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
         torch.distributed.barrier()
     k1 = [e[0].elapsed_time(e[1]) for e in evs]
     k2 = [e[1].elapsed_time(e[2]) for e in evs]
@@ -342,11 +361,7 @@ def run_ours(args):
         pp.pipeline_host(uh, vh, scale, r0p, iters, DAMPING, args.dtype, out=rh, info=infoh, workspace=pws)
     te[1].record(stream)
     torch.cuda.synchronize()
-    e2e_ms = te[0].elapsed_time(te[1]) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(te[0].elapsed_time(te[1]) / e2e_steps, world, dev)
 
     nnz, nnz0 = info["nnz"], info["nnz0"]
     peak, peak_kind = _peaks()
@@ -377,7 +392,7 @@ def run_ours(args):
 
     out = {
         "metric": METRIC,
-        "value": world * M / (ms_step * 1e-3),
+        "value": job_rate(M, world, ms_step),
         "unit": "edges/s",
         "n_gpus": world,
         "steps": args.steps,
@@ -411,7 +426,7 @@ def run_ours(args):
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "per_launch": per_launch,
                      "algorithmic_bytes_per_step": dom_bytes},
-        "e2e": {"value": world * M / (e2e_ms * 1e-3), "unit": "edges/s", "ms_per_step": e2e_ms,
+        "e2e": {"value": job_rate(M, world, e2e_ms), "unit": "edges/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": 8 * M + 8 * N, "d2h_bytes_per_step": 4 * N + 8 * pp.INFO_LEN},
         "gpu_launches": launches,
         "clocks": clocks.summary(),
