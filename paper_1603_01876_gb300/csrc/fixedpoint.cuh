@@ -61,6 +61,56 @@ __device__ __forceinline__ void fx_add(Fx128 &a, float x, int E) {
     fx_add_shifted(a, m, (e ? e : 1) - 150 + 100 - E);  // x = m * 2^((e?e:1) - 150)
 }
 
+// x * 2^(100-E) for 0 <= x < 2^(E-1), without branches (the binary64 column
+// sums of Kernel 3, one per matrix entry): the bound keeps the shift at most
+// 46 bits left; bits below 2^(E-100) are dropped.
+__device__ __forceinline__ void fx_add_term(Fx128 &a, double x, int E) {
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    const int e = (int)(b >> 52) & 0x7ff;
+    const uint64_t m = (b & ((1ull << 52) - 1)) | (e ? (1ull << 52) : 0ull);
+    const int sh = (e ? e : 1) - 1075 + 100 - E;
+    const uint64_t l = sh >= 0 ? (m << sh) : (sh > -64 ? (m >> -sh) : 0ull);
+    const uint64_t h = sh > 0 ? (m >> (64 - sh)) : 0ull;
+    fx_add(a, h, l);
+}
+
+// a * 2^(E-100) rounded to the nearest binary64 (ties to even), from integer
+// instructions only; the value must be 0 or in the normal range.
+__device__ __forceinline__ double fx_to_double(Fx128 a, int E) {
+    if (!(a.hi | a.lo)) return 0.0;
+    const int lz = a.hi ? __clzll((long long)a.hi) : 64 + __clzll((long long)a.lo);
+    uint64_t hi = a.hi, lo = a.lo;
+    if (lz >= 64) {
+        hi = lo << (lz - 64);
+        lo = 0;
+    } else if (lz > 0) {
+        hi = (hi << lz) | (lo >> (64 - lz));
+        lo <<= lz;
+    }
+    // the leading one is now bit 63 of hi: 53 bits of mantissa, then the rest
+    uint64_t mant = hi >> 11;
+    const uint64_t rest = hi & 0x7ffull;
+    const bool half = (rest >> 10) & 1ull, sticky = (rest & 0x3ffull) || lo;
+    if (half && (sticky || (mant & 1ull))) ++mant;
+    int ex = 127 - lz + E - 100;  // value = mant * 2^(ex - 52)
+    if (mant >> 53) {
+        mant >>= 1;
+        ++ex;
+    }
+    return __longlong_as_double((long long)((((uint64_t)(ex + 1023)) << 52) | (mant & ((1ull << 52) - 1))));
+}
+
+// Exact sum over a warp, in lane 0.
+__device__ __forceinline__ Fx128 fx_warp_sum(Fx128 a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t h = __shfl_down_sync(0xffffffffu, a.hi, o);
+        const uint64_t l = __shfl_down_sync(0xffffffffu, a.lo, o);
+        fx_add(a, h, l);
+    }
+    return a;
+}
+
 __device__ __forceinline__ double fx_value(uint64_t hi, uint64_t lo, int E) {
     return ldexp((double)hi, E - 36) + ldexp((double)lo, E - 100);
 }

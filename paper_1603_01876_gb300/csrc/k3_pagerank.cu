@@ -350,6 +350,9 @@ struct Epilogue {
 template <typename TA>
 __device__ __forceinline__ TA entry_product(uint32_t w, TA xv, uint32_t col, const Args &a) {
     uint32_t cf = w >> a.scale;
+    // most entries are one edge: x itself, without a conversion and a multiply
+    // on the FP64 pipe (the narrowest one on GB300) for binary64 ranks
+    if (cf == 1u) return xv;
     if (cf == a.cmax) {
         const uint32_t u = w & ((1u << a.scale) - 1u);
         cf = ovf_lookup(a.ovf_key, a.ovf_cnt, a.info[PP_INFO_NOVF],
@@ -364,6 +367,28 @@ __device__ __forceinline__ TA warp_sum(TA y) {
     for (int o = 16; o > 0; o >>= 1) y += __shfl_down_sync(0xffffffffu, y, o);
     return y;  // in lane 0
 }
+
+// A column sum.  Binary32 (and bfloat16 x): float additions in a fixed
+// order.  Binary64: exact 128-bit fixed point scaled by the bound 2^E on
+// sum(r) (every term cf * x(u) <= r(u) <= sum(r)), added with integer
+// instructions and rounded once, because GB300's FP64 pipe is far narrower
+// than its integer pipe; the sum then does not depend on the order either.
+template <typename TA>
+struct ColSum;
+template <>
+struct ColSum<float> {
+    float v = 0.f;
+    __device__ __forceinline__ void add(float x, int) { v += x; }
+    __device__ __forceinline__ float value(int) const { return v; }
+    __device__ __forceinline__ float warp_total(int) const { return warp_sum(v); }  // in lane 0
+};
+template <>
+struct ColSum<double> {
+    Fx128 v{0, 0};
+    __device__ __forceinline__ void add(double x, int E) { fx_add_term(v, x, E); }
+    __device__ __forceinline__ double value(int E) const { return fx_to_double(v, E); }
+    __device__ __forceinline__ double warp_total(int E) const { return fx_to_double(fx_warp_sum(v), E); }
+};
 
 // Dynamic shared memory of iterate_kernel: the per-warp product slabs and
 // column starts, then the block-sum scratch.
@@ -433,7 +458,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
             // ---- one chunk of a long column
             const uint32_t col = it.x & ~LONG_FLAG, first = it.y;
             const uint32_t nent = it.w & ((1u << NENT_BITS) - 1), nchunks = it.w >> NENT_BITS;
-            TA part = TA(0);
+            ColSum<TA> part;
             for (uint32_t base = 0; base < nent; base += 32 * UNROLL) {
                 uint32_t w[UNROLL];
                 TA xv[UNROLL];
@@ -450,10 +475,10 @@ __global__ void __launch_bounds__(THREADS, MINB)
 #pragma unroll
                 for (int m = 0; m < UNROLL; ++m) {
                     const uint32_t k = base + (uint32_t)(m * 32 + lane);
-                    if (k < nent) part += entry_product<TA>(w[m], xv[m], col, a);
+                    if (k < nent) part.add(entry_product<TA>(w[m], xv[m], col, a), E);
                 }
             }
-            const TA y = warp_sum(part);
+            const TA y = part.warp_total(E);
             if (lane == 0) {
                 if (nchunks == 1) {
                     epi(col, y, ld_inv(inv + col, stream), acc);
@@ -527,9 +552,9 @@ __global__ void __launch_bounds__(THREADS, MINB)
             if (lane < (int)ncol) {
                 const uint32_t s = cp[lane], e = cp[lane + 1];
                 if (e - s <= a.lane_short) {
-                    TA y = TA(0);
-                    for (uint32_t k = s; k < e; ++k) y += prod[k];
-                    epi(c0 + lane, y, myinv, acc);
+                    ColSum<TA> y;
+                    for (uint32_t k = s; k < e; ++k) y.add(prod[k], E);
+                    epi(c0 + lane, y.value(E), myinv, acc);
                 } else {
                     medium = 1;
                 }
@@ -540,11 +565,11 @@ __global__ void __launch_bounds__(THREADS, MINB)
                 const int j = __ffs(mm) - 1;
                 mm &= mm - 1;
                 const uint32_t s = cp[j], e = cp[j + 1];
-                TA y = TA(0);
-                for (uint32_t k = s + lane; k < e; k += 32) y += prod[k];
-                y = warp_sum(y);
+                ColSum<TA> y;
+                for (uint32_t k = s + lane; k < e; k += 32) y.add(prod[k], E);
+                const TA yt = y.warp_total(E);
                 const TA invj = __shfl_sync(0xffffffffu, myinv, j);
-                if (lane == 0) epi(c0 + j, y, invj, acc);
+                if (lane == 0) epi(c0 + j, yt, invj, acc);
             }
             __syncwarp();
         }
