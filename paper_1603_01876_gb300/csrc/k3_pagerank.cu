@@ -29,7 +29,10 @@
 // shared-memory / L1 array is L1.
 // Items are dealt to warps round-robin.  Every column sum has a fixed order
 // and sum(r) is accumulated exactly in 128-bit fixed point, so results are
-// bitwise reproducible whichever warp takes which item.
+// bitwise reproducible whichever warp takes which item.  With binary64
+// ranks the column sums are exact fixed-point sums as well (integer
+// instructions, rounded once per column), which keeps the work off GB300's
+// narrow FP64 pipe.
 #include <cuda_bf16.h>
 
 #include <algorithm>
