@@ -178,12 +178,12 @@ __global__ void __launch_bounds__(256) normalize_kernel(const __grid_constant__ 
     const uint64_t r_end = std::min<uint64_t>(r_begin + NORM_ROWS, G.N);
     Fx128 acc{0, 0};
     if (lane < (int)d.nrhs) {
-        const double norm = w.norm[g * 32 + lane];
+        const double rnorm = 1.0 / w.norm[g * 32 + lane];  // a multiply per element, not a division
         for (uint64_t p = r_begin + warp; p < r_end; p += WARPS) {
             // storage position p holds vertex v; r0 and r_out are in vertex order
             const uint32_t v = __ldg(G.iperm + p);
             const uint64_t at = (G.row0 + v) * d.nrhs + lane;
-            const float r = (float)(r0[at] / norm);
+            const float r = (float)(r0[at] * rnorm);
             fx_add(acc, r, 1);
             const float iv = G.inv[v];
             if (lane == 0) w.invp[G.row0 + p] = iv;

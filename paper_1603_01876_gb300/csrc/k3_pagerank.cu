@@ -259,6 +259,9 @@ __global__ void __launch_bounds__(256) setup_kernel(Args a, const double *r0) {
 
 // r = r0 / norm(r0,1) rounded to the working precision; x = r / d_out; and
 // sum(r) of that vector.  With iters == 0 the normalised r is the result.
+// r0 is scaled by the binary64 reciprocal of the norm (within an ulp of the
+// quotient; a division per element would occupy GB300's narrow FP64 pipe),
+// and sum(r) is exact, so any grid gives the same bits.
 template <typename TS, typename TA, typename TO>
 __global__ void __launch_bounds__(256) normalize_kernel(Args a, const double *r0, const TA *inv, TA *invp, TS *x0,
                                                         TO *r_out, TA *rb0) {
@@ -270,20 +273,36 @@ __global__ void __launch_bounds__(256) normalize_kernel(Args a, const double *r0
         s_norm = n;
     }
     __syncthreads();
-    const double norm = s_norm;
+    const double rnorm = 1.0 / s_norm;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     Fx128 acc{0, 0}, dm{0, 0};
-    // in storage order: position p holds vertex iperm[p]; 1/d_out is copied into that order too
-    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.N; p += stride) {
-        const uint32_t v = a.iperm[p];
-        const TA r = (TA)(r0[v] / norm);
-        fx_add(acc, r, 1);
-        const TA iv = inv[v];
-        invp[p] = iv;
-        x0[p] = from_acc<TS>(r * iv);
-        if (a.iters == 0) r_out[v] = (TO)r;
-        if (rb0) rb0[p] = r;
-        if ((a.flags & PP_K3_DANGLING) && iv == TA(0)) fx_add(dm, r, 1);
+    // in storage order: position p holds vertex iperm[p]; 1/d_out is copied into that order too.
+    // Four positions per round, so that their reads (iperm, then r0 and 1/d_out) are in flight together.
+    constexpr int R = 4;
+    for (uint64_t p0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p0 < a.N; p0 += R * stride) {
+        uint32_t v[R];
+        double q[R];
+        TA iv[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) v[k] = p0 + k * stride < a.N ? a.iperm[p0 + k * stride] : 0u;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const bool in = p0 + k * stride < a.N;
+            q[k] = in ? r0[v[k]] : 0.0;
+            iv[k] = in ? inv[v[k]] : TA(0);
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const uint64_t p = p0 + k * stride;
+            if (p >= a.N) break;
+            const TA r = (TA)(q[k] * rnorm);
+            fx_add(acc, r, 1);
+            invp[p] = iv[k];
+            x0[p] = from_acc<TS>(r * iv[k]);
+            if (a.iters == 0) r_out[v[k]] = (TO)r;
+            if (rb0) rb0[p] = r;
+            if ((a.flags & PP_K3_DANGLING) && iv[k] == TA(0)) fx_add(dm, r, 1);
+        }
     }
     const Fx128 bt = fx_block_sum<256>(acc, s_fx);
     if (threadIdx.x == 0 && (bt.hi | bt.lo)) fx_atomic_add(a.acc, bt);
@@ -773,7 +792,9 @@ pp_status run_unroll(const pp_graph *g, const double *r0, uint32_t iters, double
     plan_kernel<<<(unsigned)ceil_div(N, PLAN_TILE), PLAN_THREADS, 0, s>>>(a);
     plan_items_kernel<<<(unsigned)std::min<uint64_t>(ceil_div(N, 256), 4096), 256, 0, s>>>(a);
     TA *invp = static_cast<TA *>(L.invp);  // 1/d_out in storage order
-    normalize_kernel<TS, TA, TO><<<SETUP_BLOCKS, 256, 0, s>>>(a, r0, inv, invp, x0, r_out, EXT ? rb0 : nullptr);
+    // one wave of blocks (each sums the norm's partials once)
+    const unsigned nblocks = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(ceil_div(N, 256), 8ull * sm_count()));
+    normalize_kernel<TS, TA, TO><<<nblocks, 256, 0, s>>>(a, r0, inv, invp, x0, r_out, EXT ? rb0 : nullptr);
     count_launch(4);
 
     auto *k_mid = iterate_kernel<TS, TA, TO, false, UNROLL, MINB, EXT>;
