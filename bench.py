@@ -155,8 +155,12 @@ def k3_bytes_per_iter(nnz, N, dtype):
 
 
 def k1_bytes(M, scale):
+    """Algorithmic bytes of Kernel 1: one read of (u, v) for the histograms, then
+    per pass a read and a write of every key (4-byte keys when 2*scale <= 32,
+    8-byte otherwise)."""
     P = -(-2 * scale // 8)
-    return M * (8 + 16 * P), P
+    kb = 4 if 2 * scale <= 32 else 8
+    return M * (8 + 2 * kb * P), P
 
 
 def k2_bytes(M, N, nnz0, nnz, scale):

@@ -149,7 +149,10 @@ pp_status pp_sort_edges(const uint32_t *u, const uint32_t *v, uint64_t M, uint32
  * PP_ERR_INVALID_ARG is returned and nothing is enqueued.  The call
  * allocates nothing (no cudaMalloc or cudaFree).  Its first call on a device
  * looks up the array's device address with that device current; make that
- * first call outside any stream capture.  Calls share the array, which keeps
+ * first call outside any stream capture.  A device reset (cudaDeviceReset, or
+ * anything else that replaces the device's context) invalidates that lookup:
+ * the next call in the new context looks the address up again, so make it
+ * outside stream capture too.  Calls share the array, which keeps
  * the last call's contents: each call clears what it needs zeroed, and calls
  * that overlap on the GPU (other streams, other host threads) race on it.
  * Results are identical to pp_sort_edges.

@@ -141,12 +141,18 @@ extern "C" pp_status pp_sort_edges(const uint32_t *u, const uint32_t *v, uint64_
 // cudaMalloc's implicit device synchronisation would stall their other
 // streams.  For them this entry point keeps its scratch space in a
 // fixed-size array in device memory, which every GPU that loads the library
-// holds until the process exits.  Its device address is looked up once per
-// device (cudaGetSymbolAddress) on the first call made with that device
-// current; do that first call outside any stream capture.  All calls share
+// holds until the process exits.  Its device address is looked up
+// (cudaGetSymbolAddress) on the first call made in each CUDA context, i.e.
+// once per device, and again after cudaDeviceReset or any other replacement
+// of the device's context (the module is then loaded anew and the array may
+// sit elsewhere); make those first calls outside any stream capture.  The
+// cache is keyed by the driver's context id, which is never reused within a
+// process.  All calls share
 // the array and it keeps the last call's contents: the sort clears its
 // counters and look-back words itself, and calls whose work overlaps on the
 // GPU (concurrent streams, several host threads) race on it.
+
+#include <cuda.h>
 
 #include <mutex>
 
@@ -157,8 +163,59 @@ constexpr uint64_t kStaticMaxEdges = PP_SORT_STATIC_MAX_EDGES;
 constexpr size_t kStaticBytes = (size_t)17 << 20;
 static __device__ __align__(256) unsigned char k1_static_scratch[kStaticBytes];
 
+// The driver's cuCtxGetCurrent and cuCtxGetId, fetched through the runtime
+// so that the library does not link libcuda itself.
+typedef CUresult (*ctx_current_fn)(CUcontext *);
+typedef CUresult (*ctx_id_fn)(CUcontext, unsigned long long *);
+
+struct StaticAddr {
+    unsigned long long ctx_id;  // context the address was looked up in (0 = none yet)
+    void *addr;
+};
+
 std::mutex g_static_mutex;
-void *g_static_addr[64] = {};
+StaticAddr g_static_addr[kMaxDevices] = {};
+ctx_current_fn g_ctx_current = nullptr;
+ctx_id_fn g_ctx_id = nullptr;
+
+// Id of the calling thread's current context, 0 if there is none.
+bool current_ctx_id(unsigned long long *id) {
+    *id = 0;
+    if (!g_ctx_current || !g_ctx_id) {
+        cudaDriverEntryPointQueryResult q1, q2;
+        void *f1 = nullptr, *f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return false;
+        g_ctx_current = reinterpret_cast<ctx_current_fn>(f1);
+        g_ctx_id = reinterpret_cast<ctx_id_fn>(f2);
+    }
+    CUcontext ctx = nullptr;
+    if (g_ctx_current(&ctx) != CUDA_SUCCESS) return false;
+    if (ctx && g_ctx_id(ctx, id) != CUDA_SUCCESS) return false;
+    return true;
+}
+
+// Device address of the scratch array in the current context.
+pp_status static_scratch(void **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PP_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    unsigned long long id = 0;
+    if (!current_ctx_id(&id)) return PP_ERR_CUDA;
+    StaticAddr &c = g_static_addr[dev];
+    if (id == 0 || c.ctx_id != id || !c.addr) {
+        void *p = nullptr;
+        // creates the device's primary context if the thread has none yet
+        if (cudaGetSymbolAddress(&p, k1_static_scratch) != cudaSuccess || !p) return PP_ERR_CUDA;
+        if (!current_ctx_id(&id)) return PP_ERR_CUDA;
+        c.ctx_id = id;  // an id of 0 is never reused: the next call looks the address up again
+        c.addr = p;
+    }
+    *out = c.addr;
+    return PP_OK;
+}
 }  // namespace
 
 extern "C" pp_status pp_sort_edges_static(const uint32_t *u, const uint32_t *v, uint64_t M, uint32_t scale,
@@ -168,18 +225,9 @@ extern "C" pp_status pp_sort_edges_static(const uint32_t *u, const uint32_t *v, 
     if (!u || !v || !u_out || !v_out) return PP_ERR_INVALID_ARG;
     const k1::Layout need = k1::layout(nullptr, M, scale);
     if (need.bytes > kStaticBytes) return PP_ERR_INVALID_ARG;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return PP_ERR_CUDA;
     void *base = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_static_mutex);
-        if (!g_static_addr[dev]) {
-            void *p = nullptr;
-            if (cudaGetSymbolAddress(&p, k1_static_scratch) != cudaSuccess || !p) return PP_ERR_CUDA;
-            g_static_addr[dev] = p;
-        }
-        base = g_static_addr[dev];
-    }
+    const pp_status sa = static_scratch(&base);
+    if (sa != PP_OK) return sa;
     const k1::Layout L = k1::layout(base, M, scale);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (2 * scale <= 32)

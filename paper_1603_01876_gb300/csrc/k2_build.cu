@@ -818,11 +818,12 @@ extern "C" pp_status pp_build_filter_normalize(const uint32_t *us, const uint32_
         k2::offsets_kernel<<<(unsigned)sc_tiles, k2::SC_THREADS, 0, s>>>(
             k2::OffArgs{L.row_nent, g->iperm, N, L.uoff, L.delta, L.off_status + sc_tiles, L.ctr + 3});
         count_launch(2);
-        static int uq_occ = 0;
-        if (!uq_occ) {
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&uq_occ, k2::unique_kernel, k2::UQ_THREADS, 0);
-            if (uq_occ < 1) uq_occ = 1;
-        }
+        static PerDevice uq_occ_dev;
+        const int uq_occ = (int)uq_occ_dev.get([] {
+            int o = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k2::unique_kernel, k2::UQ_THREADS, 0);
+            return (int64_t)(o < 1 ? 1 : o);
+        });
         const unsigned ugrid = (unsigned)std::min<uint64_t>(ceil_div(M, k2::UQ_TILE), (uint64_t)sms * uq_occ);
         const int vec = (((uintptr_t)us | (uintptr_t)vs) & 15u) == 0;
         k2::UniqueArgs ua{us,    vs,      M,       scale,       cmax, L.ent[0], g->ovf_key,  g->ovf_cnt,

@@ -754,18 +754,18 @@ extern "C" pp_status pp_pagerank_batched(const pp_graph *gs, uint32_t n_graphs, 
     k3b::plan_kernel<<<(unsigned)ceil_div(rows, k3b::PLAN_TILE), k3b::PLAN_THREADS, 0, s>>>(d, w);
     k3b::plan_items_kernel<<<(unsigned)std::min<uint64_t>(ceil_div(rows, 256), 4096), 256, 0, s>>>(d, w);
     count_launch(6);
-    static int o_mid = 0, o_last = 0, v_mid = 0, v_last = 0;
-    if (!o_mid) {
+    static PerDevice occ_dev;  // four 16-bit occupancies
+    const uint64_t occs = (uint64_t)occ_dev.get([] {
         auto occ = [](auto kernel) {
             int o = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kernel, k3b::THREADS, 0);
-            return o > 0 ? o : 1;
+            return (uint64_t)(o > 0 ? o : 1);
         };
-        o_mid = occ(k3b::iterate_kernel<false>);
-        o_last = occ(k3b::iterate_kernel<true>);
-        v_mid = occ(k3b::iterate_vec_kernel<false>);
-        v_last = occ(k3b::iterate_vec_kernel<true>);
-    }
+        return (int64_t)(occ(k3b::iterate_kernel<false>) | occ(k3b::iterate_kernel<true>) << 16 |
+                         occ(k3b::iterate_vec_kernel<false>) << 32 | occ(k3b::iterate_vec_kernel<true>) << 48);
+    });
+    const int o_mid = (int)(occs & 0xffff), o_last = (int)(occs >> 16 & 0xffff);
+    const int v_mid = (int)(occs >> 32 & 0xffff), v_last = (int)(occs >> 48 & 0xffff);
     const bool vec = nrhs == 32 && tuning("k3b_vec") != 0;
     const int sms = sm_count();
     for (uint32_t it = 0; it < iters; ++it) {

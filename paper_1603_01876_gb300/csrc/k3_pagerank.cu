@@ -801,15 +801,13 @@ pp_status run_unroll(const pp_graph *g, const double *r0, uint32_t iters, double
     auto *k_last = iterate_kernel<TS, TA, TO, !EXT, UNROLL, MINB, EXT>;
     constexpr int NT = THREADS;
     constexpr size_t smem = Smem<TA>::total(WARPS);
-    // the carveout attributes and the occupancy, once per instantiation
-    static std::atomic<uint32_t> cached{0};  // o_mid << 16 | o_last
-    uint32_t cv = cached.load();
-    if (cv == 0) {
+    // the carveout attributes and the occupancy, once per instantiation and device
+    static PerDevice cached;  // o_mid << 16 | o_last
+    const uint32_t cv = (uint32_t)cached.get([&] {
         set_smem(k_mid, MINB, smem);
         set_smem(k_last, MINB, smem);
-        cv = ((uint32_t)occupancy(k_mid, NT, smem) << 16) | (uint32_t)occupancy(k_last, NT, smem);
-        cached.store(cv);
-    }
+        return (int64_t)(((uint32_t)occupancy(k_mid, NT, smem) << 16) | (uint32_t)occupancy(k_last, NT, smem));
+    });
     const int o_mid = (int)(cv >> 16), o_last = (int)(cv & 0xffff);
     const int sms = sm_count();
     for (uint32_t it = 0; it < iters; ++it) {

@@ -279,12 +279,12 @@ inline void launch_pass(const SortWs &w, int p, int npasses, Src src, Dst dst, c
     ctl.spin_limit = spin_limit;
     const unsigned grid = (unsigned)ceil_div(n_max ? n_max : 1, TILE);
     if (w.wide) {
-        static const bool once = prefer_shared(pass_kernel<KeyT, uint64_t, Src, Dst>);
-        (void)once;
+        static PerDevice carveout;
+        carveout.get([] { return (int64_t)prefer_shared(pass_kernel<KeyT, uint64_t, Src, Dst>); });
         pass_kernel<KeyT, uint64_t, Src, Dst><<<grid, THREADS, 0, s>>>(src, dst, ctl);
     } else {
-        static const bool once = prefer_shared(pass_kernel<KeyT, uint32_t, Src, Dst>);
-        (void)once;
+        static PerDevice carveout;
+        carveout.get([] { return (int64_t)prefer_shared(pass_kernel<KeyT, uint32_t, Src, Dst>); });
         pass_kernel<KeyT, uint32_t, Src, Dst><<<grid, THREADS, 0, s>>>(src, dst, ctl);
     }
     count_launch();

@@ -25,6 +25,33 @@ inline void count_launch(uint64_t n = 1) { g_launches.fetch_add(n, std::memory_o
 // Current value of a tuning knob (pp_set_tuning); defaults live in pp_api.cu.
 int64_t tuning(const char *key);
 
+constexpr int kMaxDevices = 64;
+
+inline int current_device() {
+    int d = 0;
+    cudaGetDevice(&d);
+    return d;
+}
+
+// A launch setting computed once per device by f() (nonzero result): function
+// attributes such as the shared-memory carveout are set per device, and the
+// occupancy they give may differ between devices.  Threads that race compute
+// the same value.
+struct PerDevice {
+    std::atomic<int64_t> v[kMaxDevices];
+    template <typename F>
+    int64_t get(F f) {
+        const int d = current_device();
+        if (d < 0 || d >= kMaxDevices) return f();
+        int64_t x = v[d].load(std::memory_order_acquire);
+        if (!x) {
+            x = f();
+            v[d].store(x, std::memory_order_release);
+        }
+        return x;
+    }
+};
+
 inline int sm_count() {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
