@@ -332,16 +332,15 @@ uint64_t pp_launch_count(void);
  * change the order in which some column sums are added, so results move
  * within rounding (every setting meets the stated tolerances, and one
  * setting always gives the same bits):
- *   "k3_unroll_f32"  gathers each Kernel 3 thread issues before using any,
- *                    binary32 and bfloat16 ranks: 4 or 8 (default 8)
- *   "k3_unroll_f64"  the same for binary64 ranks: 4 or 8 (default 8)
+ *   "k3_unroll_f32"  entries each Kernel 3 lane loads and gathers before
+ *                    using any, binary32 and bfloat16 ranks: 4 or 8 (default 8)
+ *   "k3_unroll_f64"  the same for binary64 ranks: 4 or 8 (default 4)
  *   "k3_minblocks"   Kernel 3 blocks per SM the registers are budgeted for:
- *                    4, 5 or 6 (default 4)
- *   "k3_shortmax"    Kernel 3 columns longer than this are cut into chunks,
- *                    the others grouped in tiles: 64, 128 or 256 (default 256)
- *   "k3_chunk"       entries per chunk of a long column: 2048 or 4096 (default 2048)
- *   "k3_lane_short"  tile columns up to this long are summed by one lane,
- *                    longer ones by the whole warp: 8, 16 or 32 (default 16)
+ *                    4, 6 or 8 (default 4)
+ *   "k3_shortmax"    Kernel 3 columns longer than this are cut into chunks
+ *                    summed by whole warps, the others are summed one per
+ *                    lane in 32-column slices: 128, 256 or 512 (default 256)
+ *   "k3_chunk"       entries per chunk of a long column: 2048 or 4096 (default 4096)
  *   "k3b_shortmax"   the long-column threshold of the batched Kernel 3:
  *                    128 or 256 (default 256)
  *   "k3b_chunk"      its entries per chunk: 256, 512 or 1024 (default 512)

@@ -18,19 +18,25 @@
 //     entries; a warp sums a chunk with coalesced index loads and a group of
 //     gathers in flight per lane, reduces it in a fixed shuffle tree, and the
 //     warp that finishes a column's last chunk adds the chunk sums in order;
-//   - the other columns form tiles of at most 32 consecutive columns and
-//     2*shortmax entries; a warp gathers count * x(u) for the tile's entries
-//     into its shared-memory slab, then each lane sums one short column (at
-//     most `lane_short` entries) in order, and the whole warp takes each
-//     medium column (lanes stride, fixed shuffle tree).
-// shortmax, chunk and lane_short are tuning knobs (k3_shortmax, k3_chunk,
-// k3_lane_short); for one setting every run gives the same bits.
-// Blocks reserve no more shared memory than they use; the rest of the SM's
-// shared-memory / L1 array is L1.
+//   - the other columns are summed one per lane, in slices of 32 columns
+//     stored as a sliced ELLPACK copy of their entries (entry k of the
+//     slice's lane j at word 32 * (slice base + k) + j): at each step the
+//     warp reads 32 consecutive words, gathers 32 values of x and each lane
+//     adds its own, so no shared memory and no reduction is needed.  Each
+//     call builds the copy from the compressed columns: the positions are cut
+//     into windows of 2^wbits consecutive columns, the short columns of a
+//     window are sorted by decreasing length (counting sort) and dealt to
+//     slices of 32, so a slice's lanes have nearly equal lengths and the
+//     padding of a window is below 32 * shortmax words.
+// shortmax and chunk are tuning knobs (k3_shortmax, k3_chunk).  The blocks
+// keep almost no shared memory, so the SM's shared-memory / L1 array is
+// nearly all L1, which the gathers of x need (the rows gathered most often
+// are cached there).
 // Items are dealt to warps round-robin.  Every column sum has a fixed order
-// and sum(r) is accumulated exactly in 128-bit fixed point, so results are
-// bitwise reproducible whichever warp takes which item.  With binary64
-// ranks the column sums are exact fixed-point sums as well (integer
+// (a lane adds its column's entries in order; chunk sums in chunk order) and
+// sum(r) is accumulated exactly in 128-bit fixed point, so results are
+// bitwise reproducible whichever warp takes which item or lane.  With
+// binary64 ranks the column sums are exact fixed-point sums as well (integer
 // instructions, rounded once per column), which keeps the work off GB300's
 // narrow FP64 pipe.
 #include <cuda_bf16.h>
@@ -48,16 +54,28 @@ namespace k3 {
 
 constexpr int THREADS = 256;
 constexpr int WARPS = THREADS / 32;
-constexpr int TILE_COLS = 32;      // one lane per column in a tile
-constexpr int SHORTMAX_MAX = 256;  // largest long-column threshold (k3_shortmax)
-constexpr int TILE_ENTRIES = 2 * SHORTMAX_MAX;
+constexpr int SHORTMAX_MAX = 512;  // largest long-column threshold (k3_shortmax)
 constexpr int CHUNK_MIN = 2048;    // smallest long-column chunk (k3_chunk)
 constexpr uint32_t NENT_BITS = 13; // a long chunk's item: entries | chunks of the column << NENT_BITS
 constexpr uint32_t LONG_FLAG = 0x80000000u;
 constexpr int SETUP_BLOCKS = 512;  // fixed, so the start-vector reduction is reproducible
-constexpr int PLAN_THREADS = 256;
-constexpr int PLAN_ITEMS = 16;
-constexpr int PLAN_TILE = PLAN_THREADS * PLAN_ITEMS;
+constexpr int WIN_THREADS = 512;   // the window (slice planning) kernels
+constexpr int SCAN_THREADS = 1024; // the one-block scan over windows
+// A slice lane's slot word: length << SLOT_LEN_SHIFT | position within the
+// window (at most 16 bits), or SLOT_NONE for a lane without a column.
+constexpr uint32_t SLOT_LEN_SHIFT = 16;
+constexpr uint32_t SLOT_NONE = 0xffffffffu;
+// A slice's metadata: (base, window << META_LEN_BITS | length), where the
+// slice's entry k of lane j is word 32 * (base + k) + j of the copy.
+constexpr uint32_t META_LEN_BITS = 11;
+constexpr uint32_t MAX_WIN_BITS = 16;
+constexpr uint32_t EMPTY_PER_ITEM = 1024;  // empty columns per work item
+
+// log2 of the window width: about 1024 windows, each of 32 .. 65536 columns.
+inline uint32_t win_bits(uint32_t scale) {
+    const int b = std::min<int>(std::max<int>((int)scale - 10, 5), (int)MAX_WIN_BITS);
+    return (uint32_t)std::min<int>(b, (int)scale);
+}
 
 __device__ __forceinline__ float to_acc(float x) { return x; }
 __device__ __forceinline__ float to_acc(__nv_bfloat16 x) { return __bfloat162float(x); }
@@ -73,9 +91,10 @@ __device__ __forceinline__ TS from_acc(double x) { return x; }
 
 // Control words in the workspace.
 struct Ctl {
-    uint32_t n_items;  // work items (tiles and long-column chunks)
-    uint32_t n_bound;  // columns that start a tile or a long column
-    uint32_t pad[2];
+    uint32_t n_chunks;  // work items of the long columns (they come first)
+    uint32_t n_slices;  // slices of 32 short columns (the next items)
+    uint32_t sell_words32;  // words of the sliced copy / 32
+    uint32_t n_empty;   // columns without entries (the last items, EMPTY_PER_ITEM each)
 };
 
 struct Args {
@@ -85,21 +104,25 @@ struct Args {
     const uint64_t *ovf_key;
     const uint32_t *ovf_cnt;
     const uint64_t *info;
-    uint32_t *bound;          // [N] boundary columns, ascending (plan)
-    uint32_t *bound_item;     // [N] index of each boundary's first work item
-    uint4 *item;              // [N + M/CHUNK_MIN + 1] work items, see plan_items_kernel
+    uint32_t wbits, nwin;     // windows of 2^wbits column positions, nwin of them
+    uint4 *wcnt;              // [nwin] slices, sum of slice lengths, chunk items, empty columns of each window
+    uint4 *woff;              // [nwin] exclusive prefix sums of the same
+    uint32_t *slot;           // [32 * max slices] slot words (see SLOT_LEN_SHIFT)
+    uint2 *meta;              // [max slices] slice metadata (see META_LEN_BITS)
+    void *invs;               // [32 * max slices] 1/d_out of each slot's column (TA), 0 for empty slots
+    uint32_t *elist;          // [N] positions of the columns without entries
+    void *einv;               // [N] their 1/d_out (TA), in list order
+    uint32_t *sell;           // the short columns' entries, sliced ELLPACK
+    uint4 *item;              // [N + M/CHUNK_MIN + 1] long-column chunks
     double *chunk_sum;        // [same] partial sums of long-column chunks
     uint32_t *ticket;         // [same] finished-chunk counters, at a column's first item
-    uint64_t *plan_status;    // [N / PLAN_TILE + 1] look-back words of the plan scan
     unsigned long long *acc;  // [2 * (iters + 1)] sum(r) per iterate, 128-bit fixed point
     int *fx_exp;              // [iters + 1] scale exponent of each accumulator
     double *ipart;            // [SETUP_BLOCKS]
     Ctl *ctl;
-    uint32_t *ctr;            // [1] plan tile counter
     double c;
-    uint32_t shortmax;    // columns longer than this are cut into chunks (power of two)
+    uint32_t shortmax;    // columns longer than this are cut into chunks
     uint32_t chunk;       // entries of a long column per work item
-    uint32_t lane_short;  // tile columns up to this long are summed by one lane
     // variants (pp_pagerank_ex); zero / null for the plain iteration
     uint32_t flags;                  // PP_K3_DANGLING | PP_K3_CONVERGE
     double tol;                      // convergence threshold on norm(r_k - r_(k-1), 1)
@@ -122,119 +145,206 @@ __device__ __forceinline__ uint32_t ovf_lookup(const uint64_t *keys, const uint3
 }
 
 // ------------------------------------------------------------------- planning
+//
+// Per window of 2^wbits column positions: the columns longer than shortmax
+// become chunk items, the other non-empty ones are sorted by decreasing
+// length and dealt to slices of 32 lanes, and the columns without entries
+// (r = teleport only) go to a list processed EMPTY_PER_ITEM at a time.  Three launches: count (per window), scan (one
+// block over the windows), fill (per window).  The placement of equal-length
+// columns among lanes comes from shared-memory atomics and may differ from
+// call to call; no result depends on it (each column is summed by one lane in
+// entry order, and sum(r) is exact).
 
-constexpr uint64_t F_AGG = 1ull << 62, F_INC = 2ull << 62;
-
-// Column v starts a work item if it is long, follows a long column, starts in
-// a new shortmax-entry span of the entry array, or is a multiple of
-// TILE_COLS.  So a tile holds at most TILE_COLS columns, all starting in one
-// span, and its last column ends at most shortmax entries past that span:
-// at most 2*shortmax entries.
-__device__ __forceinline__ uint32_t item_count(const Args &a, uint32_t len) {
-    return len > a.shortmax ? (len + a.chunk - 1) / a.chunk : 1u;
+// Slices of a window whose non-empty short columns, by decreasing length,
+// have the class counts hist[1..shortmax] (hist[L] columns of length L): the number
+// of slices and the sum of their lengths (a slice is as long as its first,
+// longest column).
+__device__ __forceinline__ uint2 slice_totals(const uint32_t *hist, uint32_t shortmax) {
+    uint32_t rank = 0, sum = 0;
+    for (int L = (int)shortmax; L >= 1; --L) {
+        const uint32_t n = hist[L];
+        if (n) {
+            sum += ((rank + n + 31) / 32 - (rank + 31) / 32) * (uint32_t)L;
+            rank += n;
+        }
+    }
+    return make_uint2((rank + 31) / 32, sum);
 }
 
-__device__ __forceinline__ void classify(const Args &a, uint32_t v, bool &bound, uint32_t &nitems) {
-    const uint32_t s = __ldg(a.colptr + v), e = __ldg(a.colptr + v + 1);
-    const bool is_long = e - s > a.shortmax;
-    nitems = item_count(a, e - s);
-    bound = true;
-    if (v == 0 || is_long || v % TILE_COLS == 0) return;
-    const uint32_t ps = __ldg(a.colptr + v - 1);
-    if (s - ps > a.shortmax) return;  // the previous column is long
-    bound = (s / a.shortmax) != (ps / a.shortmax);
-}
-
-// Compacts the boundary columns in order and numbers their work items (one
-// look-back scan of two packed counters: boundaries, items).
-__global__ void __launch_bounds__(PLAN_THREADS) plan_kernel(Args a) {
-    __shared__ uint32_t s_tile;
-    __shared__ uint64_t s_scan[40];
-    __shared__ uint64_t s_excl;
-    const int tid = threadIdx.x;
-    if (tid == 0) s_tile = atomicAdd(a.ctr, 1u);
+__global__ void __launch_bounds__(WIN_THREADS) window_count_kernel(Args a) {
+    __shared__ uint32_t hist[SHORTMAX_MAX + 1];
+    __shared__ uint32_t s_items;
+    const uint32_t W = 1u << a.wbits, p0 = blockIdx.x << a.wbits;
+    for (uint32_t i = threadIdx.x; i <= a.shortmax; i += blockDim.x) hist[i] = 0;
+    if (threadIdx.x == 0) s_items = 0;
     __syncthreads();
-    const uint64_t tile = s_tile;
-    const uint64_t ntiles = (a.N + PLAN_TILE - 1) / PLAN_TILE;
-    if (tile >= ntiles) return;
-    const uint64_t v0 = tile * PLAN_TILE + (uint64_t)tid * PLAN_ITEMS;
-    uint32_t bmask = 0, nitems = 0;
+    uint32_t items = 0;
+    for (uint32_t i = threadIdx.x; i < W; i += blockDim.x) {
+        const uint32_t p = p0 + i;
+        const uint32_t len = __ldg(a.colptr + p + 1) - __ldg(a.colptr + p);
+        if (len > a.shortmax)
+            items += (len + a.chunk - 1) / a.chunk;
+        else
+            atomicAdd(&hist[len], 1u);
+    }
 #pragma unroll
-    for (int j = 0; j < PLAN_ITEMS; ++j) {
-        const uint64_t v = v0 + j;
-        if (v < a.N) {
-            bool b;
-            uint32_t ni;
-            classify(a, (uint32_t)v, b, ni);
-            if (b) {
-                bmask |= 1u << j;
-                nitems += ni;
-            }
-        }
-    }
-    // bits 30:0 count boundaries, bits 61:31 work items
-    const uint64_t mine = (uint64_t)__popc(bmask) | ((uint64_t)nitems << 31);
-    uint64_t total;
-    const uint64_t texcl = block_exclusive_sum<uint64_t, PLAN_THREADS>(mine, s_scan, &total);
-    if (tid < 32) {
-        // warp 0: publish this tile's counts and look back over earlier tiles
-        uint64_t *st = a.plan_status + tile;
-        uint64_t ex = 0;
-        if (tile == 0) {
-            if (tid == 0) st_relaxed_u64(st, F_INC | total);
-        } else {
-            if (tid == 0) st_relaxed_u64(st, F_AGG | total);
-            ex = warp_lookback(a.plan_status, tile);
-            if (tid == 0) st_relaxed_u64(st, F_INC | (ex + total));
-        }
-        if (tid == 0) {
-            s_excl = ex;
-            if (tile == ntiles - 1) {
-                const uint64_t inc = ex + total;
-                a.ctl->n_bound = (uint32_t)(inc & 0x7fffffffull);
-                a.ctl->n_items = (uint32_t)(inc >> 31);
-            }
-        }
-    }
+    for (int o = 16; o > 0; o >>= 1) items += __shfl_xor_sync(0xffffffffu, items, o);
+    if ((threadIdx.x & 31) == 0 && items) atomicAdd(&s_items, items);
     __syncthreads();
-    const uint64_t g = s_excl + texcl;
-    uint32_t bi = (uint32_t)(g & 0x7fffffffull), ii = (uint32_t)(g >> 31);
-#pragma unroll
-    for (int j = 0; j < PLAN_ITEMS; ++j) {
-        if (!(bmask >> j & 1u)) continue;
-        const uint32_t v = (uint32_t)(v0 + j);
-        a.bound[bi] = v;
-        a.bound_item[bi] = ii;
-        const uint32_t s = __ldg(a.colptr + v), e = __ldg(a.colptr + v + 1);
-        ii += item_count(a, e - s);
-        ++bi;
+    if (threadIdx.x == 0) {
+        const uint2 t = slice_totals(hist, a.shortmax);
+        a.wcnt[blockIdx.x] = make_uint4(t.x, t.y, s_items, hist[0]);
     }
 }
 
-// Writes the work items of each boundary, so that a warp can start loading
-// entries without reading the column pointers first:
-//   tile:        (first column, number of columns, first entry, entries)
-//   long chunk:  (column | LONG_FLAG, first item of the column, first entry,
-//                 entries | chunks of the column << NENT_BITS)
-// A tile runs to the next boundary; a long column gets one item per chunk.
-__global__ void __launch_bounds__(256) plan_items_kernel(Args a) {
-    const uint32_t nb = a.ctl->n_bound;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x) {
-        const uint32_t v = a.bound[i], o = a.bound_item[i];
-        const uint32_t s = __ldg(a.colptr + v), e = __ldg(a.colptr + v + 1);
-        if (e - s > a.shortmax) {
+// Exclusive prefix sums of the windows' counts (one block); the totals go to ctl.
+__global__ void __launch_bounds__(SCAN_THREADS) window_scan_kernel(Args a) {
+    __shared__ uint32_t sc[40];
+    uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+    for (uint32_t base = 0; base < a.nwin; base += SCAN_THREADS) {
+        const uint32_t w = base + threadIdx.x;
+        const uint4 c = w < a.nwin ? a.wcnt[w] : make_uint4(0u, 0u, 0u, 0u);
+        uint32_t t0, t1, t2, t3;
+        const uint32_t e0 = block_exclusive_sum<uint32_t, SCAN_THREADS>(c.x, sc, &t0);
+        const uint32_t e1 = block_exclusive_sum<uint32_t, SCAN_THREADS>(c.y, sc, &t1);
+        const uint32_t e2 = block_exclusive_sum<uint32_t, SCAN_THREADS>(c.z, sc, &t2);
+        const uint32_t e3 = block_exclusive_sum<uint32_t, SCAN_THREADS>(c.w, sc, &t3);
+        if (w < a.nwin) a.woff[w] = make_uint4(c0 + e0, c1 + e1, c2 + e2, c3 + e3);
+        c0 += t0;
+        c1 += t1;
+        c2 += t2;
+        c3 += t3;
+    }
+    if (threadIdx.x == 0) {
+        a.ctl->n_slices = c0;
+        a.ctl->sell_words32 = c1;
+        a.ctl->n_chunks = c2;
+        a.ctl->n_empty = c3;
+    }
+}
+
+// Places a window's columns: chunk items for the long ones, slot words and
+// slice metadata for the others, then copies the short columns' entries
+// into their slices (one warp per slice; lane j copies its column's entries
+// to words 32 * (base + k) + j, so the iteration reads them coalesced).
+__global__ void __launch_bounds__(WIN_THREADS) window_fill_kernel(Args a) {
+    __shared__ uint32_t next[SHORTMAX_MAX + 1];  // class counts, then the next free rank of each class
+    __shared__ uint32_t first[SHORTMAX_MAX + 1]; // first rank of each class (classes by decreasing length)
+    __shared__ uint32_t s_item, s_empty;
+    __shared__ uint32_t sc[40];
+    const uint32_t W = 1u << a.wbits, p0 = blockIdx.x << a.wbits;
+    const uint4 off = a.woff[blockIdx.x];
+    const uint32_t ns = a.wcnt[blockIdx.x].x;
+    const uint32_t L = a.shortmax;
+    for (uint32_t i = threadIdx.x; i <= L; i += blockDim.x) next[i] = 0;
+    if (threadIdx.x == 0) {
+        s_item = off.z;
+        s_empty = off.w;
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < W; i += blockDim.x) {
+        const uint32_t p = p0 + i;
+        const uint32_t len = __ldg(a.colptr + p + 1) - __ldg(a.colptr + p);
+        if (len <= L) atomicAdd(&next[len], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t r = 0;
+        for (int c = (int)L; c >= 1; --c) {
+            first[c] = r;
+            r += next[c];
+            next[c] = first[c];
+        }
+    }
+    __syncthreads();
+    uint32_t *slot = a.slot + 32ull * off.x;
+    for (uint32_t i = threadIdx.x; i < W; i += blockDim.x) {
+        const uint32_t p = p0 + i;
+        const uint32_t s = __ldg(a.colptr + p), len = __ldg(a.colptr + p + 1) - s;
+        if (len > L) {
             // a kept column has at most M/2 <= 2^30 entries (the largest one is removed), so nc < 2^19
-            const uint32_t nc = (e - s + a.chunk - 1) / a.chunk;
+            const uint32_t nc = (len + a.chunk - 1) / a.chunk;
+            const uint32_t o = atomicAdd(&s_item, nc);
             for (uint32_t k = 0; k < nc; ++k) {
                 const uint32_t cs = s + k * a.chunk;
-                a.item[o + k] = make_uint4(v | LONG_FLAG, o, cs, min(a.chunk, e - cs) | (nc << NENT_BITS));
+                a.item[o + k] = make_uint4(p | LONG_FLAG, o, cs, min(a.chunk, s + len - cs) | (nc << NENT_BITS));
                 a.ticket[o + k] = 0;
             }
+        } else if (len == 0) {
+            a.elist[atomicAdd(&s_empty, 1u)] = p;
         } else {
-            const uint32_t c1 = i + 1 < nb ? a.bound[i + 1] : a.N;
-            a.item[o] = make_uint4(v, c1 - v, s, __ldg(a.colptr + c1) - s);
+            const uint32_t rank = atomicAdd(&next[len], 1u);
+            slot[rank] = (len << SLOT_LEN_SHIFT) | i;
         }
     }
+    __syncthreads();
+    // every class is placed, so the shortest one (length 1, the last) ends at the number of
+    // non-empty short columns
+    const uint32_t n_short = L >= 1 ? next[1] : 0u;
+    for (uint32_t r = n_short + threadIdx.x; r < 32 * ns; r += blockDim.x) slot[r] = SLOT_NONE;
+    // slice t starts at rank 32t and is as long as the class holding that rank: the first class
+    // (from the longest) whose end rank next[c] exceeds 32t
+    const uint32_t per = (ns + blockDim.x - 1) / blockDim.x;
+    const uint32_t t0 = min(ns, threadIdx.x * per), t1 = min(ns, t0 + per);
+    uint32_t mine = 0;
+    for (uint32_t t = t0; t < t1; ++t) {
+        uint32_t lo = 0, hi = L - 1;  // over j = L - c (c = L .. 1), where next[L - j] is nondecreasing in j
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (next[L - mid] > 32 * t)
+                hi = mid;
+            else
+                lo = mid + 1;
+        }
+        mine += L - lo;
+    }
+    uint32_t tot;
+    uint32_t base = off.y + block_exclusive_sum<uint32_t, WIN_THREADS>(mine, sc, &tot);
+    for (uint32_t t = t0; t < t1; ++t) {
+        uint32_t lo = 0, hi = L - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (next[L - mid] > 32 * t)
+                hi = mid;
+            else
+                lo = mid + 1;
+        }
+        const uint32_t slen = L - lo;
+        a.meta[off.x + t] = make_uint2(base, (blockIdx.x << META_LEN_BITS) | slen);
+        base += slen;
+    }
+    __syncthreads();  // the slot words and metadata of this window are visible to the block
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t t = warp; t < ns; t += WIN_THREADS / 32) {
+        const uint32_t o = slot[32 * t + lane];
+        if (o == SLOT_NONE) continue;
+        const uint32_t len = o >> SLOT_LEN_SHIFT, p = p0 + (o & ((1u << SLOT_LEN_SHIFT) - 1));
+        const uint32_t *src = a.rowc + __ldg(a.colptr + p);
+        uint32_t *dst = a.sell + 32ull * a.meta[off.x + t].x + lane;
+        for (uint32_t k = 0; k < len; ++k) dst[32ull * k] = __ldg(src + k);
+    }
+}
+
+// 1/d_out of each slot's column in slot order, and of each column without
+// entries in list order (vertex-order input), so that the iteration reads
+// them with the slot words instead of after them.
+template <typename TA>
+__global__ void __launch_bounds__(256) order_inv_kernel(Args a, const TA *inv) {
+    const uint64_t nslots = 32ull * a.ctl->n_slices, nempty = a.ctl->n_empty;
+    TA *invs = static_cast<TA *>(a.invs);
+    TA *einv = static_cast<TA *>(a.einv);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nslots; q += stride) {
+        const uint32_t o = a.slot[q];
+        TA v = TA(0);
+        if (o != SLOT_NONE) {
+            const uint32_t win = a.meta[q / 32].y >> META_LEN_BITS;
+            v = inv[a.iperm[(win << a.wbits) + (o & ((1u << SLOT_LEN_SHIFT) - 1))]];
+        }
+        invs[q] = v;
+    }
+    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nempty; q += stride)
+        einv[q] = inv[a.iperm[a.elist[q]]];
 }
 
 // Reset the per-call counters and sum |r0|.
@@ -242,14 +352,12 @@ __global__ void __launch_bounds__(256) setup_kernel(Args a, const double *r0) {
     __shared__ double s_red[32];
     const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    if (gtid == 0) a.ctr[0] = 0;
     for (uint64_t i = gtid; i < 2ull * (a.iters + 1); i += stride) {
         a.acc[i] = 0;
         if (a.dmass) a.dmass[i] = 0;
         if (a.delta) a.delta[i] = 0;
     }
     if (gtid < 2 && a.state) a.state[gtid] = 0;
-    for (uint64_t i = gtid; i < (a.N + PLAN_TILE - 1) / PLAN_TILE; i += stride) a.plan_status[i] = 0;
     if (gtid == 0) a.fx_exp[0] = 1;  // the normalised start vector has every entry <= 1 < 2^1
     double acc = 0.0;
     for (uint64_t i = gtid; i < a.N; i += stride) acc += fabs(r0[i]);
@@ -315,19 +423,29 @@ __global__ void __launch_bounds__(256) normalize_kernel(Args a, const double *r0
 
 // ------------------------------------------------------------- the iteration
 
-// Gathered-vector loads and stores, kept in L2 (evict-last).
-__device__ __forceinline__ float ld_x(const float *p, uint64_t pol) { return ld_hint(p, pol); }
-__device__ __forceinline__ double ld_x(const double *p, uint64_t pol) { return ld_hint(p, pol); }
-__device__ __forceinline__ __nv_bfloat16 ld_x(const __nv_bfloat16 *p, uint64_t pol) {
-    return __ushort_as_bfloat16(ld_hint_b16(p, pol));
+// Loads and stores of the iteration.  The gathered vector goes through L1
+// (the rows gathered most often are cached there); the entries and the
+// per-slice words are read once per iteration and bypass L1.  No L2
+// eviction-policy operands: they would hold registers the gathers need.
+__device__ __forceinline__ float ld_x(const float *p) { return __ldg(p); }
+__device__ __forceinline__ double ld_x(const double *p) { return __ldg(p); }
+__device__ __forceinline__ __nv_bfloat16 ld_x(const __nv_bfloat16 *p) {
+    return __ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short *>(p)));
 }
-__device__ __forceinline__ void st_x(float *p, float v, uint64_t pol) { st_hint(p, v, pol); }
-__device__ __forceinline__ void st_x(double *p, double v, uint64_t pol) { st_hint(p, v, pol); }
-__device__ __forceinline__ void st_x(__nv_bfloat16 *p, __nv_bfloat16 v, uint64_t pol) {
-    st_hint_b16(p, __bfloat16_as_ushort(v), pol);
+__device__ __forceinline__ void st_x(float *p, float v) { *p = v; }
+__device__ __forceinline__ void st_x(double *p, double v) { *p = v; }
+__device__ __forceinline__ void st_x(__nv_bfloat16 *p, __nv_bfloat16 v) { *p = v; }
+__device__ __forceinline__ uint32_t ld_once(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
 }
-__device__ __forceinline__ float ld_inv(const float *p, uint64_t pol) { return ld_hint(p, pol); }
-__device__ __forceinline__ double ld_inv(const double *p, uint64_t pol) { return ld_hint(p, pol); }
+__device__ __forceinline__ float ld_once(const float *p) { return __uint_as_float(ld_once(reinterpret_cast<const uint32_t *>(p))); }
+__device__ __forceinline__ double ld_once(const double *p) {
+    double v;
+    asm volatile("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
 
 // Per-thread exact accumulators: sum(r'), and for the variants the mass of
 // the dangling rows and norm(r' - r, 1).
@@ -344,7 +462,6 @@ struct Epilogue {
     TS *x_out;
     TO *r_out;
     TA cc, tele;
-    uint64_t keep, stream;
     int E;
     const uint32_t *iperm;
     const TA *rb_in;
@@ -354,7 +471,7 @@ struct Epilogue {
     __device__ __forceinline__ void operator()(uint32_t col, TA y, TA inv_col, Sums &acc) const {
         const TA r = cc * y + tele;
         if (LAST && !EXT) r_out[__ldg(iperm + col)] = (TO)r;
-        st_x(x_out + col, from_acc<TS>(r * inv_col), keep);
+        st_x(x_out + col, from_acc<TS>(r * inv_col));
         fx_add(acc.s, r, E);
         if (EXT) {
             if (flags & PP_K3_CONVERGE) {
@@ -412,23 +529,11 @@ struct ColSum<double> {
     __device__ __forceinline__ double warp_total(int E) const { return fx_to_double(fx_warp_sum(v), E); }
 };
 
-// Dynamic shared memory of iterate_kernel: the per-warp product slabs and
-// column starts, then the block-sum scratch.
-template <typename TA>
-struct Smem {
-    static constexpr size_t cp(int nw) { return (size_t)nw * TILE_ENTRIES * sizeof(TA); }
-    static constexpr size_t fx(int nw) { return (cp(nw) + (size_t)nw * (TILE_COLS + 1) * 4 + 15) & ~(size_t)15; }
-    static constexpr size_t total(int nw) { return fx(nw) + (size_t)nw * 2 * 8; }
-};
-
 template <typename TS, typename TA, typename TO, bool LAST, int UNROLL, int MINB, bool EXT>
 __global__ void __launch_bounds__(THREADS, MINB)
     iterate_kernel(Args a, const TA *inv, const TS *__restrict__ x_in, TS *__restrict__ x_out, TO *r_out,
                    uint32_t iter, const TA *rb_in, TA *rb_out) {
-    static_assert(TILE_ENTRIES % (32 * UNROLL) == 0, "unroll must divide the work");
-    constexpr int NT = THREADS, NW = WARPS;
-    extern __shared__ __align__(16) unsigned char k3_smem[];
-    uint64_t *s_fx = reinterpret_cast<uint64_t *>(k3_smem + Smem<TA>::fx(NW));
+    constexpr int NW = WARPS;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double tele_extra = 0.0;
@@ -446,64 +551,85 @@ __global__ void __launch_bounds__(THREADS, MINB)
         if (a.flags & PP_K3_DANGLING)
             tele_extra = a.c / (double)a.N * fx_value(a.dmass[2 * iter], a.dmass[2 * iter + 1], a.fx_exp[iter]);
     }
-    const uint32_t n_items = a.ctl->n_items;
+    const uint32_t n_chunks = a.ctl->n_chunks;
+    const uint32_t n_cs = n_chunks + a.ctl->n_slices;  // chunks and slices; then the empty columns
+    const uint32_t n_empty = a.ctl->n_empty;
+    const uint32_t n_items = n_cs + (n_empty + EMPTY_PER_ITEM - 1) / EMPTY_PER_ITEM;
     const double S = fx_value(a.acc[2 * iter], a.acc[2 * iter + 1], a.fx_exp[iter]);
     const int E = fx_exponent(S);
     if (blockIdx.x == 0 && threadIdx.x == 0) a.fx_exp[iter + 1] = E;
     const uint32_t umask = (1u << a.scale) - 1u;
-    const uint64_t keep = policy_evict_last(), stream = policy_evict_first();
     const Epilogue<TS, TA, TO, LAST, EXT> epi{inv,
                                               x_out,
                                               r_out,
                                               (TA)a.c,
                                               (TA)(((1.0 - a.c) / (double)a.N) * S + tele_extra),
-                                              keep,
-                                              stream,
                                               E,
                                               a.iperm,
                                               rb_in,
                                               rb_out,
                                               a.flags};
-    TA *prod = reinterpret_cast<TA *>(k3_smem) + warp * TILE_ENTRIES;
-    uint32_t *cp = reinterpret_cast<uint32_t *>(k3_smem + Smem<TA>::cp(NW)) + warp * (TILE_COLS + 1);
     Sums acc{{0, 0}, {0, 0}, {0, 0}};
     const uint32_t nwarps = gridDim.x * NW;
 
+    // An item's descriptor: a chunk's (column | LONG_FLAG, first item, first
+    // entry, entries | chunks << NENT_BITS), or a slice's (base, window <<
+    // META_LEN_BITS | length, this lane's slot word, -) with this lane's
+    // 1/d_out (stored in slot order, so it does not wait for the slot word).
+    // The next one is fetched while this one is processed.
+    struct Desc {
+        uint4 d;
+        TA iv;
+    };
+    auto descriptor = [&](uint32_t i) -> Desc {
+        if (i >= n_cs) return Desc{make_uint4(0u, 0u, 0u, 0u), TA(0)};
+        if (i < n_chunks) return Desc{__ldg(a.item + i), TA(0)};
+        const uint32_t sl = i - n_chunks;
+        const uint2 m = __ldg(a.meta + sl);
+        return Desc{make_uint4(m.x, m.y, ld_once(a.slot + 32ull * sl + lane), 0u),
+                    ld_once(static_cast<const TA *>(a.invs) + 32ull * sl + lane)};
+    };
     uint32_t item = blockIdx.x * NW + warp;
-    uint4 it = item < n_items ? __ldg(a.item + item) : make_uint4(0, 0, 0, 0);
+    Desc cur = descriptor(item);
     while (item < n_items) {
-        // the next item's descriptor is fetched while this one is processed
         const uint32_t next = item + nwarps;
-        const uint4 nit = next < n_items ? __ldg(a.item + next) : make_uint4(0, 0, 0, 0);
-        const uint32_t e0 = it.z;
-        if (it.x & LONG_FLAG) {
-            // ---- one chunk of a long column
-            const uint32_t col = it.x & ~LONG_FLAG, first = it.y;
+        const Desc nxt = descriptor(next);
+        const uint4 it = cur.d;
+        if (item < n_chunks) {
+            // ---- one chunk of a long column: coalesced entries, a group of gathers in flight per lane
+            const uint32_t col = it.x & ~LONG_FLAG, first = it.y, e0 = it.z;
             const uint32_t nent = it.w & ((1u << NENT_BITS) - 1), nchunks = it.w >> NENT_BITS;
             ColSum<TA> part;
+            // the entries of step s + 1 are loaded while the gathers of step s are in flight
+            const uint32_t *rw = a.rowc + e0 + lane;
+            uint32_t w[UNROLL];
+#pragma unroll
+            for (int m = 0; m < UNROLL; ++m) w[m] = (uint32_t)(m * 32 + lane) < nent ? ld_once(rw + m * 32) : 0u;
             for (uint32_t base = 0; base < nent; base += 32 * UNROLL) {
-                uint32_t w[UNROLL];
                 TA xv[UNROLL];
 #pragma unroll
                 for (int m = 0; m < UNROLL; ++m) {
                     const uint32_t k = base + (uint32_t)(m * 32 + lane);
-                    w[m] = k < nent ? ld_stream_u32(a.rowc + e0 + k, stream) : 0u;
+                    xv[m] = k < nent ? to_acc(ld_x(x_in + (w[m] & umask))) : TA(0);
                 }
+                uint32_t wn[UNROLL];
+                const uint32_t nb = base + 32 * UNROLL;
 #pragma unroll
                 for (int m = 0; m < UNROLL; ++m) {
-                    const uint32_t k = base + (uint32_t)(m * 32 + lane);
-                    xv[m] = k < nent ? to_acc(ld_x(x_in + (w[m] & umask), keep)) : TA(0);
+                    const uint32_t k = nb + (uint32_t)(m * 32 + lane);
+                    wn[m] = k < nent ? ld_once(rw + nb + m * 32) : 0u;
                 }
 #pragma unroll
                 for (int m = 0; m < UNROLL; ++m) {
                     const uint32_t k = base + (uint32_t)(m * 32 + lane);
                     if (k < nent) part.add(entry_product<TA>(w[m], xv[m], col, a), E);
+                    w[m] = wn[m];
                 }
             }
             const TA y = part.warp_total(E);
             if (lane == 0) {
                 if (nchunks == 1) {
-                    epi(col, y, ld_inv(inv + col, stream), acc);
+                    epi(col, y, __ldg(inv + col), acc);
                 } else {
                     // the warp finishing the column's last chunk adds the chunk sums in order
                     a.chunk_sum[item] = (double)y;
@@ -513,102 +639,60 @@ __global__ void __launch_bounds__(THREADS, MINB)
                         __threadfence();
                         TA tot = TA(0);
                         for (uint32_t q = 0; q < nchunks; ++q) tot += (TA)__ldcg(a.chunk_sum + first + q);
-                        epi(col, tot, ld_inv(inv + col, stream), acc);
+                        epi(col, tot, __ldg(inv + col), acc);
                     }
                 }
             }
+        } else if (item >= n_cs) {
+            // ---- columns without entries: r = teleport, EMPTY_PER_ITEM of them, coalesced list reads
+            const uint32_t q0 = (item - n_cs) * EMPTY_PER_ITEM;
+            const uint32_t q1 = min(n_empty, q0 + EMPTY_PER_ITEM);
+            const TA *einv = static_cast<const TA *>(a.einv);
+            for (uint32_t q = q0 + lane; q < q1; q += 32) epi(ld_once(a.elist + q), TA(0), ld_once(einv + q), acc);
         } else {
-            // ---- a tile of up to 32 short columns
-            const uint32_t c0 = it.x, ncol = it.y, nent = it.w;
-            // column starts and 1/d_out of lane's column, in flight with the entries
-            const uint32_t mycp = lane < (int)ncol ? ld_stream_u32(a.colptr + c0 + lane, stream) : 0u;
-            const TA myinv = lane < (int)ncol ? ld_inv(inv + c0 + lane, stream) : TA(0);
+            // ---- a slice of 32 short columns, one per lane: step k reads 32 consecutive words
+            const uint32_t slen = it.y & ((1u << META_LEN_BITS) - 1), win = it.y >> META_LEN_BITS;
+            const uint32_t o = it.z;
+            const bool valid = o != SLOT_NONE;
+            const uint32_t len = valid ? (o >> SLOT_LEN_SHIFT) : 0u;
+            const uint32_t col = (win << a.wbits) + (o & ((1u << SLOT_LEN_SHIFT) - 1));
+            const TA myinv = cur.iv;
+            const uint32_t *src = a.sell + 32ull * it.x + lane;
+            ColSum<TA> y;
+            uint32_t w[UNROLL];
 #pragma unroll
-            for (int g = 0; g < TILE_ENTRIES / 32; g += UNROLL) {
-                if ((uint32_t)(g * 32) >= nent) break;
-                uint32_t w[UNROLL];
+            for (int m = 0; m < UNROLL; ++m) w[m] = (uint32_t)m < len ? ld_once(src + 32 * m) : 0u;
+            for (uint32_t k = 0; k < slen; k += UNROLL) {
                 TA xv[UNROLL];
 #pragma unroll
-                for (int m = 0; m < UNROLL; ++m) {
-                    const uint32_t k = (uint32_t)((g + m) * 32 + lane);
-                    w[m] = k < nent ? ld_stream_u32(a.rowc + e0 + k, stream) : 0u;
-                }
+                for (int m = 0; m < UNROLL; ++m)
+                    xv[m] = k + m < len ? to_acc(ld_x(x_in + (w[m] & umask))) : TA(0);
+                uint32_t wn[UNROLL];
+#pragma unroll
+                for (int m = 0; m < UNROLL; ++m)
+                    wn[m] = k + UNROLL + m < len ? ld_once(src + 32ull * (k + UNROLL + m)) : 0u;
 #pragma unroll
                 for (int m = 0; m < UNROLL; ++m) {
-                    const uint32_t k = (uint32_t)((g + m) * 32 + lane);
-                    xv[m] = k < nent ? to_acc(ld_x(x_in + (w[m] & umask), keep)) : TA(0);
-                }
-                if (g == 0) {
-                    if (lane < (int)ncol) cp[lane] = mycp - e0;
-                    if (lane == 0) cp[ncol] = nent;
-                    __syncwarp();
-                }
-#pragma unroll
-                for (int m = 0; m < UNROLL; ++m) {
-                    const uint32_t k = (uint32_t)((g + m) * 32 + lane);
-                    if (k < nent) {
-                        uint32_t col = 0;
-                        if ((w[m] >> a.scale) == a.cmax) {
-                            // the count did not fit inline: find this entry's column
-                            uint32_t lo = 0, hi = ncol;
-                            while (lo < hi) {
-                                const uint32_t mid = (lo + hi) >> 1;
-                                if (cp[mid + 1] <= k)
-                                    lo = mid + 1;
-                                else
-                                    hi = mid;
-                            }
-                            col = c0 + lo;
-                        }
-                        prod[k] = entry_product<TA>(w[m], xv[m], col, a);
-                    }
+                    if (k + m < len) y.add(entry_product<TA>(w[m], xv[m], col, a), E);
+                    w[m] = wn[m];
                 }
             }
-            if (nent == 0) {
-                if (lane < (int)ncol) cp[lane] = mycp - e0;
-                if (lane == 0) cp[ncol] = nent;
-            }
-            __syncwarp();
-            // short columns: one lane each, entries in order
-            uint32_t medium = 0;
-            if (lane < (int)ncol) {
-                const uint32_t s = cp[lane], e = cp[lane + 1];
-                if (e - s <= a.lane_short) {
-                    ColSum<TA> y;
-                    for (uint32_t k = s; k < e; ++k) y.add(prod[k], E);
-                    epi(c0 + lane, y.value(E), myinv, acc);
-                } else {
-                    medium = 1;
-                }
-            }
-            // medium columns: the whole warp, lanes stride, fixed shuffle tree
-            uint32_t mm = __ballot_sync(0xffffffffu, medium);
-            while (mm) {
-                const int j = __ffs(mm) - 1;
-                mm &= mm - 1;
-                const uint32_t s = cp[j], e = cp[j + 1];
-                ColSum<TA> y;
-                for (uint32_t k = s + lane; k < e; k += 32) y.add(prod[k], E);
-                const TA yt = y.warp_total(E);
-                const TA invj = __shfl_sync(0xffffffffu, myinv, j);
-                if (lane == 0) epi(c0 + j, yt, invj, acc);
-            }
-            __syncwarp();
+            if (valid) epi(col, y.value(E), myinv, acc);
         }
         item = next;
-        it = nit;
+        cur = nxt;
     }
-    const Fx128 bt = fx_block_sum<NT>(acc.s, s_fx);
-    if (threadIdx.x == 0 && (bt.hi | bt.lo)) fx_atomic_add(a.acc + 2 * (iter + 1), bt);
+    // exact sums per warp, added with one atomic pair per warp: the kernel
+    // keeps no shared memory, so the driver leaves the whole array to L1
+    const Fx128 bt = fx_warp_sum(acc.s);
+    if (lane == 0 && (bt.hi | bt.lo)) fx_atomic_add(a.acc + 2 * (iter + 1), bt);
     if (EXT && (a.flags & PP_K3_DANGLING)) {
-        __syncthreads();
-        const Fx128 bd = fx_block_sum<NT>(acc.dm, s_fx);
-        if (threadIdx.x == 0 && (bd.hi | bd.lo)) fx_atomic_add(a.dmass + 2 * (iter + 1), bd);
+        const Fx128 bd = fx_warp_sum(acc.dm);
+        if (lane == 0 && (bd.hi | bd.lo)) fx_atomic_add(a.dmass + 2 * (iter + 1), bd);
     }
     if (EXT && (a.flags & PP_K3_CONVERGE)) {
-        __syncthreads();
-        const Fx128 bf = fx_block_sum<NT>(acc.df, s_fx);
-        if (threadIdx.x == 0 && (bf.hi | bf.lo)) fx_atomic_add(a.delta + 2 * (iter + 1), bf);
+        const Fx128 bf = fx_warp_sum(acc.df);
+        if (lane == 0 && (bf.hi | bf.lo)) fx_atomic_add(a.delta + 2 * (iter + 1), bf);
     }
 }
 
@@ -652,43 +736,62 @@ __global__ void __launch_bounds__(256) l1_scale_kernel(const TO *r, uint32_t N, 
 struct Layout {
     void *x[2];
     void *invp;  // 1/d_out in storage order (TA)
-    uint32_t *bound, *bound_item;
+    uint4 *wcnt, *woff;
+    uint32_t *slot;
+    uint2 *meta;
+    void *invs;
+    uint32_t *elist;
+    void *einv;
+    uint32_t *sell;
     uint4 *item;
     double *chunk_sum;
     uint32_t *ticket;
-    uint64_t *plan_status;
     unsigned long long *acc;
     int *fx_exp;
     double *ipart;
     Ctl *ctl;
-    uint32_t *ctr;
     // the variants only
     void *rb[2];  // r in storage order (TA), ping-pong
     unsigned long long *dmass, *delta;
     uint32_t *state;
+    uint32_t wbits, nwin;
+    uint64_t max_slices;
     size_t bytes;
 };
 
+// The sliced copy holds each short column's entries plus padding; with the
+// columns of a window sorted by decreasing length, a window pads fewer than
+// 32 * shortmax words (slice t is as long as its first column, which is no
+// longer than any column of slice t - 1), so M + windows * 32 * SHORTMAX_MAX
+// words always suffice (nnz <= M).
 inline Layout layout(void *ws, uint64_t M, uint32_t scale, uint32_t iters, pp_dtype dt, bool ext = false) {
     Carver c(ws);
     Layout L;
     const uint64_t N = 1ull << scale;
+    L.wbits = win_bits(scale);
+    L.nwin = (uint32_t)(N >> L.wbits);
+    const uint64_t max_slices = (uint64_t)L.nwin * ceil_div(1ull << L.wbits, 32);
+    L.max_slices = max_slices;
     const uint64_t max_items = N + M / CHUNK_MIN + 1;
     const size_t xs = dt == PP_FP64 ? 8 : (dt == PP_FP32 ? 4 : 2);
     L.x[0] = c.take<char>(N * xs);
     L.x[1] = c.take<char>(N * xs);
     L.invp = c.take<char>(N * (dt == PP_FP64 ? 8 : 4));
-    L.bound = c.take<uint32_t>(N);
-    L.bound_item = c.take<uint32_t>(N);
+    L.wcnt = c.take<uint4>(L.nwin);
+    L.woff = c.take<uint4>(L.nwin);
+    L.slot = c.take<uint32_t>(32 * max_slices);
+    L.meta = c.take<uint2>(max_slices);
+    L.invs = c.take<char>(32 * max_slices * (dt == PP_FP64 ? 8 : 4));
+    L.elist = c.take<uint32_t>(N);
+    L.einv = c.take<char>(N * (dt == PP_FP64 ? 8 : 4));
+    L.sell = c.take<uint32_t>(M + (uint64_t)L.nwin * 32 * SHORTMAX_MAX);
     L.item = c.take<uint4>(max_items);
     L.chunk_sum = c.take<double>(max_items);
     L.ticket = c.take<uint32_t>(max_items);
-    L.plan_status = c.take<uint64_t>(ceil_div(N, PLAN_TILE));
     L.acc = c.take<unsigned long long>(2ull * (iters + 1));
     L.fx_exp = c.take<int>((uint64_t)iters + 1);
     L.ipart = c.take<double>(SETUP_BLOCKS);
     L.ctl = c.take<Ctl>(1);
-    L.ctr = c.take<uint32_t>(1);
     L.rb[0] = L.rb[1] = nullptr;
     L.dmass = L.delta = nullptr;
     L.state = nullptr;
@@ -762,21 +865,26 @@ pp_status run_unroll(const pp_graph *g, const double *r0, uint32_t iters, double
     a.ovf_key = g->ovf_key;
     a.ovf_cnt = g->ovf_cnt;
     a.info = g->info;
-    a.bound = L.bound;
-    a.bound_item = L.bound_item;
+    a.wbits = L.wbits;
+    a.nwin = L.nwin;
+    a.wcnt = L.wcnt;
+    a.woff = L.woff;
+    a.slot = L.slot;
+    a.meta = L.meta;
+    a.invs = L.invs;
+    a.elist = L.elist;
+    a.einv = L.einv;
+    a.sell = L.sell;
     a.item = L.item;
     a.chunk_sum = L.chunk_sum;
     a.ticket = L.ticket;
-    a.plan_status = L.plan_status;
     a.acc = L.acc;
     a.fx_exp = L.fx_exp;
     a.ipart = L.ipart;
     a.ctl = L.ctl;
-    a.ctr = L.ctr;
     a.c = c;
     a.shortmax = (uint32_t)tuning("k3_shortmax");
     a.chunk = (uint32_t)tuning("k3_chunk");
-    a.lane_short = (uint32_t)tuning("k3_lane_short");
     a.flags = EXT ? var.flags : 0u;
     a.tol = var.tol;
     a.dmass = L.dmass;
@@ -789,23 +897,26 @@ pp_status run_unroll(const pp_graph *g, const double *r0, uint32_t iters, double
     TS *x0 = static_cast<TS *>(L.x[0]);
     TS *x1 = static_cast<TS *>(L.x[1]);
     setup_kernel<<<SETUP_BLOCKS, 256, 0, s>>>(a, r0);
-    plan_kernel<<<(unsigned)ceil_div(N, PLAN_TILE), PLAN_THREADS, 0, s>>>(a);
-    plan_items_kernel<<<(unsigned)std::min<uint64_t>(ceil_div(N, 256), 4096), 256, 0, s>>>(a);
+    window_count_kernel<<<L.nwin, WIN_THREADS, 0, s>>>(a);
+    window_scan_kernel<<<1, SCAN_THREADS, 0, s>>>(a);
+    window_fill_kernel<<<L.nwin, WIN_THREADS, 0, s>>>(a);
+    order_inv_kernel<TA><<<(unsigned)std::min<uint64_t>(ceil_div(32ull * L.max_slices + N, 256), 16ull * sm_count()),
+                           256, 0, s>>>(a, inv);
     TA *invp = static_cast<TA *>(L.invp);  // 1/d_out in storage order
     // one wave of blocks (each sums the norm's partials once)
     const unsigned nblocks = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(ceil_div(N, 256), 8ull * sm_count()));
     normalize_kernel<TS, TA, TO><<<nblocks, 256, 0, s>>>(a, r0, inv, invp, x0, r_out, EXT ? rb0 : nullptr);
-    count_launch(4);
+    count_launch(6);
 
     auto *k_mid = iterate_kernel<TS, TA, TO, false, UNROLL, MINB, EXT>;
     auto *k_last = iterate_kernel<TS, TA, TO, !EXT, UNROLL, MINB, EXT>;
     constexpr int NT = THREADS;
-    constexpr size_t smem = Smem<TA>::total(WARPS);
+    constexpr size_t smem = 0;
     // the carveout attributes and the occupancy, once per instantiation and device
     static PerDevice cached;  // o_mid << 16 | o_last
     const uint32_t cv = (uint32_t)cached.get([&] {
-        set_smem(k_mid, MINB, smem);
-        set_smem(k_last, MINB, smem);
+        set_smem(k_mid, MINB, 0);
+        set_smem(k_last, MINB, 0);
         return (int64_t)(((uint32_t)occupancy(k_mid, NT, smem) << 16) | (uint32_t)occupancy(k_last, NT, smem));
     });
     const int o_mid = (int)(cv >> 16), o_last = (int)(cv & 0xffff);
@@ -840,23 +951,24 @@ pp_status run(const pp_graph *g, const double *r0, uint32_t iters, double c, pp_
     const Variant none{0u, 0.0, nullptr};
     const bool u4 = tuning(sizeof(TA) == 8 ? "k3_unroll_f64" : "k3_unroll_f32") == 4;
     switch (tuning("k3_minblocks")) {
-        case 5:
-            return u4 ? run_unroll<TS, TA, TO, 4, 5, false>(g, r0, iters, c, dt, r_out, r_l1, L, s, none)
-                      : run_unroll<TS, TA, TO, 8, 5, false>(g, r0, iters, c, dt, r_out, r_l1, L, s, none);
-        case 6:
-            return u4 ? run_unroll<TS, TA, TO, 4, 6, false>(g, r0, iters, c, dt, r_out, r_l1, L, s, none)
-                      : run_unroll<TS, TA, TO, 8, 6, false>(g, r0, iters, c, dt, r_out, r_l1, L, s, none);
-        default:
+        case 4:
             return u4 ? run_unroll<TS, TA, TO, 4, 4, false>(g, r0, iters, c, dt, r_out, r_l1, L, s, none)
                       : run_unroll<TS, TA, TO, 8, 4, false>(g, r0, iters, c, dt, r_out, r_l1, L, s, none);
+        case 8:
+            return u4 ? run_unroll<TS, TA, TO, 4, 8, false>(g, r0, iters, c, dt, r_out, r_l1, L, s, none)
+                      : run_unroll<TS, TA, TO, 8, 8, false>(g, r0, iters, c, dt, r_out, r_l1, L, s, none);
+        default:
+            return u4 ? run_unroll<TS, TA, TO, 4, 6, false>(g, r0, iters, c, dt, r_out, r_l1, L, s, none)
+                      : run_unroll<TS, TA, TO, 8, 6, false>(g, r0, iters, c, dt, r_out, r_l1, L, s, none);
     }
 }
 
-// The variants run one instantiation (unroll 4, 4 blocks per SM).
+// The variants run one instantiation per precision (4 blocks per SM; unroll
+// 8 for binary32 sums, 4 for the binary64 fixed-point sums).
 template <typename TS, typename TA, typename TO>
 pp_status run_ext(const pp_graph *g, const double *r0, uint32_t iters, double c, pp_dtype dt, TO *r_out,
                   double *r_l1, const Layout &L, cudaStream_t s, const Variant &var) {
-    return run_unroll<TS, TA, TO, 4, 4, true>(g, r0, iters, c, dt, r_out, r_l1, L, s, var);
+    return run_unroll<TS, TA, TO, sizeof(TA) == 8 ? 4 : 8, 4, true>(g, r0, iters, c, dt, r_out, r_l1, L, s, var);
 }
 
 }  // namespace k3

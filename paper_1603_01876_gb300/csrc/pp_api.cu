@@ -24,11 +24,10 @@ struct Knob {
 };
 Knob g_knobs[] = {
     {"k3_unroll_f32", {8}, 2, {4, 8}},
-    {"k3_unroll_f64", {8}, 2, {4, 8}},
-    {"k3_minblocks", {4}, 3, {4, 5, 6}},
-    {"k3_shortmax", {256}, 3, {64, 128, 256}},
-    {"k3_chunk", {2048}, 2, {2048, 4096}},
-    {"k3_lane_short", {16}, 3, {8, 16, 32}},
+    {"k3_unroll_f64", {4}, 2, {4, 8}},
+    {"k3_minblocks", {4}, 3, {4, 6, 8}},
+    {"k3_shortmax", {256}, 3, {128, 256, 512}},
+    {"k3_chunk", {4096}, 2, {2048, 4096}},
     {"k3b_shortmax", {256}, 2, {128, 256}},
     {"k3b_chunk", {512}, 3, {256, 512, 1024}},
     {"k3b_vec", {1}, 2, {0, 1}},

@@ -1,8 +1,8 @@
 """Autotuner for Kernel 3's work split (the knobs of pp_set_tuning).
 
-The thresholds that decide which columns are cut into chunks, how long a
-chunk is, which tile columns one lane sums, plus the unroll depth and the
-register budget, are measured on the GPU at hand: each setting runs the
+The threshold that decides which columns are cut into chunks (the others
+are summed one per lane in 32-column slices), how long a chunk is, plus the
+unroll depth and the register budget, are measured on the GPU at hand: each setting runs the
 20-iteration Kernel 3 on a graph of the requested scale (CUDA events, after
 warm-up) and the fastest setting is kept.  The single-vector search is a
 coordinate descent over the knobs (two rounds), the batched one a full grid.
@@ -19,10 +19,9 @@ import os
 import time
 
 SINGLE_KNOBS = {
-    "k3_shortmax": [64, 128, 256],
-    "k3_lane_short": [8, 16, 32],
+    "k3_shortmax": [128, 256, 512],
     "k3_chunk": [2048, 4096],
-    "k3_minblocks": [4, 5, 6],
+    "k3_minblocks": [4, 6, 8],
     "k3_unroll_f32": [4, 8],
 }
 BATCH_KNOBS = {

@@ -1,6 +1,7 @@
 """Kernel 3 under non-default tuning knobs, against the oracle.
 
-The thresholds move columns between the tile, warp and chunk paths; every
+The thresholds move columns between the sliced one-lane-per-column path
+and the chunk path; every
 setting must stay within the stated tolerances (binary64 L1 <= 1e-12,
 binary32 L1 <= 1e-6 and max relative <= 1e-4) and be reproducible.
 """
@@ -12,10 +13,10 @@ from gpu_helpers import host_u32, rank_errors
 pytestmark = pytest.mark.gpu
 
 SINGLE = [
-    {"k3_shortmax": 64, "k3_lane_short": 8},
-    {"k3_chunk": 4096, "k3_lane_short": 32},
-    {"k3_shortmax": 128, "k3_minblocks": 6, "k3_unroll_f32": 4, "k3_unroll_f64": 4},
-    {"k3_minblocks": 5, "k3_chunk": 4096, "k3_shortmax": 64},
+    {"k3_shortmax": 128},
+    {"k3_chunk": 2048, "k3_shortmax": 512},
+    {"k3_shortmax": 128, "k3_minblocks": 8, "k3_unroll_f32": 8, "k3_unroll_f64": 8},
+    {"k3_minblocks": 4, "k3_chunk": 2048},
 ]
 BATCHED = [{"k3b_shortmax": 128, "k3b_chunk": 256}, {"k3b_chunk": 1024}, {"k3b_vec": 0},
            {"k3b_vec": 0, "k3b_chunk": 256}]
