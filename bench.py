@@ -179,6 +179,16 @@ def run_ours(args):
     import paper_1603_01876_gb300 as pp
 
     world, rank, local = dist_env()
+    # the oracle on the same graph, in a child process started before the
+    # first CUDA call, for the errors against it reported per run
+    oracle_run = None
+    if rank == 0 and not args.no_oracle:
+        from oracle import fullsize
+
+        import atexit
+
+        oracle_run = fullsize.start(args.scale, rank_seed(rank))
+        atexit.register(oracle_run.cancel)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
@@ -275,6 +285,7 @@ def run_ours(args):
 
     l1_fp32, maxrel_fp32 = errors(r_out)
     l1_bf, maxrel_bf = errors(r_bf)
+    ranks_host = {"fp64": r64.cpu().numpy(), args.dtype: r_out.cpu().numpy(), "bf16": r_bf.cpu().numpy()}
 
     # Kernel 3 variants on the same graph (pp_pagerank_ex): the dangling-node
     # term (20 iterations), and with the convergence test as well
@@ -439,12 +450,33 @@ def run_ours(args):
         del pws
         torch.cuda.empty_cache()
         out["batched"] = run_batched(dev)
+    if oracle_run is not None:
+        out["accuracy_vs_oracle"] = accuracy_vs_oracle(oracle_run, ranks_host, info)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(scale, seed, max_seconds=args.cpu_seconds)
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def accuracy_vs_oracle(run, ranks, info, timeout=3600):
+    """Errors of this run's ranks against the oracle's (binary64, one thread,
+    the same graph and start vector), relative to norm(r, 1), and whether
+    Kernel 2's scalars agree."""
+    import numpy as np
+
+    want = run.wait(timeout=timeout)
+    r = want["r"]
+    out = {"reference": "CPU oracle, binary64, one thread, the same graph and start vector",
+           "k2_scalars_equal": all(info[k] == want[k] for k in ("nnz0", "nnz", "dmax", "vmax", "ties")),
+           "oracle_seconds": want["seconds"]}
+    for name, got in ranks.items():
+        d = np.abs(got.astype(np.float64) - r)
+        nz = r != 0
+        out[name] = {"l1": float(d.sum() / np.abs(r).sum()),
+                     "max_rel": float((d[nz] / np.abs(r[nz])).max()) if nz.any() else 0.0}
+    return out
 
 
 def run_k3_only(args):
@@ -643,6 +675,8 @@ def main():
     ap.add_argument("--scale", type=int, default=SCALE)
     ap.add_argument("--dtype", choices=["fp32", "fp64", "bf16"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-oracle", action="store_true",
+                    help="skip the errors against the oracle run on the whole graph (a few minutes of one host core)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-batched", action="store_true", help="skip the batched Kernel 3 section")
     ap.add_argument("--no-files", action="store_true", help="skip the edge-file (Kernel 1 with files) section")

@@ -11,6 +11,32 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a); runs the CUDA path through the C-ABI")
     config.addinivalue_line("markers", "slow: long-running; still part of its marker's suite")
+    config.addinivalue_line("markers", "oracle_fullsize(scales): compares with the oracle run on the whole graph "
+                                       "of these scales (started in child processes when the session begins)")
+
+
+ORACLE_SEED = 1
+
+
+def pytest_collection_finish(session):
+    """Start the whole-graph oracle runs that the selected tests need, in
+    child processes, so that they overlap the GPU tests collected before them."""
+    scales = set()
+    for item in session.items:
+        m = item.get_closest_marker("oracle_fullsize")
+        if m and m.args:
+            scales.update(m.args[0])
+    runs = {}
+    if scales:
+        from oracle import fullsize
+
+        runs = {s: fullsize.start(s, ORACLE_SEED) for s in sorted(scales)}
+    session.config.pp_oracle_runs = runs
+
+
+def pytest_sessionfinish(session, exitstatus):
+    for run in getattr(session.config, "pp_oracle_runs", {}).values():
+        run.cancel()
 
 
 @pytest.fixture(scope="session", autouse=True)

@@ -1,9 +1,11 @@
 """Parity at full size, in the configuration the benchmark times (the
 stored tuning for this GPU applied, as bench.py does).
 
-The oracle cannot rerun a 2^28-edge pipeline within a test, so the checks at
-scale 24 (and 26, when PP_FULLSIZE_26=1) are the definitions evaluated
-directly on the host and properties that hold at any size:
+Beside the comparison with the oracle's whole-graph run
+(test_gpu_oracle_fullsize.py), the checks here evaluate the definitions
+directly on the host from the GPU's own intermediate arrays, at scales 24
+and 26 (PP_FULLSIZE_SKIP_26=1 leaves scale 26 out: its host-side checks
+hold about 40 GB), and properties that hold at any size:
 
 - Kernel 1: the output is ordered by (u, v) and is a permutation of the input
   (compared with a library sort of the same keys).
@@ -60,8 +62,8 @@ def fullsize(request):
     import paper_1603_01876_gb300 as pp
 
     scale = request.param
-    if scale == 26 and os.environ.get("PP_FULLSIZE_26") != "1":
-        pytest.skip("scale 26 runs with PP_FULLSIZE_26=1 (about 40 GB of host memory)")
+    if scale == 26 and os.environ.get("PP_FULLSIZE_SKIP_26") == "1":
+        pytest.skip("scale 26 left out (PP_FULLSIZE_SKIP_26=1)")
     # the benchmark's launch configuration: the stored tuning for this GPU
     from paper_1603_01876_gb300 import tune
 

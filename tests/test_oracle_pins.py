@@ -62,3 +62,26 @@ def test_k3_sums_output(O, kron12):
     r, sums = O.k3_pagerank(R, r0, 4, 0.85, want_sums=True)
     assert abs(sums[0] - 1.0) < 1e-15
     assert abs(sums[4] - r.sum()) < 1e-14
+
+
+def test_fullsize_script_matches_direct_oracle_calls(tmp_path, k0):
+    """oracle/fullsize.py stores what the oracle itself returns (no other arithmetic)."""
+    import hashlib
+
+    import oracle
+    from oracle import fullsize
+
+    scale, seed = 12, 3
+    path = fullsize.compute(scale, seed, out=str(tmp_path / "o.npz"))
+    d = fullsize.load(path)
+    u, v = k0.edges_host(scale, seed)
+    us, vs = oracle.k1_sort(u, v)
+    A = oracle.k2_filter(us, vs, 1 << scale)
+    r = oracle.k3_pagerank(A, k0.r0_host(1 << scale, seed), 20, 0.85)
+    sha = lambda a: hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
+    assert d["us_sha"] == sha(us) and d["vs_sha"] == sha(vs)
+    assert d["col_sha"] == sha(A["col"]) and d["cnt_sha"] == sha(A["cnt"]) and d["val_sha"] == sha(A["val"])
+    assert (d["nnz0"], d["nnz"], d["dmax"], d["vmax"]) == (A["nnz0"], A["nnz"], A["dmax"], A["vmax"])
+    np.testing.assert_array_equal(d["d_in"], A["d_in"])
+    np.testing.assert_array_equal(d["rowptr"], A["rowptr"])
+    np.testing.assert_array_equal(d["r"], r)
