@@ -55,7 +55,8 @@ namespace k3 {
 constexpr int THREADS = 256;
 constexpr int WARPS = THREADS / 32;
 constexpr int SHORTMAX_MAX = 512;  // largest long-column threshold (k3_shortmax)
-constexpr int CHUNK_MIN = 2048;    // smallest long-column chunk (k3_chunk)
+constexpr int CHUNK_MIN = 256;     // smallest long-column chunk (small graphs; the k3_chunk knob is 2048 or 4096)
+constexpr int SHORTMAX_MIN = 32;   // smallest long-column threshold (small graphs)
 constexpr uint32_t NENT_BITS = 13; // a long chunk's item: entries | chunks of the column << NENT_BITS
 constexpr uint32_t LONG_FLAG = 0x80000000u;
 constexpr int SETUP_BLOCKS = 512;  // fixed, so the start-vector reduction is reproducible
@@ -70,6 +71,11 @@ constexpr uint32_t SLOT_NONE = 0xffffffffu;
 constexpr uint32_t META_LEN_BITS = 11;
 constexpr uint32_t MAX_WIN_BITS = 16;
 constexpr uint32_t EMPTY_PER_ITEM = 1024;  // empty columns per work item
+// Exact sums (sum(r), and for the variants the dangling mass and the norm of
+// the change) are spread over FX_SLOTS 128-bit accumulators per iterate, so
+// that the warps' atomics do not all meet at one address; the readers add
+// the slots (exactly: any order gives the same bits).
+constexpr int FX_SLOTS = 32;
 
 // log2 of the window width: about 1024 windows, each of 32 .. 65536 columns.
 inline uint32_t win_bits(uint32_t scale) {
@@ -113,10 +119,10 @@ struct Args {
     uint32_t *elist;          // [N] positions of the columns without entries
     void *einv;               // [N] their 1/d_out (TA), in list order
     uint32_t *sell;           // the short columns' entries, sliced ELLPACK
-    uint4 *item;              // [N + M/CHUNK_MIN + 1] long-column chunks
+    uint4 *item;              // [min(N, M/(SHORTMAX_MIN+1)) + M/CHUNK_MIN + 1] long-column chunks
     double *chunk_sum;        // [same] partial sums of long-column chunks
     uint32_t *ticket;         // [same] finished-chunk counters, at a column's first item
-    unsigned long long *acc;  // [2 * (iters + 1)] sum(r) per iterate, 128-bit fixed point
+    unsigned long long *acc;  // [2 * FX_SLOTS * (iters + 1)] sum(r) per iterate, 128-bit fixed point
     int *fx_exp;              // [iters + 1] scale exponent of each accumulator
     double *ipart;            // [SETUP_BLOCKS]
     Ctl *ctl;
@@ -126,8 +132,8 @@ struct Args {
     // variants (pp_pagerank_ex); zero / null for the plain iteration
     uint32_t flags;                  // PP_K3_DANGLING | PP_K3_CONVERGE
     double tol;                      // convergence threshold on norm(r_k - r_(k-1), 1)
-    unsigned long long *dmass;       // [2 * (iters + 1)] sum of r over dangling rows, per iterate
-    unsigned long long *delta;       // [2 * (iters + 1)] norm(r_k - r_(k-1), 1), per iterate
+    unsigned long long *dmass;       // [2 * FX_SLOTS * (iters + 1)] sum of r over dangling rows, per iterate
+    unsigned long long *delta;       // [2 * FX_SLOTS * (iters + 1)] norm(r_k - r_(k-1), 1), per iterate
     uint32_t *state;                 // [0] converged, [1] iterations run
 };
 
@@ -142,6 +148,27 @@ __device__ __forceinline__ uint32_t ovf_lookup(const uint64_t *keys, const uint3
             hi = mid;
     }
     return (lo < n && __ldg(keys + lo) == key) ? __ldg(cnts + lo) : 0u;
+}
+
+// The accumulator slots of iterate k.
+__device__ __forceinline__ unsigned long long *fx_slot(unsigned long long *base, uint32_t k, uint32_t slot) {
+    return base + 2ull * ((uint64_t)k * FX_SLOTS + slot % FX_SLOTS);
+}
+
+// Value of the exact sum of iterate k (every thread of the warp calls it;
+// lane j reads slot j, the warp adds them in 128-bit fixed point).
+__device__ __forceinline__ double fx_slots_value(const unsigned long long *base, uint32_t k, int E) {
+    static_assert(FX_SLOTS == 32, "one slot per lane");
+    const int lane = threadIdx.x & 31;
+    const unsigned long long *p = base + 2ull * ((uint64_t)k * FX_SLOTS + lane);
+    Fx128 t{p[0], p[1]};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t h = __shfl_xor_sync(0xffffffffu, t.hi, o);
+        const uint64_t l = __shfl_xor_sync(0xffffffffu, t.lo, o);
+        fx_add(t, h, l);
+    }
+    return fx_value(t.hi, t.lo, E);
 }
 
 // ------------------------------------------------------------------- planning
@@ -262,7 +289,8 @@ __global__ void __launch_bounds__(WIN_THREADS) window_fill_kernel(Args a) {
         const uint32_t p = p0 + i;
         const uint32_t s = __ldg(a.colptr + p), len = __ldg(a.colptr + p + 1) - s;
         if (len > L) {
-            // a kept column has at most M/2 <= 2^30 entries (the largest one is removed), so nc < 2^19
+            // a kept column has at most M/2 entries (the largest one is removed); the host picks
+            // the chunk so that nc < 2^19 fits the item's high bits
             const uint32_t nc = (len + a.chunk - 1) / a.chunk;
             const uint32_t o = atomicAdd(&s_item, nc);
             for (uint32_t k = 0; k < nc; ++k) {
@@ -352,7 +380,7 @@ __global__ void __launch_bounds__(256) setup_kernel(Args a, const double *r0) {
     __shared__ double s_red[32];
     const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = gtid; i < 2ull * (a.iters + 1); i += stride) {
+    for (uint64_t i = gtid; i < 2ull * FX_SLOTS * (a.iters + 1); i += stride) {
         a.acc[i] = 0;
         if (a.dmass) a.dmass[i] = 0;
         if (a.delta) a.delta[i] = 0;
@@ -413,11 +441,11 @@ __global__ void __launch_bounds__(256) normalize_kernel(Args a, const double *r0
         }
     }
     const Fx128 bt = fx_block_sum<256>(acc, s_fx);
-    if (threadIdx.x == 0 && (bt.hi | bt.lo)) fx_atomic_add(a.acc, bt);
+    if (threadIdx.x == 0 && (bt.hi | bt.lo)) fx_atomic_add(fx_slot(a.acc, 0, blockIdx.x), bt);
     if (a.flags & PP_K3_DANGLING) {
         __syncthreads();
         const Fx128 bd = fx_block_sum<256>(dm, s_fx);
-        if (threadIdx.x == 0 && (bd.hi | bd.lo)) fx_atomic_add(a.dmass, bd);
+        if (threadIdx.x == 0 && (bd.hi | bd.lo)) fx_atomic_add(fx_slot(a.dmass, 0, blockIdx.x), bd);
     }
 }
 
@@ -541,7 +569,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
         // the variants: stop once converged; the dangling rows' mass is spread evenly
         if (ld_relaxed_u32(a.state)) return;
         if ((a.flags & PP_K3_CONVERGE) && iter >= 1 &&
-            fx_value(a.delta[2 * iter], a.delta[2 * iter + 1], a.fx_exp[iter]) < a.tol) {
+            fx_slots_value(a.delta, iter, a.fx_exp[iter]) < a.tol) {
             if (blockIdx.x == 0 && threadIdx.x == 0) {
                 a.state[1] = iter;
                 st_relaxed_u32(a.state, 1u);
@@ -549,13 +577,13 @@ __global__ void __launch_bounds__(THREADS, MINB)
             return;
         }
         if (a.flags & PP_K3_DANGLING)
-            tele_extra = a.c / (double)a.N * fx_value(a.dmass[2 * iter], a.dmass[2 * iter + 1], a.fx_exp[iter]);
+            tele_extra = a.c / (double)a.N * fx_slots_value(a.dmass, iter, a.fx_exp[iter]);
     }
     const uint32_t n_chunks = a.ctl->n_chunks;
     const uint32_t n_cs = n_chunks + a.ctl->n_slices;  // chunks and slices; then the empty columns
     const uint32_t n_empty = a.ctl->n_empty;
     const uint32_t n_items = n_cs + (n_empty + EMPTY_PER_ITEM - 1) / EMPTY_PER_ITEM;
-    const double S = fx_value(a.acc[2 * iter], a.acc[2 * iter + 1], a.fx_exp[iter]);
+    const double S = fx_slots_value(a.acc, iter, a.fx_exp[iter]);
     const int E = fx_exponent(S);
     if (blockIdx.x == 0 && threadIdx.x == 0) a.fx_exp[iter + 1] = E;
     const uint32_t umask = (1u << a.scale) - 1u;
@@ -685,14 +713,15 @@ __global__ void __launch_bounds__(THREADS, MINB)
     // exact sums per warp, added with one atomic pair per warp: the kernel
     // keeps no shared memory, so the driver leaves the whole array to L1
     const Fx128 bt = fx_warp_sum(acc.s);
-    if (lane == 0 && (bt.hi | bt.lo)) fx_atomic_add(a.acc + 2 * (iter + 1), bt);
+    const uint32_t gw = blockIdx.x * NW + warp;
+    if (lane == 0 && (bt.hi | bt.lo)) fx_atomic_add(fx_slot(a.acc, iter + 1, gw), bt);
     if (EXT && (a.flags & PP_K3_DANGLING)) {
         const Fx128 bd = fx_warp_sum(acc.dm);
-        if (lane == 0 && (bd.hi | bd.lo)) fx_atomic_add(a.dmass + 2 * (iter + 1), bd);
+        if (lane == 0 && (bd.hi | bd.lo)) fx_atomic_add(fx_slot(a.dmass, iter + 1, gw), bd);
     }
     if (EXT && (a.flags & PP_K3_CONVERGE)) {
         const Fx128 bf = fx_warp_sum(acc.df);
-        if (lane == 0 && (bf.hi | bf.lo)) fx_atomic_add(a.delta + 2 * (iter + 1), bf);
+        if (lane == 0 && (bf.hi | bf.lo)) fx_atomic_add(fx_slot(a.delta, iter + 1, gw), bf);
     }
 }
 
@@ -772,7 +801,9 @@ inline Layout layout(void *ws, uint64_t M, uint32_t scale, uint32_t iters, pp_dt
     L.nwin = (uint32_t)(N >> L.wbits);
     const uint64_t max_slices = (uint64_t)L.nwin * ceil_div(1ull << L.wbits, 32);
     L.max_slices = max_slices;
-    const uint64_t max_items = N + M / CHUNK_MIN + 1;
+    // chunks: at most one per long column plus nnz/chunk, and a long column has
+    // more than SHORTMAX_MIN of the nnz <= M entries
+    const uint64_t max_items = std::min<uint64_t>(N, M / (SHORTMAX_MIN + 1)) + M / CHUNK_MIN + 1;
     const size_t xs = dt == PP_FP64 ? 8 : (dt == PP_FP32 ? 4 : 2);
     L.x[0] = c.take<char>(N * xs);
     L.x[1] = c.take<char>(N * xs);
@@ -788,7 +819,7 @@ inline Layout layout(void *ws, uint64_t M, uint32_t scale, uint32_t iters, pp_dt
     L.item = c.take<uint4>(max_items);
     L.chunk_sum = c.take<double>(max_items);
     L.ticket = c.take<uint32_t>(max_items);
-    L.acc = c.take<unsigned long long>(2ull * (iters + 1));
+    L.acc = c.take<unsigned long long>(2ull * FX_SLOTS * (iters + 1));
     L.fx_exp = c.take<int>((uint64_t)iters + 1);
     L.ipart = c.take<double>(SETUP_BLOCKS);
     L.ctl = c.take<Ctl>(1);
@@ -799,8 +830,8 @@ inline Layout layout(void *ws, uint64_t M, uint32_t scale, uint32_t iters, pp_dt
         const size_t ta = dt == PP_FP64 ? 8 : 4;
         L.rb[0] = c.take<char>(N * ta);
         L.rb[1] = c.take<char>(N * ta);
-        L.dmass = c.take<unsigned long long>(2ull * (iters + 1));
-        L.delta = c.take<unsigned long long>(2ull * (iters + 1));
+        L.dmass = c.take<unsigned long long>(2ull * FX_SLOTS * (iters + 1));
+        L.delta = c.take<unsigned long long>(2ull * FX_SLOTS * (iters + 1));
         L.state = c.take<uint32_t>(2);
     }
     L.bytes = c.size();
@@ -883,8 +914,32 @@ pp_status run_unroll(const pp_graph *g, const double *r0, uint32_t iters, double
     a.ipart = L.ipart;
     a.ctl = L.ctl;
     a.c = c;
-    a.shortmax = (uint32_t)tuning("k3_shortmax");
-    a.chunk = (uint32_t)tuning("k3_chunk");
+    auto *k_mid = iterate_kernel<TS, TA, TO, false, UNROLL, MINB, EXT>;
+    auto *k_last = iterate_kernel<TS, TA, TO, !EXT, UNROLL, MINB, EXT>;
+    constexpr int NT = THREADS;
+    constexpr size_t smem = 0;
+    // the carveout attributes and the occupancy, once per instantiation and device
+    static PerDevice cached;  // o_mid << 16 | o_last
+    const uint32_t cv = (uint32_t)cached.get([&] {
+        set_smem(k_mid, MINB, 0);
+        set_smem(k_last, MINB, 0);
+        return (int64_t)(((uint32_t)occupancy(k_mid, NT, smem) << 16) | (uint32_t)occupancy(k_last, NT, smem));
+    });
+    const int o_mid = (int)(cv >> 16), o_last = (int)(cv & 0xffff);
+    const int sms = sm_count();
+    // A small graph gives each warp a few entries, and the iteration then
+    // lasts as long as its longest item (a chain of dependent loads and
+    // gathers in one warp): halve the long-column threshold and the chunk
+    // while they exceed the entries per warp (resp. 8 times that).  A column
+    // has at most M/2 entries (the largest one is removed), and its chunk
+    // count must fit the item's 19-bit field.
+    const uint64_t per_warp = g->M / ((uint64_t)sms * o_mid * WARPS);
+    uint32_t shortmax = (uint32_t)tuning("k3_shortmax"), chunk = (uint32_t)tuning("k3_chunk");
+    while (shortmax > (uint32_t)SHORTMAX_MIN && shortmax > per_warp) shortmax >>= 1;
+    while (chunk > (uint32_t)CHUNK_MIN && chunk > 8 * per_warp) chunk >>= 1;
+    while ((g->M / 2 + chunk - 1) / chunk >= (1ull << (32 - NENT_BITS))) chunk <<= 1;
+    a.shortmax = shortmax;
+    a.chunk = chunk;
     a.flags = EXT ? var.flags : 0u;
     a.tol = var.tol;
     a.dmass = L.dmass;
@@ -908,19 +963,16 @@ pp_status run_unroll(const pp_graph *g, const double *r0, uint32_t iters, double
     normalize_kernel<TS, TA, TO><<<nblocks, 256, 0, s>>>(a, r0, inv, invp, x0, r_out, EXT ? rb0 : nullptr);
     count_launch(6);
 
-    auto *k_mid = iterate_kernel<TS, TA, TO, false, UNROLL, MINB, EXT>;
-    auto *k_last = iterate_kernel<TS, TA, TO, !EXT, UNROLL, MINB, EXT>;
-    constexpr int NT = THREADS;
-    constexpr size_t smem = 0;
-    // the carveout attributes and the occupancy, once per instantiation and device
-    static PerDevice cached;  // o_mid << 16 | o_last
-    const uint32_t cv = (uint32_t)cached.get([&] {
-        set_smem(k_mid, MINB, 0);
-        set_smem(k_last, MINB, 0);
-        return (int64_t)(((uint32_t)occupancy(k_mid, NT, smem) << 16) | (uint32_t)occupancy(k_last, NT, smem));
-    });
-    const int o_mid = (int)(cv >> 16), o_last = (int)(cv & 0xffff);
-    const int sms = sm_count();
+    // no more blocks than the graph can give work to (warps take items
+    // round-robin, so any grid is correct): an upper bound on the items --
+    // slices, chunks (at most nnz/chunk plus one per long column, and a long
+    // column has more than shortmax of the nnz <= M entries), runs of empty
+    // columns -- over WARPS per block
+    const uint64_t item_bound = L.max_slices + g->M / a.chunk + std::min<uint64_t>(N, g->M / (a.shortmax + 1)) +
+                                N / EMPTY_PER_ITEM + 2;
+    const unsigned blocks_cap = (unsigned)std::max<uint64_t>(1, ceil_div(item_bound, WARPS));
+    const unsigned grid_mid = std::min<unsigned>(sms * o_mid, blocks_cap);
+    const unsigned grid_last = std::min<unsigned>(sms * o_last, blocks_cap);
     for (uint32_t it = 0; it < iters; ++it) {
         const TS *xin = (it & 1) ? x1 : x0;
         TS *xout = (it & 1) ? x0 : x1;
@@ -928,9 +980,9 @@ pp_status run_unroll(const pp_graph *g, const double *r0, uint32_t iters, double
         TA *rout = (it & 1) ? rb0 : rb1;
         // the variants write r every iteration and finish_kernel picks the last one
         if (it + 1 == iters && !EXT)
-            k_last<<<sms * o_last, NT, smem, s>>>(a, invp, xin, xout, r_out, it, rin, rout);
+            k_last<<<grid_last, NT, smem, s>>>(a, invp, xin, xout, r_out, it, rin, rout);
         else
-            k_mid<<<sms * o_mid, NT, smem, s>>>(a, invp, xin, xout, r_out, it, rin, rout);
+            k_mid<<<grid_mid, NT, smem, s>>>(a, invp, xin, xout, r_out, it, rin, rout);
         count_launch();
     }
     if (EXT) {
