@@ -62,6 +62,7 @@ typedef enum {
 #define PP_DEV_RANGE 1u   /* an input vertex id was >= N */
 #define PP_DEV_TIMEOUT 2u /* a bounded cross-block wait expired; outputs are invalid */
 #define PP_DEV_PARSE 4u   /* edge-file text was malformed (pp_parse_tsv) */
+#define PP_DEV_CAPACITY 8u /* an output array was too short for the result (pp_export_csr) */
 
 /* Slots of pp_graph.info (device uint64[PP_INFO_LEN]), written by Kernel 2. */
 #define PP_INFO_NNZ0 0       /* nonzeros of A before the column filters */
@@ -190,6 +191,27 @@ pp_status pp_build_filter_normalize_workspace(uint64_t M, uint32_t scale, size_t
 pp_status pp_build_filter_normalize(const uint32_t *u_sorted, const uint32_t *v_sorted, uint64_t M,
                                     uint32_t scale, pp_supernode_rule rule, const pp_graph *g,
                                     void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * Kernel 2's filtered matrix A (Sec. IV-C step 4, A(i,:) = A(i,:) ./ d_out(i))
+ * in compressed-row form, in vertex order: row u holds the entries of start
+ * vertex u with their end vertices ascending.
+ *   rowptr[N+1]  (uint64) row u is entries rowptr[u] .. rowptr[u+1]-1;
+ *                rowptr[N] = nnz = g->info[PP_INFO_NNZ]
+ *   col[nnz]     end vertex v of each entry
+ *   cnt[nnz]     count(u,v), the number of edges from u to v (sparse(u,v,1))
+ *   val64[nnz]   cnt / d_out(u), IEEE binary64 division (NULL: not written)
+ *   val32[nnz]   (float)cnt / (float)d_out(u), IEEE binary32 division (NULL:
+ *                not written)
+ * All device arrays owned by the caller.  cap is the room (entries) in col,
+ * cnt, val64 and val32; nnz <= g->M, so cap = g->M always suffices.  If nnz
+ * exceeds cap, those four are left untouched, rowptr is still written and
+ * PP_DEV_CAPACITY is recorded in the device error word.  The graph is only
+ * read; workspace from pp_export_csr_workspace(g->M, g->scale).
+ */
+pp_status pp_export_csr_workspace(uint64_t M, uint32_t scale, size_t *bytes);
+pp_status pp_export_csr(const pp_graph *g, uint64_t *rowptr, uint32_t *col, uint32_t *cnt, double *val64,
+                        float *val32, uint64_t cap, void *workspace, size_t workspace_bytes, void *stream);
 
 /*
  * Kernel 3 (Sec. IV-D and the appendix): from the start vector r0 (device

@@ -7,6 +7,7 @@ library is missing: there is no CPU fallback.
 
     sort_edges(u, v, scale)                      Kernel 1 (Sec. IV-B)
     build_filter_normalize(us, vs, scale, rule)  Kernel 2 (Sec. IV-C) -> Graph
+    export_csr(graph)                            Kernel 2's A in vertex-order rows
     pagerank(graph, r0, iters, c, dtype)         Kernel 3 (Sec. IV-D)
     pipeline_host(u, v, scale, r0, ...)          Kernels 1-3 from host buffers
 
@@ -26,7 +27,7 @@ RULES = {"lowest": 0, "all_ties": 1}
 INFO = {"nnz0": 0, "nnz": 1, "dmax": 2, "vmax": 3, "ties": 4, "novf": 5, "supernodes": 6}
 INFO_LEN = 8
 GRAPH_ARRAYS = 11
-DEV_RANGE, DEV_TIMEOUT = 1, 2
+DEV_RANGE, DEV_TIMEOUT, DEV_PARSE, DEV_CAPACITY = 1, 2, 4, 8
 
 
 class PPError(RuntimeError):
@@ -81,6 +82,8 @@ def _lib():
             "pp_pagerank_batched_capture": [ctypes.POINTER(CGraph), u32, vp, u32, u32, dbl, vp, vp, ctypes.c_size_t,
                                             vp, ctypes.POINTER(vp)],
             "pp_exec_launch": [vp, vp],
+            "pp_export_csr_workspace": [u64, u32, sz],
+            "pp_export_csr": [ctypes.POINTER(CGraph), vp, vp, vp, vp, vp, u64, vp, ctypes.c_size_t, vp],
             "pp_exec_destroy": [vp],
         }
         for name, args in sig.items():
@@ -237,6 +240,27 @@ def build_filter_normalize(us, vs, scale, rule="lowest", graph=None, workspace=N
                                           ws.numel(), _stream(stream, dev))
     _check("pp_build_filter_normalize", st)
     return g
+
+
+def export_csr(graph, cap=None, values=True, workspace=None, stream=None):
+    """Kernel 2's filtered A in compressed rows, vertex order (pp_export_csr):
+    (rowptr int64[N+1], col int32[cap], cnt int32[cap], val64 float64[cap],
+    val32 float32[cap]); the first rowptr[N] entries are valid.  The value
+    arrays are None with values=False."""
+    dev = graph.colptr.device
+    cap = graph.M if cap is None else int(cap)
+    rowptr = torch.empty(graph.N + 1, dtype=torch.int64, device=dev)
+    col = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    cnt = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    v64 = torch.empty(max(cap, 1), dtype=torch.float64, device=dev) if values else None
+    v32 = torch.empty(max(cap, 1), dtype=torch.float32, device=dev) if values else None
+    need = ctypes.c_size_t(0)
+    _check("pp_export_csr_workspace", _lib().pp_export_csr_workspace(graph.M, graph.scale, ctypes.byref(need)))
+    ws = workspace if workspace is not None and workspace.numel() >= need.value else _workspace(need.value, dev)
+    st = _lib().pp_export_csr(ctypes.byref(graph.c), _ptr(rowptr), _ptr(col), _ptr(cnt), _ptr(v64), _ptr(v32), cap,
+                              _ptr(ws), ws.numel(), _stream(stream, dev))
+    _check("pp_export_csr", st)
+    return rowptr, col, cnt, v64, v32
 
 
 def pagerank(graph, r0, iters=20, c=0.85, dtype="fp32", out=None, want_l1=False, workspace=None, stream=None):

@@ -9,7 +9,9 @@ stored tuning for this GPU applied) and then waits for them.  Compared:
 
 - Kernel 1: the sorted (u, v) bit for bit (SHA-256 of both arrays);
 - Kernel 2: nnz0, nnz, max(d_in), its lowest column, the tie count, the
-  supernodes removed, d_in and d_out bit for bit;
+  supernodes removed, d_in and d_out bit for bit, and the filtered A as
+  exported rows (pp_export_csr): row pointers equal, columns, counts and
+  binary64 values through SHA-256;
 - Kernel 3 after 20 iterations: binary64 within L1 1e-12 of the oracle's r,
   binary32 within L1 1e-6 and max relative 1e-4, the bfloat16-stored
   vector within L1 2e-2 (reported).  Errors are relative to norm(r, 1).
@@ -61,6 +63,12 @@ def gpu_and_oracle(request):
     got = {"us_sha": _sha(us), "vs_sha": _sha(vs), "info": g.info_dict(),
            "d_in": host_u32(g.d_in)[:N].copy(), "d_out": host_u32(g.d_out)[:N].copy()}
     del us, vs
+    # Kernel 2's A as vertex-order rows (pp_export_csr)
+    nnz = got["info"]["nnz"]
+    rowptr, col, cnt, v64, _ = pp.export_csr(g, cap=nnz, workspace=ws)
+    got.update(rowptr=rowptr.cpu().numpy(), col_sha=_sha(col[:nnz]), cnt_sha=_sha(cnt[:nnz]),
+               val_sha=_sha(v64[:nnz]))
+    del rowptr, col, cnt, v64
     r0 = torch.from_numpy(kernel0.r0_host(N, SEED)).to(dev)
     for dtype in ("fp64", "fp32", "bf16"):
         got[dtype] = pp.pagerank(g, r0, ITERS, C, dtype, workspace=ws).cpu().numpy()
@@ -81,6 +89,10 @@ def test_k1_k2_bit_exact(gpu_and_oracle):
         assert info[k] == want[k], (k, info[k], want[k])
     np.testing.assert_array_equal(got["d_in"], want["d_in"])
     np.testing.assert_array_equal(got["d_out"], want["d_out"])
+    # the exported rows: pointers equal, columns, counts and binary64 values through SHA-256
+    np.testing.assert_array_equal(got["rowptr"], want["rowptr"].astype(np.int64))
+    for k in ("col_sha", "cnt_sha", "val_sha"):
+        assert got[k] == want[k], k
 
 
 def test_k3_within_tolerance(gpu_and_oracle, record_property):
