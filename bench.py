@@ -149,7 +149,7 @@ def job_rate(units_per_rank, world, ms):
 def k3_bytes_per_iter(nnz, N, dtype):
     """Algorithmic bytes of one Kernel 3 iteration: packed entries, column ends,
     one read of each gathered x, 1/d_out, the new x."""
-    xs = {"fp64": 8, "fp32": 4, "bf16": 2}[dtype]
+    xs = {"fp64": 8, "fp32": 4, "bf16": 2, "fp16": 2}[dtype]
     inv = 8 if dtype == "fp64" else 4
     return 4 * nnz + 4 * N + xs * N + inv * N + xs * N
 
@@ -274,10 +274,16 @@ def run_ours(args):
     k3_64 = time_k3("fp64", r64, iters)
     r_bf = torch.empty(N, dtype=torch.float32, device=dev)
     k3_bf = time_k3("bf16", r_bf, iters)
+    r_h = torch.empty(N, dtype=torch.float32, device=dev)
+    k3_h = time_k3("fp16", r_h, iters)
     # the iteration kernel alone: the stage minus its set-up (the same call with 0 iterations)
     r_tmp = torch.empty(N, dtype=torch.float64 if args.dtype == "fp64" else torch.float32, device=dev)
     k3_setup = time_k3(args.dtype, r_tmp, 0)
     del r_tmp
+
+    # the gather ceiling of an iteration on this graph: its nnz packed entries
+    # streamed and x gathered with nothing else done (pp_gather_probe)
+    gather_ms = time_gather_probe(g, nnz_of(g), dev)
 
     def errors(r):
         d = (r.double() - r64).abs()
@@ -285,7 +291,8 @@ def run_ours(args):
 
     l1_fp32, maxrel_fp32 = errors(r_out)
     l1_bf, maxrel_bf = errors(r_bf)
-    ranks_host = {"fp64": r64.cpu().numpy(), args.dtype: r_out.cpu().numpy(), "bf16": r_bf.cpu().numpy()}
+    ranks_host = {"fp64": r64.cpu().numpy(), args.dtype: r_out.cpu().numpy(), "bf16": r_bf.cpu().numpy(),
+                  "fp16": r_h.cpu().numpy()}
 
     # Kernel 3 variants on the same graph (pp_pagerank_ex): the dangling-node
     # term (20 iterations), and with the convergence test as well
@@ -394,12 +401,18 @@ def run_ours(args):
         kname, launches_per_stage = "k3 iterate_kernel (warp-tiled, degree-bucketed pull SpMV)", iters
         achieved = b3_iter / (iter_ms * 1e-3) / 1e9
         per_launch = {"bytes": b3_iter, "ms": iter_ms,
-                      "how": "(K3 stage time - same call with 0 iterations) / iterations, CUDA events"}
+                      "how": "(K3 stage time - same call with 0 iterations) / iterations, CUDA events; bytes: "
+                             "4 nnz (packed entries) + 4 N (column ends) + N (x gathered once, 1/d_out, x written) "
+                             "at the stored widths; r itself is written only in the last iteration, so the "
+                             "per-iteration r write of the survey's count is left out"}
     else:
         kname = "k1 onesweep pass_kernel (8-bit LSD pass)" if dom == "k1_sort" else "k2 stage"
         launches_per_stage = P if dom == "k1_sort" else 1
         achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
         per_launch = {"bytes": dom_bytes, "ms": dom_ms, "how": "whole stage, CUDA events"}
+    gather_ceiling = {"ms": gather_ms, "gathers": nnz, "kernel": "pp_gather_probe (nnz packed entries streamed, x "
+                      "gathered through L1, 8 loads in flight per thread, nothing else)",
+                      "iteration_frac_of_ceiling": gather_ms / iter_ms}
     tr = TRAFFIC.get(dom)
     traffic = None
     if tr and tr.get("sha") == _sha(tr["source"]) and (tr.get("dtype"), tr.get("scale")) == (args.dtype, scale):
@@ -431,6 +444,8 @@ def run_ours(args):
                                  "gbs": k3_bytes_per_iter(nnz, N, "fp64") * iters / k3_64 / 1e6},
             "k3_pagerank_bf16": {"ms": k3_bf, "edges_per_s": iters * M / (k3_bf * 1e-3),
                                  "gbs": k3_bytes_per_iter(nnz, N, "bf16") * iters / k3_bf / 1e6},
+            "k3_pagerank_fp16": {"ms": k3_h, "edges_per_s": iters * M / (k3_h * 1e-3),
+                                 "gbs": k3_bytes_per_iter(nnz, N, "fp16") * iters / k3_h / 1e6},
             "k3_iteration": {"ms": iter_ms, "setup_ms": k3_setup},
         },
         "k3_variants": variants,
@@ -440,7 +455,7 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": kname, "stage": dom, "launches_per_step": launches_per_stage,
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "per_launch": per_launch,
-                     "algorithmic_bytes_per_step": dom_bytes},
+                     "algorithmic_bytes_per_step": dom_bytes, "gather_ceiling": gather_ceiling},
         "e2e": {"value": job_rate(M, world, e2e_ms), "unit": "edges/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": 8 * M + 8 * N, "d2h_bytes_per_step": 4 * N + 8 * pp.INFO_LEN},
         "gpu_launches": launches,
@@ -458,6 +473,32 @@ def run_ours(args):
         print(json.dumps(out))
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def nnz_of(g):
+    return g.info_dict()["nnz"]
+
+
+def time_gather_probe(g, n, dev, reps=5):
+    """Best of `reps` CUDA-event timings (ms) of pp_gather_probe over the
+    graph's first n packed entries, x a random binary32 vector."""
+    import torch
+
+    import paper_1603_01876_gb300 as pp
+
+    x = torch.rand(g.N, device=dev)
+    out = torch.zeros(1, device=dev)
+    pp.gather_probe(g, x, out, n)
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record()
+        pp.gather_probe(g, x, out, n)
+        e[1].record()
+        torch.cuda.synchronize()
+        best = min(best, e[0].elapsed_time(e[1]))
+    return best
 
 
 def accuracy_vs_oracle(run, ranks, info, timeout=3600):
@@ -523,8 +564,10 @@ def run_k3_only(args):
     torch.cuda.synchronize()
     setup_ms = e[0].elapsed_time(e[1]) / args.steps
     b = k3_bytes_per_iter(info["nnz"], N, args.dtype) * iters
+    gather_ms = time_gather_probe(g, info["nnz"], dev)
     print(json.dumps({"stage": "k3", "scale": scale, "dtype": args.dtype, "tune": args.tune, "tuned": args.tuned,
                       "ms": ms, "setup_ms": setup_ms, "iter_ms": (ms - setup_ms) / iters, "nnz": info["nnz"],
+                      "gather_ceiling_ms": gather_ms, "iteration_frac_of_gather_ceiling": gather_ms / ((ms - setup_ms) / iters),
                       "edges_per_s": iters * M / (ms * 1e-3), "gbs": b / ms / 1e6,
                       "device_error": pp.last_device_error()}))
 
@@ -559,6 +602,30 @@ def run_batched(dev, steps=3, warmup=1, nrhs=32, n_graphs=64, lo=12, hi=18):
     e[1].record()
     torch.cuda.synchronize()
     ms_stream = e[0].elapsed_time(e[1]) / steps
+    # the set-up alone (0 iterations), for the iteration kernel's roofline
+    out0 = torch.empty_like(out)
+    pp.pagerank_batched(graphs, r0d, nrhs, 0, DAMPING, out=out0)
+    torch.cuda.synchronize()
+    e[0].record()
+    for _ in range(steps):
+        pp.pagerank_batched(graphs, r0d, nrhs, 0, DAMPING, out=out0)
+    e[1].record()
+    torch.cuda.synchronize()
+    ms_setup = e[0].elapsed_time(e[1]) / steps
+    del out0
+    nnzs = [nnz_of(gr) for gr in graphs]
+    # per iteration: packed entries, column ends, 1/d_out, and the nrhs-wide rows
+    # of X gathered once and written once, binary32
+    b_iter = sum(4 * z + 4 * (gr.N + 1) + 4 * gr.N + 2 * 4 * nrhs * gr.N for z, gr in zip(nnzs, graphs))
+    iter_ms = (ms_stream - ms_setup) / ITERS
+    peak, peak_kind = _peaks()
+    roof = {"bound": "hbm", "kernel": "k3b iterate_vec_kernel (one launch per iteration over all graphs)",
+            "achieved": b_iter / (iter_ms * 1e-3) / 1e9, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+            "frac": b_iter / (iter_ms * 1e-3) / 1e9 / peak,
+            "per_launch": {"bytes": b_iter, "ms": iter_ms,
+                           "how": "(stage time with stream launches - same call with 0 iterations) / iterations; "
+                                  "bytes: 4 nnz + 8 N + 8 nrhs N per graph (entries, column ends, 1/d_out, the "
+                                  "nrhs-wide rows gathered once and written once)"}}
     # the stage captured once as a CUDA graph and replayed (the headline batched number)
     ex = pp.BatchedExec(graphs, r0d, nrhs, ITERS, DAMPING, out=out)
     for _ in range(warmup):
@@ -595,7 +662,7 @@ def run_batched(dev, steps=3, warmup=1, nrhs=32, n_graphs=64, lo=12, hi=18):
             "edges_per_s": ITERS * edges * nrhs / (ms_b * 1e-3),
             "sequential_fp64_ms": ms_s, "sequential_fp64_edges_per_s": ITERS * edges * nrhs / (ms_s * 1e-3),
             "speedup_vs_sequential_fp64": ms_s / ms_b, "max_l1_err_vs_fp64": l1,
-            "max_rel_err_vs_fp64": float((d[nz] / ref[nz].abs()).max()),
+            "max_rel_err_vs_fp64": float((d[nz] / ref[nz].abs()).max()), "roofline": roof,
             "device_error": pp.last_device_error()}
 
 
@@ -673,7 +740,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--scale", type=int, default=SCALE)
-    ap.add_argument("--dtype", choices=["fp32", "fp64", "bf16"], default="fp32")
+    ap.add_argument("--dtype", choices=["fp32", "fp64", "bf16", "fp16"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-oracle", action="store_true",
                     help="skip the errors against the oracle run on the whole graph (a few minutes of one host core)")

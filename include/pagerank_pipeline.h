@@ -49,7 +49,9 @@ typedef enum {
 typedef enum {
     PP_FP64 = 0,          /* stored and accumulated in binary64 */
     PP_FP32 = 1,          /* stored and accumulated in binary32 */
-    PP_BF16_FP32ACC = 2   /* the gathered vector stored in bfloat16, sums in binary32 */
+    PP_BF16_FP32ACC = 2,  /* the gathered vector stored in bfloat16, sums in binary32 */
+    PP_FP16_FP32ACC = 3   /* the gathered vector stored in binary16 (scaled by a power of
+                             two into its range), sums in binary32 */
 } pp_dtype;
 
 /* Which columns the supernode statement A(:, d_in == max(d_in)) = 0 zeroes. */
@@ -336,6 +338,18 @@ pp_status pp_pipeline_host(const uint32_t *u_host, const uint32_t *v_host, uint6
                            const double *r0_host, uint32_t iters, double c, pp_dtype dtype,
                            pp_supernode_rule rule, void *r_out_host, uint64_t *info_host,
                            void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * Measurement aid (no counterpart in the paper): the gather rate that bounds
+ * a Kernel 3 iteration.  Reads rowc[0 .. n) once (Kernel 2's packed entries:
+ * a row position in the low `scale` bits) and, for each, gathers
+ * x[rowc[e] mod 2^scale] (x: device float[2^scale]) with nothing else to do
+ * per entry; the sum of the gathered values is added to *out (device float,
+ * caller-initialised).  Timing this call on a graph's first nnz entries gives
+ * the time an iteration over those entries cannot beat with these loads.
+ */
+pp_status pp_gather_probe(const uint32_t *rowc, uint64_t n, uint32_t scale, const float *x, float *out,
+                          void *stream);
 
 /* Synchronise `stream`, then return and clear the device error word (a
  * PP_DEV_* bit set) of the current device in *code.  Returns PP_ERR_DEVICE if

@@ -22,7 +22,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpp.so")
 
 PP_OK, PP_ERR_INVALID_ARG, PP_ERR_WORKSPACE, PP_ERR_CUDA, PP_ERR_DEVICE = range(5)
-DTYPES = {"fp64": 0, "fp32": 1, "bf16": 2}
+DTYPES = {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3}
 RULES = {"lowest": 0, "all_ties": 1}
 INFO = {"nnz0": 0, "nnz": 1, "dmax": 2, "vmax": 3, "ties": 4, "novf": 5, "supernodes": 6}
 INFO_LEN = 8
@@ -85,6 +85,7 @@ def _lib():
             "pp_export_csr_workspace": [u64, u32, sz],
             "pp_export_csr": [ctypes.POINTER(CGraph), vp, vp, vp, vp, vp, u64, vp, ctypes.c_size_t, vp],
             "pp_exec_destroy": [vp],
+            "pp_gather_probe": [vp, u64, u32, vp, vp, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -275,6 +276,15 @@ def pagerank(graph, r0, iters=20, c=0.85, dtype="fp32", out=None, want_l1=False,
                             ws.numel(), _stream(stream, dev))
     _check("pp_pagerank", st)
     return (out, l1) if want_l1 else out
+
+
+def gather_probe(graph, x, out, n=None, stream=None):
+    """Gathers x at the row positions of the graph's first n packed entries
+    (pp_gather_probe, a measurement aid); adds their sum to out[0]."""
+    n = graph.info_dict()["nnz"] if n is None else n
+    _check("pp_gather_probe", _lib().pp_gather_probe(_ptr(graph.rowc), n, graph.scale, _ptr(x), _ptr(out),
+                                                     _stream(stream, x.device)))
+    return out
 
 
 BATCH_MAX_GRAPHS, BATCH_MAX_RHS = 128, 32

@@ -40,6 +40,7 @@
 // instructions, rounded once per column), which keeps the work off GB300's
 // narrow FP64 pipe.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <atomic>
@@ -85,6 +86,7 @@ inline uint32_t win_bits(uint32_t scale) {
 
 __device__ __forceinline__ float to_acc(float x) { return x; }
 __device__ __forceinline__ float to_acc(__nv_bfloat16 x) { return __bfloat162float(x); }
+__device__ __forceinline__ float to_acc(__half x) { return __half2float(x); }
 __device__ __forceinline__ double to_acc(double x) { return x; }
 template <typename TS>
 __device__ __forceinline__ TS from_acc(float x);
@@ -92,6 +94,18 @@ template <>
 __device__ __forceinline__ float from_acc<float>(float x) { return x; }
 template <>
 __device__ __forceinline__ __nv_bfloat16 from_acc<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+template <>
+__device__ __forceinline__ __half from_acc<__half>(float x) { return __float2half_rn(x); }
+
+// binary16 keeps 5 exponent bits: the stored vector is x * 2^k (see xscale)
+template <typename TS>
+struct Scaled {
+    static constexpr bool value = false;
+};
+template <>
+struct Scaled<__half> {
+    static constexpr bool value = true;
+};
 template <typename TS>
 __device__ __forceinline__ TS from_acc(double x) { return x; }
 
@@ -127,6 +141,11 @@ struct Args {
     double *ipart;            // [SETUP_BLOCKS]
     Ctl *ctl;
     double c;
+    // The stored vector is x * xscale (a power of two): 2^min(scale - 9, 15)
+    // for binary16, whose range (6e-8 .. 65504) would lose the small x = r /
+    // d_out of a large graph (r is about 1/N); every r <= sum(r) <= 1, so the
+    // stored values stay below 2^15.  1 for the other precisions.
+    float xscale;
     uint32_t shortmax;    // columns longer than this are cut into chunks
     uint32_t chunk;       // entries of a long column per work item
     // variants (pp_pagerank_ex); zero / null for the plain iteration
@@ -434,7 +453,7 @@ __global__ void __launch_bounds__(256) normalize_kernel(Args a, const double *r0
             const TA r = (TA)(q[k] * rnorm);
             fx_add(acc, r, 1);
             invp[p] = iv[k];
-            x0[p] = from_acc<TS>(r * iv[k]);
+            x0[p] = Scaled<TS>::value ? from_acc<TS>(r * iv[k] * (TA)a.xscale) : from_acc<TS>(r * iv[k]);
             if (a.iters == 0) r_out[v[k]] = (TO)r;
             if (rb0) rb0[p] = r;
             if ((a.flags & PP_K3_DANGLING) && iv[k] == TA(0)) fx_add(dm, r, 1);
@@ -463,6 +482,10 @@ __device__ __forceinline__ __nv_bfloat16 ld_x(const __nv_bfloat16 *p) {
 __device__ __forceinline__ void st_x(float *p, float v) { *p = v; }
 __device__ __forceinline__ void st_x(double *p, double v) { *p = v; }
 __device__ __forceinline__ void st_x(__nv_bfloat16 *p, __nv_bfloat16 v) { *p = v; }
+__device__ __forceinline__ __half ld_x(const __half *p) {
+    return __ushort_as_half(__ldg(reinterpret_cast<const unsigned short *>(p)));
+}
+__device__ __forceinline__ void st_x(__half *p, __half v) { *p = v; }
 __device__ __forceinline__ uint32_t ld_once(const uint32_t *p) {
     uint32_t v;
     asm volatile("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(v) : "l"(p));
@@ -489,7 +512,8 @@ struct Epilogue {
     const TA *inv;
     TS *x_out;
     TO *r_out;
-    TA cc, tele;
+    TA cc, tele;  // cc = c / xscale: the column sums are of the stored (scaled) vector
+    TA xscale;
     int E;
     const uint32_t *iperm;
     const TA *rb_in;
@@ -499,7 +523,7 @@ struct Epilogue {
     __device__ __forceinline__ void operator()(uint32_t col, TA y, TA inv_col, Sums &acc) const {
         const TA r = cc * y + tele;
         if (LAST && !EXT) r_out[__ldg(iperm + col)] = (TO)r;
-        st_x(x_out + col, from_acc<TS>(r * inv_col));
+        st_x(x_out + col, Scaled<TS>::value ? from_acc<TS>(r * inv_col * xscale) : from_acc<TS>(r * inv_col));
         fx_add(acc.s, r, E);
         if (EXT) {
             if (flags & PP_K3_CONVERGE) {
@@ -535,7 +559,7 @@ __device__ __forceinline__ TA warp_sum(TA y) {
     return y;  // in lane 0
 }
 
-// A column sum.  Binary32 (and bfloat16 x): float additions in a fixed
+// A column sum.  Binary32 (and bfloat16 or binary16 x): float additions in a fixed
 // order.  Binary64: exact 128-bit fixed point scaled by the bound 2^E on
 // sum(r) (every term cf * x(u) <= r(u) <= sum(r)), added with integer
 // instructions and rounded once, because GB300's FP64 pipe is far narrower
@@ -590,8 +614,9 @@ __global__ void __launch_bounds__(THREADS, MINB)
     const Epilogue<TS, TA, TO, LAST, EXT> epi{inv,
                                               x_out,
                                               r_out,
-                                              (TA)a.c,
+                                              (TA)(a.c / (double)a.xscale),
                                               (TA)(((1.0 - a.c) / (double)a.N) * S + tele_extra),
+                                              (TA)a.xscale,
                                               E,
                                               a.iperm,
                                               rb_in,
@@ -804,7 +829,7 @@ inline Layout layout(void *ws, uint64_t M, uint32_t scale, uint32_t iters, pp_dt
     // chunks: at most one per long column plus nnz/chunk, and a long column has
     // more than SHORTMAX_MIN of the nnz <= M entries
     const uint64_t max_items = std::min<uint64_t>(N, M / (SHORTMAX_MIN + 1)) + M / CHUNK_MIN + 1;
-    const size_t xs = dt == PP_FP64 ? 8 : (dt == PP_FP32 ? 4 : 2);
+    const size_t xs = dt == PP_FP64 ? 8 : (dt == PP_FP32 ? 4 : 2);  // bfloat16, binary16: 2
     L.x[0] = c.take<char>(N * xs);
     L.x[1] = c.take<char>(N * xs);
     L.invp = c.take<char>(N * (dt == PP_FP64 ? 8 : 4));
@@ -940,6 +965,7 @@ pp_status run_unroll(const pp_graph *g, const double *r0, uint32_t iters, double
     while ((g->M / 2 + chunk - 1) / chunk >= (1ull << (32 - NENT_BITS))) chunk <<= 1;
     a.shortmax = shortmax;
     a.chunk = chunk;
+    a.xscale = Scaled<TS>::value ? (float)(1u << std::min<int>(std::max<int>((int)g->scale - 9, 0), 15)) : 1.0f;
     a.flags = EXT ? var.flags : 0u;
     a.tol = var.tol;
     a.dmass = L.dmass;
@@ -1023,14 +1049,54 @@ pp_status run_ext(const pp_graph *g, const double *r0, uint32_t iters, double c,
     return run_unroll<TS, TA, TO, sizeof(TA) == 8 ? 4 : 8, 4, true>(g, r0, iters, c, dt, r_out, r_l1, L, s, var);
 }
 
+// The gather rate that bounds an iteration: the packed entries streamed once
+// (coalesced, bypassing L1) and x gathered through L1 for each, with eight
+// independent loads in flight per thread and nothing else; every thread's
+// sum goes to *out (one atomic per warp) so that no load is dead.
+constexpr int PROBE_UNROLL = 8;
+__global__ void __launch_bounds__(256, 8) gather_probe_kernel(const uint32_t *rowc, uint64_t n, uint32_t umask,
+                                                              const float *x, float *out) {
+    float acc = 0.f;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t b = tid; b < n; b += PROBE_UNROLL * stride) {
+        uint32_t w[PROBE_UNROLL];
+        float xv[PROBE_UNROLL];
+#pragma unroll
+        for (int m = 0; m < PROBE_UNROLL; ++m) w[m] = b + m * stride < n ? ld_once(rowc + b + m * stride) : 0u;
+#pragma unroll
+        for (int m = 0; m < PROBE_UNROLL; ++m) xv[m] = b + m * stride < n ? __ldg(x + (w[m] & umask)) : 0.f;
+#pragma unroll
+        for (int m = 0; m < PROBE_UNROLL; ++m) acc += xv[m];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
 }  // namespace k3
 }  // namespace pp
 
 using namespace pp;
 
+extern "C" pp_status pp_gather_probe(const uint32_t *rowc, uint64_t n, uint32_t scale, const float *x, float *out,
+                                     void *stream) {
+    if (scale < 1 || scale > 27 || (n && (!rowc || !x)) || !out) return PP_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    static PerDevice occ_dev;
+    const int occ = (int)occ_dev.get([] {
+        k3::set_smem(k3::gather_probe_kernel, 8, 0);
+        return (int64_t)k3::occupancy(k3::gather_probe_kernel, 256, 0);
+    });
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)sm_count() * occ,
+                                                                             ceil_div(n, 256)));
+    k3::gather_probe_kernel<<<grid, 256, 0, s>>>(rowc, n, (1u << scale) - 1u, x, out);
+    count_launch();
+    return launch_status();
+}
+
 extern "C" pp_status pp_pagerank_workspace(uint64_t M, uint32_t scale, uint32_t iters, pp_dtype dt,
                                            size_t *bytes) {
-    if (!bytes || scale < 1 || scale > 27 || M > (1ull << 31) || (int)dt < 0 || (int)dt > 2)
+    if (!bytes || scale < 1 || scale > 27 || M > (1ull << 31) || (int)dt < 0 || (int)dt > 3)
         return PP_ERR_INVALID_ARG;
     *bytes = k3::layout(nullptr, M, scale, iters, dt).bytes;
     return PP_OK;
@@ -1038,7 +1104,7 @@ extern "C" pp_status pp_pagerank_workspace(uint64_t M, uint32_t scale, uint32_t 
 
 extern "C" pp_status pp_pagerank(const pp_graph *g, const double *r0, uint32_t iters, double c, pp_dtype dt,
                                  void *r_out, double *r_l1, void *ws, size_t ws_bytes, void *stream) {
-    if (!g || !r0 || !r_out || (int)dt < 0 || (int)dt > 2) return PP_ERR_INVALID_ARG;
+    if (!g || !r0 || !r_out || (int)dt < 0 || (int)dt > 3) return PP_ERR_INVALID_ARG;
     if (g->scale < 1 || g->scale > 27 || g->M > (1ull << 31) || !(c >= 0.0 && c <= 1.0)) return PP_ERR_INVALID_ARG;
     if (!g->colptr || !g->rowc || !g->ovf_key || !g->ovf_cnt || !g->info || !g->perm || !g->iperm)
         return PP_ERR_INVALID_ARG;
@@ -1052,15 +1118,17 @@ extern "C" pp_status pp_pagerank(const pp_graph *g, const double *r0, uint32_t i
             return k3::run<double, double, double>(g, r0, iters, c, dt, static_cast<double *>(r_out), r_l1, L, s);
         case PP_FP32:
             return k3::run<float, float, float>(g, r0, iters, c, dt, static_cast<float *>(r_out), r_l1, L, s);
-        default:
+        case PP_BF16_FP32ACC:
             return k3::run<__nv_bfloat16, float, float>(g, r0, iters, c, dt, static_cast<float *>(r_out), r_l1, L,
                                                         s);
+        default:
+            return k3::run<__half, float, float>(g, r0, iters, c, dt, static_cast<float *>(r_out), r_l1, L, s);
     }
 }
 
 extern "C" pp_status pp_pagerank_ex_workspace(uint64_t M, uint32_t scale, uint32_t iters, pp_dtype dt,
                                               size_t *bytes) {
-    if (!bytes || scale < 1 || scale > 27 || M > (1ull << 31) || (int)dt < 0 || (int)dt > 2)
+    if (!bytes || scale < 1 || scale > 27 || M > (1ull << 31) || (int)dt < 0 || (int)dt > 3)
         return PP_ERR_INVALID_ARG;
     *bytes = k3::layout(nullptr, M, scale, iters, dt, true).bytes;
     return PP_OK;
@@ -1069,7 +1137,7 @@ extern "C" pp_status pp_pagerank_ex_workspace(uint64_t M, uint32_t scale, uint32
 extern "C" pp_status pp_pagerank_ex(const pp_graph *g, const double *r0, uint32_t iters, double c, pp_dtype dt,
                                     uint32_t flags, double tol, void *r_out, double *r_l1, uint32_t *iters_done,
                                     void *ws, size_t ws_bytes, void *stream) {
-    if (!g || !r0 || !r_out || (int)dt < 0 || (int)dt > 2) return PP_ERR_INVALID_ARG;
+    if (!g || !r0 || !r_out || (int)dt < 0 || (int)dt > 3) return PP_ERR_INVALID_ARG;
     if (g->scale < 1 || g->scale > 27 || g->M > (1ull << 31) || !(c >= 0.0 && c <= 1.0)) return PP_ERR_INVALID_ARG;
     if (flags & ~(uint32_t)(PP_K3_DANGLING | PP_K3_CONVERGE)) return PP_ERR_INVALID_ARG;
     if ((flags & PP_K3_CONVERGE) && !(tol > 0.0)) return PP_ERR_INVALID_ARG;
@@ -1087,8 +1155,11 @@ extern "C" pp_status pp_pagerank_ex(const pp_graph *g, const double *r0, uint32_
                                                        var);
         case PP_FP32:
             return k3::run_ext<float, float, float>(g, r0, iters, c, dt, static_cast<float *>(r_out), r_l1, L, s, var);
-        default:
+        case PP_BF16_FP32ACC:
             return k3::run_ext<__nv_bfloat16, float, float>(g, r0, iters, c, dt, static_cast<float *>(r_out), r_l1, L,
                                                             s, var);
+        default:
+            return k3::run_ext<__half, float, float>(g, r0, iters, c, dt, static_cast<float *>(r_out), r_l1, L, s,
+                                                     var);
     }
 }

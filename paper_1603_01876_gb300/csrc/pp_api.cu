@@ -147,7 +147,7 @@ PipeLayout pipe_layout(void *ws, uint64_t M, uint32_t scale, uint32_t iters, pp_
 
 extern "C" pp_status pp_pipeline_workspace(uint64_t M, uint32_t scale, uint32_t iters, pp_dtype dt,
                                            size_t *bytes) {
-    if (!bytes || scale < 1 || scale > 27 || M > (1ull << 31) || (int)dt < 0 || (int)dt > 2)
+    if (!bytes || scale < 1 || scale > 27 || M > (1ull << 31) || (int)dt < 0 || (int)dt > 3)
         return PP_ERR_INVALID_ARG;
     *bytes = pipe_layout(nullptr, M, scale, iters, dt).bytes;
     return PP_OK;
@@ -157,7 +157,7 @@ extern "C" pp_status pp_pipeline_host(const uint32_t *u_host, const uint32_t *v_
                                       uint32_t scale, const double *r0_host, uint32_t iters, double c,
                                       pp_dtype dt, pp_supernode_rule rule, void *r_out_host,
                                       uint64_t *info_host, void *ws, size_t ws_bytes, void *stream) {
-    if (scale < 1 || scale > 27 || M > (1ull << 31) || (int)dt < 0 || (int)dt > 2) return PP_ERR_INVALID_ARG;
+    if (scale < 1 || scale > 27 || M > (1ull << 31) || (int)dt < 0 || (int)dt > 3) return PP_ERR_INVALID_ARG;
     if ((M && (!u_host || !v_host)) || !r0_host || !r_out_host) return PP_ERR_INVALID_ARG;
     const PipeLayout need = pipe_layout(nullptr, M, scale, iters, dt);
     pp_status st = check_ws(ws, ws_bytes, need.bytes);

@@ -13,8 +13,8 @@ stored tuning for this GPU applied) and then waits for them.  Compared:
   exported rows (pp_export_csr): row pointers equal, columns, counts and
   binary64 values through SHA-256;
 - Kernel 3 after 20 iterations: binary64 within L1 1e-12 of the oracle's r,
-  binary32 within L1 1e-6 and max relative 1e-4, the bfloat16-stored
-  vector within L1 2e-2 (reported).  Errors are relative to norm(r, 1).
+  binary32 within L1 1e-6 and max relative 1e-4, the bfloat16-stored and
+  binary16-stored vectors within L1 2e-2 and 2e-3 (reported).  Errors are relative to norm(r, 1).
 """
 import json
 import os
@@ -70,7 +70,7 @@ def gpu_and_oracle(request):
                val_sha=_sha(v64[:nnz]))
     del rowptr, col, cnt, v64
     r0 = torch.from_numpy(kernel0.r0_host(N, SEED)).to(dev)
-    for dtype in ("fp64", "fp32", "bf16"):
+    for dtype in ("fp64", "fp32", "bf16", "fp16"):
         got[dtype] = pp.pagerank(g, r0, ITERS, C, dtype, workspace=ws).cpu().numpy()
     assert pp.last_device_error() == 0
     del g, ws
@@ -98,9 +98,10 @@ def test_k1_k2_bit_exact(gpu_and_oracle):
 def test_k3_within_tolerance(gpu_and_oracle, record_property):
     scale, got, want, tuned = gpu_and_oracle
     r = want["r"]
-    e = {d: rank_errors(got[d], r) for d in ("fp64", "fp32", "bf16")}
+    e = {d: rank_errors(got[d], r) for d in ("fp64", "fp32", "bf16", "fp16")}
     record_property("k3_errors_vs_oracle", json.dumps(e))
     print("scale %d, errors against the oracle: %s (tuning %s)" % (scale, json.dumps(e), tuned))
     assert e["fp64"]["l1"] <= 1e-12, e["fp64"]
     assert e["fp32"]["l1"] <= 1e-6 and e["fp32"]["max_rel"] <= 1e-4, e["fp32"]
     assert e["bf16"]["l1"] <= 2e-2, e["bf16"]
+    assert e["fp16"]["l1"] <= 2e-3, e["fp16"]
