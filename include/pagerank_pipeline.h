@@ -195,6 +195,38 @@ pp_status pp_build_filter_normalize(const uint32_t *u_sorted, const uint32_t *v_
                                     void *workspace, size_t workspace_bytes, void *stream);
 
 /*
+ * Kernels 1 and 2 for a batch of graphs of uneven scale (the batched
+ * configuration), each stage one set of launches over every graph at once.
+ * The graphs are laid side by side in one union vertex space (graph g's
+ * vertex u is union vertex N_0 + ... + N_(g-1) + u), sorted and filtered
+ * together, and split again; every output equals that of the single-graph
+ * call on the same graph (pp_sort_edges, pp_build_filter_normalize).
+ *   n_graphs     1 .. PP_BATCH_MAX_GRAPHS; sum of 2^scale[g] <= 2^27 and of
+ *                M[g] <= 2^31.
+ *   u, v         host arrays of n_graphs device pointers (graph g's M[g] ids).
+ *   u_out, v_out host arrays of device pointers, M[g] each, not overlapping
+ *                the inputs: graph g's edges sorted by (u, v).
+ *   gs           host array of n_graphs graphs (device arrays inside, sized
+ *                by pp_graph_lengths(gs[g].M, gs[g].scale)); graph g is built
+ *                from u_sorted[g], v_sorted[g] (gs[g].M edges, ids below
+ *                2^gs[g].scale).
+ * An id >= N of its graph sets PP_DEV_RANGE; the outputs are then
+ * unspecified.  Workspace from the matching *_workspace query.  The batch
+ * tables travel as kernel parameters, so the calls can be stream-captured.
+ */
+pp_status pp_sort_edges_batched_workspace(uint32_t n_graphs, const uint64_t *M, const uint32_t *scale,
+                                          size_t *bytes);
+pp_status pp_sort_edges_batched(uint32_t n_graphs, const uint32_t *const *u, const uint32_t *const *v,
+                                const uint64_t *M, const uint32_t *scale, uint32_t *const *u_out,
+                                uint32_t *const *v_out, void *workspace, size_t workspace_bytes, void *stream);
+pp_status pp_build_filter_normalize_batched_workspace(uint32_t n_graphs, const uint64_t *M, const uint32_t *scale,
+                                                      size_t *bytes);
+pp_status pp_build_filter_normalize_batched(uint32_t n_graphs, const uint32_t *const *u_sorted,
+                                            const uint32_t *const *v_sorted, pp_supernode_rule rule,
+                                            const pp_graph *gs, void *workspace, size_t workspace_bytes,
+                                            void *stream);
+
+/*
  * Kernel 2's filtered matrix A (Sec. IV-C step 4, A(i,:) = A(i,:) ./ d_out(i))
  * in compressed-row form, in vertex order: row u holds the entries of start
  * vertex u with their end vertices ascending.
@@ -293,6 +325,22 @@ typedef struct pp_exec pp_exec;
 pp_status pp_pagerank_batched_capture(const pp_graph *gs, uint32_t n_graphs, const double *r0, uint32_t nrhs,
                                       uint32_t iters, double c, float *r_out, void *workspace,
                                       size_t workspace_bytes, void *stream, pp_exec **exec);
+/*
+ * The whole batched pipeline recorded as one CUDA graph: Kernel 1 on every
+ * graph's edges (u, v into u_sorted, v_sorted), Kernel 2 into gs, Kernel 3
+ * on r0 into r_out (binary32, nrhs start vectors per graph), each stage as
+ * pp_sort_edges_batched, pp_build_filter_normalize_batched and
+ * pp_pagerank_batched would enqueue it.  The three stages run one after the
+ * other in the same workspace (size from pp_pipeline_batched_workspace).
+ * Replay with pp_exec_launch; buffers as for the three calls.
+ */
+pp_status pp_pipeline_batched_workspace(uint32_t n_graphs, const pp_graph *gs, uint32_t nrhs, uint32_t iters,
+                                        size_t *bytes);
+pp_status pp_pipeline_batched_capture(uint32_t n_graphs, const uint32_t *const *u, const uint32_t *const *v,
+                                      uint32_t *const *u_sorted, uint32_t *const *v_sorted, pp_supernode_rule rule,
+                                      const pp_graph *gs, const double *r0, uint32_t nrhs, uint32_t iters,
+                                      double c, float *r_out, void *workspace, size_t workspace_bytes,
+                                      void *stream, pp_exec **exec);
 pp_status pp_exec_launch(pp_exec *exec, void *stream);
 pp_status pp_exec_destroy(pp_exec *exec);
 

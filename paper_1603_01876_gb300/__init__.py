@@ -86,6 +86,13 @@ def _lib():
             "pp_export_csr": [ctypes.POINTER(CGraph), vp, vp, vp, vp, vp, u64, vp, ctypes.c_size_t, vp],
             "pp_exec_destroy": [vp],
             "pp_gather_probe": [vp, u64, u32, vp, vp, vp],
+            "pp_sort_edges_batched_workspace": [u32, vp, vp, sz],
+            "pp_sort_edges_batched": [u32, vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp],
+            "pp_build_filter_normalize_batched_workspace": [u32, vp, vp, sz],
+            "pp_build_filter_normalize_batched": [u32, vp, vp, i32, ctypes.POINTER(CGraph), vp, ctypes.c_size_t, vp],
+            "pp_pipeline_batched_workspace": [u32, ctypes.POINTER(CGraph), u32, u32, sz],
+            "pp_pipeline_batched_capture": [u32, vp, vp, vp, vp, i32, ctypes.POINTER(CGraph), vp, u32, u32, dbl, vp,
+                                            vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -288,6 +295,93 @@ def gather_probe(graph, x, out, n=None, stream=None):
 
 
 BATCH_MAX_GRAPHS, BATCH_MAX_RHS = 128, 32
+
+
+def _ptr_array(tensors):
+    return (ctypes.c_void_p * len(tensors))(*[t.data_ptr() if t is not None else 0 for t in tensors])
+
+
+def sort_edges_batched(us, vs, scales, outs=None, workspace=None, stream=None):
+    """Kernel 1 for a batch of graphs (pp_sort_edges_batched): one sort of all
+    their edges; returns [(u_out, v_out)] per graph."""
+    n = len(us)
+    dev = us[0].device
+    if outs is None:
+        outs = [(torch.empty_like(u), torch.empty_like(v)) for u, v in zip(us, vs)]
+    M = (ctypes.c_uint64 * n)(*[u.numel() for u in us])
+    S = (ctypes.c_uint32 * n)(*scales)
+    need = ctypes.c_size_t(0)
+    _check("pp_sort_edges_batched_workspace", _lib().pp_sort_edges_batched_workspace(n, M, S, ctypes.byref(need)))
+    ws = workspace if workspace is not None and workspace.numel() >= need.value else _workspace(need.value, dev)
+    st = _lib().pp_sort_edges_batched(n, _ptr_array(us), _ptr_array(vs), M, S, _ptr_array([o[0] for o in outs]),
+                                      _ptr_array([o[1] for o in outs]), _ptr(ws), ws.numel(), _stream(stream, dev))
+    _check("pp_sort_edges_batched", st)
+    return outs
+
+
+def build_filter_normalize_batched(sorted_edges, scales, rule="lowest", graphs=None, workspace=None, stream=None):
+    """Kernel 2 for a batch of graphs (pp_build_filter_normalize_batched);
+    sorted_edges: [(us, vs)] per graph; returns a Graph per graph."""
+    n = len(sorted_edges)
+    dev = sorted_edges[0][0].device
+    if graphs is None:
+        graphs = [Graph(u.numel(), s, dev) for (u, _), s in zip(sorted_edges, scales)]
+    arr = (CGraph * n)(*[g.c for g in graphs])
+    M = (ctypes.c_uint64 * n)(*[g.M for g in graphs])
+    S = (ctypes.c_uint32 * n)(*[g.scale for g in graphs])
+    need = ctypes.c_size_t(0)
+    _check("pp_build_filter_normalize_batched_workspace",
+           _lib().pp_build_filter_normalize_batched_workspace(n, M, S, ctypes.byref(need)))
+    ws = workspace if workspace is not None and workspace.numel() >= need.value else _workspace(need.value, dev)
+    st = _lib().pp_build_filter_normalize_batched(n, _ptr_array([e[0] for e in sorted_edges]),
+                                                  _ptr_array([e[1] for e in sorted_edges]), RULES[rule], arr,
+                                                  _ptr(ws), ws.numel(), _stream(stream, dev))
+    _check("pp_build_filter_normalize_batched", st)
+    return graphs
+
+
+class BatchedPipelineExec:
+    """Kernels 1-3 for a batch of graphs recorded as one CUDA graph
+    (pp_pipeline_batched_capture); launch() replays the whole pipeline."""
+
+    def __init__(self, us, vs, scales, r0, nrhs, iters=20, c=0.85, rule="lowest", stream=None):
+        n = len(us)
+        dev = us[0].device
+        self.sorted = [(torch.empty_like(u), torch.empty_like(v)) for u, v in zip(us, vs)]
+        self.graphs = [Graph(u.numel(), s, dev) for u, s in zip(us, scales)]
+        self._arr = (CGraph * n)(*[g.c for g in self.graphs])
+        rows = sum(g.N for g in self.graphs)
+        assert r0.shape == (rows, nrhs) and r0.dtype == torch.float64 and r0.is_contiguous()
+        self.out = torch.empty(rows, nrhs, dtype=torch.float32, device=dev)
+        need = ctypes.c_size_t(0)
+        _check("pp_pipeline_batched_workspace",
+               _lib().pp_pipeline_batched_workspace(n, self._arr, nrhs, iters, ctypes.byref(need)))
+        self.ws = _workspace(need.value, dev)
+        self._keep = (list(us), list(vs), r0)
+        self._dev = dev
+        h = ctypes.c_void_p(None)
+        _check("pp_pipeline_batched_capture",
+               _lib().pp_pipeline_batched_capture(n, _ptr_array(us), _ptr_array(vs),
+                                                  _ptr_array([o[0] for o in self.sorted]),
+                                                  _ptr_array([o[1] for o in self.sorted]), RULES[rule], self._arr,
+                                                  _ptr(r0), nrhs, iters, c, _ptr(self.out), _ptr(self.ws),
+                                                  self.ws.numel(), _stream(stream, dev), ctypes.byref(h)))
+        self._h = h
+
+    def launch(self, stream=None):
+        _check("pp_exec_launch", _lib().pp_exec_launch(self._h, _stream(stream, self._dev)))
+        return self.out
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _lib().pp_exec_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 TSV_MAX_LINE = 22

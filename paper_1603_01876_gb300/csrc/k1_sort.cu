@@ -135,6 +135,187 @@ extern "C" pp_status pp_sort_edges(const uint32_t *u, const uint32_t *v, uint64_
 }
 
 // ---------------------------------------------------------------------------
+// Kernel 1 for a batch of graphs (pp_sort_edges_batched): one sort of every
+// graph's edges at once.  Graph g's vertices get the ids base_g .. base_g +
+// N_g - 1 of a union vertex space (base_g = N_0 + ... + N_(g-1)); its edges
+// become the keys (U << S | V) of that union (S = ceil(log2(sum N_g))), one
+// gather launch over all graphs writes them, the radix passes sort them
+// together, and one unpack launch writes each graph's output.  The union ids
+// of a graph form one range, so sorting by (U, V) leaves every graph's edges
+// in its own segment, ordered by (u, v).  The batch table travels as a
+// kernel parameter (no host-to-device copy), so the call can be captured in
+// a CUDA graph.
+
+namespace pp {
+namespace k1b {
+
+constexpr int MAX_G = PP_BATCH_MAX_GRAPHS;
+constexpr int TILE = 4096;
+
+struct Batch {
+    uint32_t n, S;  // graphs, union scale
+    const uint32_t *u[MAX_G], *v[MAX_G];
+    uint32_t *uo[MAX_G], *vo[MAX_G];
+    uint64_t eoff[MAX_G + 1];   // union index of graph g's first edge
+    uint32_t vbase[MAX_G + 1];  // union id of graph g's vertex 0
+    uint64_t toff[MAX_G + 1];   // first tile of graph g in the gather / unpack grids
+    uint32_t scale[MAX_G];
+};
+
+// graph of tile t: the last g with toff[g] <= t (same for every thread of a block)
+__device__ __forceinline__ uint32_t tile_graph(const Batch &b, uint64_t t) {
+    uint32_t lo = 0, hi = b.n - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (b.toff[mid] <= t)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename KeyT>
+__global__ void __launch_bounds__(256) gather_kernel(Batch b, KeyT *keys) {
+    const uint32_t g = tile_graph(b, blockIdx.x);
+    const uint64_t e0 = (blockIdx.x - b.toff[g]) * (uint64_t)TILE, M = b.eoff[g + 1] - b.eoff[g];
+    const uint32_t base = b.vbase[g], sc = b.scale[g];
+    KeyT *out = keys + b.eoff[g];
+    for (uint64_t i = e0 + threadIdx.x; i < min(M, e0 + TILE); i += blockDim.x) {
+        uint32_t a = __ldg(b.u[g] + i), c = __ldg(b.v[g] + i);
+        if ((a | c) >> sc) {
+            pp_set_error(PP_DEV_RANGE);
+            a &= (1u << sc) - 1u;
+            c &= (1u << sc) - 1u;
+        }
+        out[i] = ((KeyT)(base + a) << b.S) | (KeyT)(base + c);
+    }
+}
+
+template <typename KeyT>
+__global__ void __launch_bounds__(256) unpack_kernel(Batch b, const KeyT *keys) {
+    const uint32_t g = tile_graph(b, blockIdx.x);
+    const uint64_t e0 = (blockIdx.x - b.toff[g]) * (uint64_t)TILE, M = b.eoff[g + 1] - b.eoff[g];
+    const uint32_t base = b.vbase[g];
+    const KeyT *in = keys + b.eoff[g];
+    const KeyT mask = ((KeyT)1 << b.S) - 1;
+    for (uint64_t i = e0 + threadIdx.x; i < min(M, e0 + TILE); i += blockDim.x) {
+        const KeyT k = in[i];
+        b.uo[g][i] = (uint32_t)(k >> b.S) - base;
+        b.vo[g][i] = (uint32_t)(k & mask) - base;
+    }
+}
+
+struct Layout {
+    void *keys[2];
+    os::SortWs sort;
+    size_t bytes;
+};
+
+inline Layout layout(void *ws, uint64_t Mtot, uint32_t S) {
+    Carver c(ws);
+    Layout L;
+    const size_t kb = (2 * S <= 32) ? 4 : 8;
+    const uint64_t cap = Mtot ? Mtot : 1;
+    L.keys[0] = c.take<char>(cap * kb);
+    L.keys[1] = c.take<char>(cap * kb);
+    L.sort = os::carve_sort_ws(c, cap);
+    L.bytes = c.size();
+    return L;
+}
+
+// Union scale and totals of a batch; false if it does not fit the limits.
+inline bool batch_shape(uint32_t n, const uint64_t *M, const uint32_t *scale, uint64_t *Mtot, uint32_t *S) {
+    if (n < 1 || n > (uint32_t)MAX_G || !M || !scale) return false;
+    uint64_t nv = 0, me = 0;
+    for (uint32_t g = 0; g < n; ++g) {
+        if (scale[g] < 1 || scale[g] > 27) return false;
+        nv += 1ull << scale[g];
+        me += M[g];
+    }
+    if (nv > (1ull << 27) || me > (1ull << 31)) return false;
+    uint32_t s = 1;
+    while ((1ull << s) < nv) ++s;
+    *Mtot = me;
+    *S = s;
+    return true;
+}
+
+template <typename KeyT>
+void run(const Batch &b, uint64_t Mtot, uint64_t ntiles_g, const Layout &L, cudaStream_t s) {
+    const int P = (int)ceil_div(2u * b.S, 8u);
+    const size_t word = L.sort.wide ? 8 : 4;
+    KeyT *A = static_cast<KeyT *>(L.keys[0]), *B = static_cast<KeyT *>(L.keys[1]);
+    gather_kernel<KeyT><<<(unsigned)ntiles_g, 256, 0, s>>>(b, A);
+    cudaMemsetAsync(L.sort.hist, 0, os::kCtlBytes, s);
+    const unsigned hgrid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(ceil_div(Mtot, 256 * 8), (uint64_t)sm_count() * 8));
+    os::hist_kernel<KeyT, k1::KeySrc<KeyT>><<<hgrid, 256, 0, s>>>(
+        k1::KeySrc<KeyT>{A}, nullptr, Mtot, P, L.sort.hist, static_cast<uint32_t *>(L.sort.status[0]),
+        ceil_div(Mtot, os::TILE) * os::RADIX * word / 4);
+    count_launch(2);
+    for (int p = 0; p < P; ++p) {
+        KeyT *in = (p & 1) ? B : A;
+        KeyT *out = (p & 1) ? A : B;
+        os::launch_pass<KeyT>(L.sort, p, P, k1::KeySrc<KeyT>{in}, k1::KeyDst<KeyT>{out}, nullptr, Mtot, s);
+    }
+    unpack_kernel<KeyT><<<(unsigned)ntiles_g, 256, 0, s>>>(b, (P & 1) ? B : A);
+    count_launch();
+}
+
+}  // namespace k1b
+}  // namespace pp
+
+extern "C" pp_status pp_sort_edges_batched_workspace(uint32_t n_graphs, const uint64_t *M, const uint32_t *scale,
+                                                     size_t *bytes) {
+    uint64_t Mtot;
+    uint32_t S;
+    if (!bytes || !k1b::batch_shape(n_graphs, M, scale, &Mtot, &S)) return PP_ERR_INVALID_ARG;
+    *bytes = k1b::layout(nullptr, Mtot, S).bytes;
+    return PP_OK;
+}
+
+extern "C" pp_status pp_sort_edges_batched(uint32_t n_graphs, const uint32_t *const *u, const uint32_t *const *v,
+                                           const uint64_t *M, const uint32_t *scale, uint32_t *const *u_out,
+                                           uint32_t *const *v_out, void *ws, size_t ws_bytes, void *stream) {
+    uint64_t Mtot;
+    uint32_t S;
+    if (!k1b::batch_shape(n_graphs, M, scale, &Mtot, &S) || !u || !v || !u_out || !v_out) return PP_ERR_INVALID_ARG;
+    k1b::Batch b;
+    b.n = n_graphs;
+    b.S = S;
+    uint64_t eo = 0, to = 0;
+    uint32_t vb = 0;
+    for (uint32_t g = 0; g < n_graphs; ++g) {
+        if (M[g] && (!u[g] || !v[g] || !u_out[g] || !v_out[g])) return PP_ERR_INVALID_ARG;
+        b.u[g] = u[g];
+        b.v[g] = v[g];
+        b.uo[g] = u_out[g];
+        b.vo[g] = v_out[g];
+        b.scale[g] = scale[g];
+        b.eoff[g] = eo;
+        b.vbase[g] = vb;
+        b.toff[g] = to;
+        eo += M[g];
+        vb += 1u << scale[g];
+        to += ceil_div(M[g], k1b::TILE);
+    }
+    b.eoff[n_graphs] = eo;
+    b.vbase[n_graphs] = vb;
+    b.toff[n_graphs] = to;
+    if (Mtot == 0) return PP_OK;
+    const k1b::Layout need = k1b::layout(nullptr, Mtot, S);
+    pp_status st = check_ws(ws, ws_bytes, need.bytes);
+    if (st != PP_OK) return st;
+    const k1b::Layout L = k1b::layout(ws, Mtot, S);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (2 * S <= 32)
+        k1b::run<uint32_t>(b, Mtot, to, L, s);
+    else
+        k1b::run<uint64_t>(b, Mtot, to, L, s);
+    return launch_status();
+}
+
+// ---------------------------------------------------------------------------
 // Kernel 1 without allocation (pp_sort_edges_static).  Some callers cannot
 // allocate device memory at all: their GPU memory belongs to another
 // allocator (a framework's caching pool, a fixed real-time budget) or

@@ -501,15 +501,68 @@ __global__ void __launch_bounds__(256) dmax_kernel(const unsigned long long *deg
     if ((threadIdx.x & 31) == 0) atomicMax(dmaxkey, best);
 }
 
+constexpr int MAX_G = PP_BATCH_MAX_GRAPHS;
+
+// A batch's union vertex space: graph g owns union ids vbase[g] .. vbase[g+1]-1;
+// ids from vbase[n] on belong to no graph (padding up to a power of two).
+struct VBases {
+    uint32_t n;
+    uint32_t vbase[MAX_G + 1];
+};
+
+// graph owning union id v (n for the padding)
+__device__ __forceinline__ uint32_t graph_of(const VBases &b, uint32_t v) {
+    if (v >= b.vbase[b.n]) return b.n;
+    uint32_t lo = 0, hi = b.n - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (b.vbase[mid] <= v)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// The batch's d_in out; per graph max(d_in) with its lowest vertex (one
+// atomic per graph a thread's 16 consecutive vertices touch).
+__global__ void __launch_bounds__(256) dmax_batched_kernel(const unsigned long long *deg, uint32_t N, VBases vb,
+                                                           uint32_t *d_in, unsigned long long *dmaxkeys) {
+    constexpr int ITEMS = 16;
+    for (uint64_t v0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * ITEMS; v0 < N;
+         v0 += (uint64_t)gridDim.x * blockDim.x * ITEMS) {
+        uint32_t gr = graph_of(vb, (uint32_t)v0);
+        unsigned long long best = 0;
+        for (int j = 0; j < ITEMS && v0 + j < N; ++j) {
+            const uint32_t v = (uint32_t)(v0 + j);
+            const uint32_t d = (uint32_t)deg[v];
+            d_in[v] = d;
+            if (gr < vb.n && v >= vb.vbase[gr + 1]) {
+                atomicMax(&dmaxkeys[gr], best);
+                best = 0;
+                gr = graph_of(vb, v);
+            }
+            const unsigned long long key = ((unsigned long long)d << 32) | (unsigned long long)(~v);
+            best = key > best ? key : best;
+        }
+        if (gr < vb.n) atomicMax(&dmaxkeys[gr], best);
+    }
+}
+
 struct ScanArgs {
     const unsigned long long *deg;  // entries << 32 | d_in, per vertex
     uint32_t N;
     int all_ties;
-    const unsigned long long *dmaxkey;
+    const unsigned long long *dmaxkey;  // batch: one per graph
     uint32_t *vstart;  // first entry of each column in the sorted words | KILL_BIT
     uint64_t *status;
     uint32_t *tile_ctr;
     uint64_t *info;
+    // a batch (union of graphs): each column is tested against its own
+    // graph's maximum, and ties / supernodes are counted per graph
+    int batched;
+    unsigned long long *gcount;  // [2 * n]: ties, supernodes
+    VBases vb;
 };
 
 __global__ void __launch_bounds__(SC_THREADS) mask_scan_kernel(ScanArgs a) {
@@ -523,10 +576,11 @@ __global__ void __launch_bounds__(SC_THREADS) mask_scan_kernel(ScanArgs a) {
     const uint64_t tile = s_tile;
     const uint64_t ntiles = (a.N + SC_TILE - 1) / SC_TILE;
     if (tile >= ntiles) return;
-    const unsigned long long key = *a.dmaxkey;
-    const uint32_t dmax = (uint32_t)(key >> 32);
-    const uint32_t vmax = ~(uint32_t)key;
     const uint64_t v0 = tile * SC_TILE + (uint64_t)tid * SC_ITEMS;
+    uint32_t gr = a.batched && v0 < a.N ? graph_of(a.vb, (uint32_t)v0) : 0u;
+    unsigned long long key = a.dmaxkey[a.batched ? min(gr, a.vb.n - 1) : 0u];
+    uint32_t dmax = (uint32_t)(key >> 32);
+    uint32_t vmax = ~(uint32_t)key;
     uint32_t ent[SC_ITEMS], killed = 0;
     uint64_t sum = 0;
     unsigned long long ties = 0, sup = 0;
@@ -538,7 +592,25 @@ __global__ void __launch_bounds__(SC_THREADS) mask_scan_kernel(ScanArgs a) {
             const unsigned long long w = a.deg[v];
             const uint32_t din = (uint32_t)w;
             ent[j] = (uint32_t)(w >> 32);
+            if (a.batched) {
+                while (gr < a.vb.n && (uint32_t)v >= a.vb.vbase[gr + 1]) {
+                    ++gr;
+                    if (gr < a.vb.n) {
+                        key = a.dmaxkey[gr];
+                        dmax = (uint32_t)(key >> 32);
+                        vmax = ~(uint32_t)key;
+                    }
+                }
+                if (gr >= a.vb.n) {  // padding: no graph, no entries
+                    sum += ent[j];
+                    continue;
+                }
+            }
             const bool is_max = din == dmax && (a.all_ties || (uint32_t)v == vmax);
+            if (a.batched) {
+                if (din == dmax) atomicAdd(&a.gcount[2 * gr], 1ull);
+                if (is_max) atomicAdd(&a.gcount[2 * gr + 1], 1ull);
+            }
             ties += din == dmax;
             sup += is_max;
             killed |= (uint32_t)(is_max || din == 1) << j;
@@ -549,7 +621,7 @@ __global__ void __launch_bounds__(SC_THREADS) mask_scan_kernel(ScanArgs a) {
     const uint64_t ex = block_exclusive_sum<uint64_t, SC_THREADS>(sum, s_scan, &total);
     if (tid < 32) warp_tile_prefix(a.status, tile, total, &s_excl);
     __syncthreads();
-    if (tid == 0 && tile == ntiles - 1) {
+    if (tid == 0 && tile == ntiles - 1 && !a.batched) {
         a.info[PP_INFO_DMAX] = dmax;
         a.info[PP_INFO_VMAX] = vmax;
     }
@@ -571,7 +643,7 @@ __global__ void __launch_bounds__(SC_THREADS) mask_scan_kernel(ScanArgs a) {
         s_red[1][tid >> 5] = sup;
     }
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && !a.batched) {
         unsigned long long t = 0, s = 0;
         for (int w = 0; w < SC_THREADS / 32; ++w) {
             t += s_red[0][w];
@@ -678,6 +750,43 @@ struct PermDst {
     }
 };
 
+// A batch's storage order is graph-major: graph, then row bucket, then id,
+// so that every graph's rows and columns keep one range of positions (its
+// union ids) and, inside it, the order a single-graph call gives.  Key:
+// (graph << 5 | bucket) << 32 | union id, sorted on bits 32..47 (two passes).
+__global__ void __launch_bounds__(256) vkey_kernel(const uint32_t *d_out, uint32_t N, VBases vb,
+                                                   unsigned long long *vkey) {
+    constexpr int ITEMS = 16;
+    for (uint64_t v0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * ITEMS; v0 < N;
+         v0 += (uint64_t)gridDim.x * blockDim.x * ITEMS) {
+        uint32_t gr = graph_of(vb, (uint32_t)v0);
+        for (int j = 0; j < ITEMS && v0 + j < N; ++j) {
+            const uint32_t v = (uint32_t)(v0 + j);
+            while (gr < vb.n && v >= vb.vbase[gr + 1]) ++gr;
+            vkey[v] = ((unsigned long long)((gr << 5) | row_bucket(d_out[v])) << 32) | v;
+        }
+    }
+}
+struct VKeySrc {
+    const unsigned long long *k;
+    __device__ __forceinline__ bool load(uint64_t i, unsigned long long &key, uint32_t &) const {
+        key = k[i];
+        return true;
+    }
+};
+struct VKeyDst {
+    unsigned long long *k;
+    __device__ __forceinline__ void store(uint64_t pos, unsigned long long key, uint32_t) const { k[pos] = key; }
+};
+struct PermDst64 {
+    uint32_t *perm, *iperm;
+    __device__ __forceinline__ void store(uint64_t pos, unsigned long long key, uint32_t) const {
+        const uint32_t u = (uint32_t)key;
+        iperm[pos] = u;
+        perm[u] = (uint32_t)pos;
+    }
+};
+
 // The transpose sorts the 64-bit entry words by their column (bits 63:32).
 struct EntSrc {
     const unsigned long long *e;
@@ -760,21 +869,21 @@ extern "C" pp_status pp_build_filter_normalize_workspace(uint64_t M, uint32_t sc
     return PP_OK;
 }
 
-extern "C" pp_status pp_build_filter_normalize(const uint32_t *us, const uint32_t *vs, uint64_t M,
-                                               uint32_t scale, pp_supernode_rule rule, const pp_graph *g,
-                                               void *ws, size_t ws_bytes, void *stream) {
-    if (scale < 1 || scale > 27 || M > (1ull << 31) || !g) return PP_ERR_INVALID_ARG;
-    if (rule != PP_SUPERNODE_LOWEST && rule != PP_SUPERNODE_ALL_TIES) return PP_ERR_INVALID_ARG;
-    if (g->scale != scale || g->M != M) return PP_ERR_INVALID_ARG;
-    if (!g->colptr || !g->rowc || !g->ovf_key || !g->ovf_cnt || !g->d_in || !g->d_out || !g->info || !g->perm ||
-        !g->iperm)
-        return PP_ERR_INVALID_ARG;
-    if (M && (!us || !vs)) return PP_ERR_INVALID_ARG;
-    const k2::Layout need = k2::layout(nullptr, M, scale);
-    pp_status st = check_ws(ws, ws_bytes, need.bytes);
-    if (st != PP_OK) return st;
-    const k2::Layout L = k2::layout(ws, M, scale);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
+namespace pp {
+namespace k2 {
+
+// What a batch changes in the sequence below: the relabel (graph-major
+// storage order), max(d_in) and the supernode test per graph.
+struct BatchCtx {
+    VBases vb;
+    unsigned long long *vkey[2];  // [N] vertex keys of the relabel, ping-pong
+    unsigned long long *dmaxkeys; // [n] zeroed by the caller
+    unsigned long long *gcount;   // [2 n] zeroed by the caller
+};
+
+// Kernel 2 on sorted (us, vs) into g; a batch runs it on the union of its graphs.
+inline pp_status run(const uint32_t *us, const uint32_t *vs, uint64_t M, uint32_t scale, pp_supernode_rule rule,
+                     const pp_graph *g, const Layout &L, cudaStream_t s, const BatchCtx *bc) {
     const uint32_t N = 1u << scale;
     const uint32_t cmax = (uint32_t)((1ull << (32 - scale)) - 1);
     const int P = k2::num_passes(scale);
@@ -806,11 +915,25 @@ extern "C" pp_status pp_build_filter_normalize(const uint32_t *us, const uint32_
     // relabel: the vertices by row bucket (one pass), giving perm and iperm
     const uint64_t vtiles = ceil_div(N, os::TILE);
     const size_t vword = L.vsort.wide ? 8 : 4;
-    k2::relabel_hist_kernel<<<ngrid, 256, 0, s>>>(g->d_out, N, L.vsort.hist, static_cast<uint32_t *>(L.vsort.status[0]),
-                                                  vtiles * os::RADIX * vword / 4);
-    count_launch();
-    os::launch_pass<uint32_t>(L.vsort, 0, 1, k2::VertexSrc{g->d_out}, k2::PermDst{g->perm, g->iperm}, nullptr, N, s,
-                              k2::VKEY_SHIFT);
+    if (!bc) {
+        k2::relabel_hist_kernel<<<ngrid, 256, 0, s>>>(g->d_out, N, L.vsort.hist,
+                                                      static_cast<uint32_t *>(L.vsort.status[0]),
+                                                      vtiles * os::RADIX * vword / 4);
+        count_launch();
+        os::launch_pass<uint32_t>(L.vsort, 0, 1, k2::VertexSrc{g->d_out}, k2::PermDst{g->perm, g->iperm}, nullptr, N,
+                                  s, k2::VKEY_SHIFT);
+    } else {
+        // graph-major: (graph, bucket) in two 8-bit passes over bits 32..47 of the vertex keys
+        k2::vkey_kernel<<<ngrid, 256, 0, s>>>(g->d_out, N, bc->vb, bc->vkey[0]);
+        os::hist_kernel<unsigned long long, k2::VKeySrc><<<ngrid, 256, 0, s>>>(
+            k2::VKeySrc{bc->vkey[0]}, nullptr, N, 2, L.vsort.hist, static_cast<uint32_t *>(L.vsort.status[0]),
+            vtiles * os::RADIX * vword / 4, 32u);
+        count_launch(2);
+        os::launch_pass<unsigned long long>(L.vsort, 0, 2, k2::VKeySrc{bc->vkey[0]}, k2::VKeyDst{bc->vkey[1]}, nullptr,
+                                            N, s, 32u);
+        os::launch_pass<unsigned long long>(L.vsort, 1, 2, k2::VKeySrc{bc->vkey[1]},
+                                            k2::PermDst64{g->perm, g->iperm}, nullptr, N, s, 32u);
+    }
     if (M) {
         // each row's first entry in vertex order, then in position order
         k2::offsets_kernel<<<(unsigned)sc_tiles, k2::SC_THREADS, 0, s>>>(
@@ -843,8 +966,23 @@ extern "C" pp_status pp_build_filter_normalize(const uint32_t *us, const uint32_
                                                  L.deg);
         count_launch();
     }
-    k2::dmax_kernel<<<ngrid, 256, 0, s>>>(L.deg, N, g->d_in, L.dmaxkey);
-    k2::ScanArgs sa{L.deg, N, rule == PP_SUPERNODE_ALL_TIES, L.dmaxkey, L.shift, L.sc_status, L.ctr + 1, g->info};
+    if (!bc)
+        k2::dmax_kernel<<<ngrid, 256, 0, s>>>(L.deg, N, g->d_in, L.dmaxkey);
+    else
+        k2::dmax_batched_kernel<<<ngrid, 256, 0, s>>>(L.deg, N, bc->vb, g->d_in, bc->dmaxkeys);
+    k2::ScanArgs sa;
+    sa.deg = L.deg;
+    sa.N = N;
+    sa.all_ties = rule == PP_SUPERNODE_ALL_TIES;
+    sa.dmaxkey = bc ? bc->dmaxkeys : L.dmaxkey;
+    sa.vstart = L.shift;
+    sa.status = L.sc_status;
+    sa.tile_ctr = L.ctr + 1;
+    sa.info = g->info;
+    sa.batched = bc != nullptr;
+    sa.gcount = bc ? bc->gcount : nullptr;
+    sa.vb.n = 0;
+    if (bc) sa.vb = bc->vb;
     k2::mask_scan_kernel<<<(unsigned)sc_tiles, k2::SC_THREADS, 0, s>>>(sa);
     k2::PosArgs pa{L.deg, g->iperm, L.shift, N, g->colptr, L.sc_status + sc_tiles, L.ctr + 5, g->info};
     k2::pos_scan_kernel<<<(unsigned)sc_tiles, k2::SC_THREADS, 0, s>>>(pa);
@@ -857,5 +995,383 @@ extern "C" pp_status pp_build_filter_normalize(const uint32_t *us, const uint32_
     }
     k2::finalize_kernel<<<ngrid, 256, 0, s>>>(g->d_out, N, g->inv_dout32, g->inv_dout64);
     count_launch();
+    return launch_status();
+}
+
+}  // namespace k2
+}  // namespace pp
+
+extern "C" pp_status pp_build_filter_normalize(const uint32_t *us, const uint32_t *vs, uint64_t M,
+                                               uint32_t scale, pp_supernode_rule rule, const pp_graph *g,
+                                               void *ws, size_t ws_bytes, void *stream) {
+    if (scale < 1 || scale > 27 || M > (1ull << 31) || !g) return PP_ERR_INVALID_ARG;
+    if (rule != PP_SUPERNODE_LOWEST && rule != PP_SUPERNODE_ALL_TIES) return PP_ERR_INVALID_ARG;
+    if (g->scale != scale || g->M != M) return PP_ERR_INVALID_ARG;
+    if (!g->colptr || !g->rowc || !g->ovf_key || !g->ovf_cnt || !g->d_in || !g->d_out || !g->info || !g->perm ||
+        !g->iperm)
+        return PP_ERR_INVALID_ARG;
+    if (M && (!us || !vs)) return PP_ERR_INVALID_ARG;
+    const k2::Layout need = k2::layout(nullptr, M, scale);
+    pp_status st = check_ws(ws, ws_bytes, need.bytes);
+    if (st != PP_OK) return st;
+    const k2::Layout L = k2::layout(ws, M, scale);
+    return k2::run(us, vs, M, scale, rule, g, L, static_cast<cudaStream_t>(stream), nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// Kernel 2 for a batch of graphs (pp_build_filter_normalize_batched).  The
+// graphs' sorted edges are gathered into one union graph (graph g's vertex u
+// becomes union id vbase[g] + u; the union stays sorted by (u, v) because
+// the id ranges follow the graph order), Kernel 2 runs once on it with a
+// graph-major storage order and per-graph supernodes, and split passes write
+// each graph's own outputs: local ids and positions, counts repacked into
+// the graph's count field (32 - scale bits) with its own overflow table,
+// and its scalars.  Every output equals that of a single-graph call.
+
+namespace pp {
+namespace k2b {
+
+constexpr int MAX_G = PP_BATCH_MAX_GRAPHS;
+constexpr int TILE = 4096;
+
+struct Shape {
+    uint32_t n, S;        // graphs, union scale
+    uint64_t Mtot;
+    uint32_t nvert;       // sum of N_g
+};
+
+// The union's inputs: graph g's sorted edges and where they go.
+struct GatherArgs {
+    uint32_t n;
+    const uint32_t *us[MAX_G], *vs[MAX_G];
+    uint64_t eoff[MAX_G + 1];
+    uint32_t vbase[MAX_G + 1];
+    uint64_t toff[MAX_G + 1];  // first tile of graph g
+    uint32_t scale[MAX_G];
+};
+
+__device__ __forceinline__ uint32_t tile_graph(const uint64_t *toff, uint32_t n, uint64_t t) {
+    uint32_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (toff[mid] <= t)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) gather_kernel(GatherArgs a, uint32_t *U, uint32_t *V) {
+    const uint32_t g = tile_graph(a.toff, a.n, blockIdx.x);
+    const uint64_t e0 = (blockIdx.x - a.toff[g]) * (uint64_t)TILE, M = a.eoff[g + 1] - a.eoff[g];
+    const uint32_t base = a.vbase[g], sc = a.scale[g];
+    for (uint64_t i = e0 + threadIdx.x; i < min(M, e0 + TILE); i += blockDim.x) {
+        uint32_t x = __ldg(a.us[g] + i), y = __ldg(a.vs[g] + i);
+        if ((x | y) >> sc) {  // an id >= N_g: reported, kept inside the graph's own range
+            pp_set_error(PP_DEV_RANGE);
+            x &= (1u << sc) - 1u;
+            y &= (1u << sc) - 1u;
+        }
+        U[a.eoff[g] + i] = base + x;
+        V[a.eoff[g] + i] = base + y;
+    }
+}
+
+// The union's outputs and each graph's.
+struct SplitArgs {
+    uint32_t n, S, cmaxU;
+    uint32_t vbase[MAX_G + 1];
+    uint64_t vtoff[MAX_G + 1];  // first vertex tile of graph g
+    const uint32_t *colptr, *rowc, *ovf_cnt, *d_in, *d_out, *perm, *iperm, *row_nent;
+    const uint64_t *ovf_key, *info;
+    const float *inv32;
+    const double *inv64;
+    const unsigned long long *dmaxkeys, *gcount;
+    pp_graph out[MAX_G];
+};
+
+// Per vertex of every graph: degrees, 1/d_out, the storage order and the column pointers, local.
+__global__ void __launch_bounds__(256) split_vertex_kernel(SplitArgs a) {
+    const uint32_t g = tile_graph(a.vtoff, a.n, blockIdx.x);
+    const uint32_t base = a.vbase[g], Ng = a.vbase[g + 1] - base;
+    const pp_graph &o = a.out[g];
+    const uint32_t c0 = a.colptr[base];
+    const uint64_t l0 = (blockIdx.x - a.vtoff[g]) * (uint64_t)TILE;
+    for (uint64_t l = l0 + threadIdx.x; l < min((uint64_t)Ng, l0 + TILE); l += blockDim.x) {
+        const uint32_t u = base + (uint32_t)l;
+        o.d_in[l] = a.d_in[u];
+        o.d_out[l] = a.d_out[u];
+        if (o.inv_dout32) o.inv_dout32[l] = a.inv32[u];
+        if (o.inv_dout64) o.inv_dout64[l] = a.inv64[u];
+        o.perm[l] = a.perm[u] - base;
+        o.iperm[l] = a.iperm[u] - base;
+        o.colptr[l] = a.colptr[u] - c0;
+        if (l + 1 == Ng) o.colptr[Ng] = a.colptr[base + Ng] - c0;
+    }
+}
+
+__device__ __forceinline__ uint32_t ovf_find(const uint64_t *keys, const uint32_t *cnts, uint64_t n, uint64_t key) {
+    uint64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (keys[mid] < key)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return (lo < n && keys[lo] == key) ? cnts[lo] : 0u;
+}
+
+// One warp per union column position: its kept entries as the graph's words
+// (local row position, count in the graph's field, escaped past its maximum).
+__global__ void __launch_bounds__(256) split_entry_kernel(SplitArgs a) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t nvert = a.vbase[a.n], umaskU = (1u << a.S) - 1u;
+    const uint64_t novf = a.info[PP_INFO_NOVF];
+    const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x / 32);
+    for (uint64_t q = (uint64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); q < nvert; q += nw) {
+        uint32_t g = 0, lo = 0, hi = a.n - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (a.vbase[mid] <= q)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        g = lo;
+        const uint32_t base = a.vbase[g], sg = a.out[g].scale;
+        const uint32_t cmaxg = (uint32_t)((1ull << (32 - sg)) - 1);
+        const uint32_t s = a.colptr[q], e = a.colptr[q + 1], d0 = s - a.colptr[base];
+        uint32_t *dst = a.out[g].rowc + d0;
+        for (uint32_t k = lane; k < e - s; k += 32) {
+            const uint32_t w = a.rowc[s + k];
+            const uint32_t pos = w & umaskU;
+            uint32_t c = w >> a.S;
+            if (c == a.cmaxU) c = ovf_find(a.ovf_key, a.ovf_cnt, novf, ((uint64_t)a.iperm[pos] << 32) | a.iperm[q]);
+            dst[k] = ((c >= cmaxg ? cmaxg : c) << sg) | (pos - base);
+        }
+    }
+}
+
+// One thread per graph: its overflow table (the union table's entries of the
+// graph whose count reaches the graph's own escape value, in key order).
+__global__ void __launch_bounds__(128) split_ovf_kernel(SplitArgs a) {
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= a.n) return;
+    const uint64_t novf = a.info[PP_INFO_NOVF];
+    const uint32_t base = a.vbase[g], end = a.vbase[g + 1], sg = a.out[g].scale;
+    const uint32_t cmaxg = (uint32_t)((1ull << (32 - sg)) - 1);
+    uint64_t lo = 0, hi = novf;
+    const uint64_t first_key = (uint64_t)base << 32;
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (a.ovf_key[mid] < first_key)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    uint64_t k = 0;
+    for (uint64_t i = lo; i < novf && (uint32_t)(a.ovf_key[i] >> 32) < end; ++i) {
+        if (a.ovf_cnt[i] < cmaxg) continue;
+        const uint64_t key = a.ovf_key[i];
+        a.out[g].ovf_key[k] = ((uint64_t)((uint32_t)(key >> 32) - base) << 32) | (uint32_t)((uint32_t)key - base);
+        a.out[g].ovf_cnt[k] = a.ovf_cnt[i];
+        ++k;
+    }
+    a.out[g].info[PP_INFO_NOVF] = k;
+}
+
+// One block per graph: its scalars.
+__global__ void __launch_bounds__(256) split_info_kernel(SplitArgs a) {
+    __shared__ unsigned long long s_red[8];
+    const uint32_t g = blockIdx.x;
+    const uint32_t base = a.vbase[g], Ng = a.vbase[g + 1] - base;
+    unsigned long long nnz0 = 0;
+    for (uint32_t l = threadIdx.x; l < Ng; l += blockDim.x) nnz0 += a.row_nent[base + l];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nnz0 += __shfl_down_sync(0xffffffffu, nnz0, o);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = nnz0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < 8; ++w) t += s_red[w];
+        uint64_t *info = a.out[g].info;
+        const unsigned long long key = a.dmaxkeys[g];
+        info[PP_INFO_NNZ0] = t;
+        info[PP_INFO_NNZ] = a.colptr[base + Ng] - a.colptr[base];
+        info[PP_INFO_DMAX] = key >> 32;
+        info[PP_INFO_VMAX] = ~(uint32_t)key - base;
+        info[PP_INFO_TIES] = a.gcount[2 * g];
+        info[PP_INFO_SUPERNODES] = a.gcount[2 * g + 1];
+        info[7] = 0;
+    }
+}
+
+struct Layout {
+    uint32_t *U, *V;
+    pp_graph ug;  // the union graph
+    unsigned long long *vkey[2], *dmaxkeys, *gcount;
+    k2::Layout k2;
+    size_t bytes;
+};
+
+inline Layout layout(void *ws, const Shape &sh) {
+    Carver c(ws);
+    Layout L;
+    const uint64_t N = 1ull << sh.S, cap = sh.Mtot ? sh.Mtot : 1;
+    uint64_t len[PP_GRAPH_ARRAYS];
+    pp_graph_lengths(sh.Mtot, sh.S, len);
+    L.U = c.take<uint32_t>(cap);
+    L.V = c.take<uint32_t>(cap);
+    L.ug.scale = sh.S;
+    L.ug.reserved = 0;
+    L.ug.M = sh.Mtot;
+    L.ug.colptr = c.take<uint32_t>(len[0]);
+    L.ug.rowc = c.take<uint32_t>(len[1]);
+    L.ug.ovf_key = c.take<uint64_t>(len[2]);
+    L.ug.ovf_cnt = c.take<uint32_t>(len[3]);
+    L.ug.d_in = c.take<uint32_t>(len[4]);
+    L.ug.d_out = c.take<uint32_t>(len[5]);
+    L.ug.inv_dout32 = c.take<float>(len[6]);
+    L.ug.inv_dout64 = c.take<double>(len[7]);
+    L.ug.info = c.take<uint64_t>(len[8]);
+    L.ug.perm = c.take<uint32_t>(len[9]);
+    L.ug.iperm = c.take<uint32_t>(len[10]);
+    L.vkey[0] = c.take<unsigned long long>(N);
+    L.vkey[1] = c.take<unsigned long long>(N);
+    L.dmaxkeys = c.take<unsigned long long>(MAX_G);
+    L.gcount = c.take<unsigned long long>(2 * MAX_G);
+    const size_t head = c.size();
+    L.k2 = k2::layout(ws ? static_cast<char *>(ws) + head : nullptr, sh.Mtot, sh.S);
+    L.bytes = head + L.k2.bytes;
+    return L;
+}
+
+inline bool shape(uint32_t n, const uint64_t *M, const uint32_t *scale, Shape *sh) {
+    if (n < 1 || n > (uint32_t)MAX_G || !M || !scale) return false;
+    uint64_t nv = 0, me = 0;
+    for (uint32_t g = 0; g < n; ++g) {
+        if (scale[g] < 1 || scale[g] > 27 || M[g] > (1ull << 31)) return false;
+        nv += 1ull << scale[g];
+        me += M[g];
+    }
+    if (nv > (1ull << 27) || me > (1ull << 31)) return false;
+    uint32_t s = 1;
+    while ((1ull << s) < nv) ++s;
+    sh->n = n;
+    sh->S = s;
+    sh->Mtot = me;
+    sh->nvert = (uint32_t)nv;
+    return true;
+}
+
+}  // namespace k2b
+}  // namespace pp
+
+extern "C" pp_status pp_build_filter_normalize_batched_workspace(uint32_t n_graphs, const uint64_t *M,
+                                                                 const uint32_t *scale, size_t *bytes) {
+    k2b::Shape sh;
+    if (!bytes || !k2b::shape(n_graphs, M, scale, &sh)) return PP_ERR_INVALID_ARG;
+    *bytes = k2b::layout(nullptr, sh).bytes;
+    return PP_OK;
+}
+
+extern "C" pp_status pp_build_filter_normalize_batched(uint32_t n_graphs, const uint32_t *const *u_sorted,
+                                                       const uint32_t *const *v_sorted, pp_supernode_rule rule,
+                                                       const pp_graph *gs, void *ws, size_t ws_bytes,
+                                                       void *stream) {
+    if (!gs || !u_sorted || !v_sorted || n_graphs < 1 || n_graphs > (uint32_t)k2b::MAX_G) return PP_ERR_INVALID_ARG;
+    if (rule != PP_SUPERNODE_LOWEST && rule != PP_SUPERNODE_ALL_TIES) return PP_ERR_INVALID_ARG;
+    uint64_t M[k2b::MAX_G];
+    uint32_t scale[k2b::MAX_G];
+    for (uint32_t g = 0; g < n_graphs; ++g) {
+        const pp_graph &o = gs[g];
+        M[g] = o.M;
+        scale[g] = o.scale;
+        if (!o.colptr || !o.rowc || !o.ovf_key || !o.ovf_cnt || !o.d_in || !o.d_out || !o.info || !o.perm ||
+            !o.iperm)
+            return PP_ERR_INVALID_ARG;
+        if (o.M && (!u_sorted[g] || !v_sorted[g])) return PP_ERR_INVALID_ARG;
+    }
+    k2b::Shape sh;
+    if (!k2b::shape(n_graphs, M, scale, &sh)) return PP_ERR_INVALID_ARG;
+    const k2b::Layout need = k2b::layout(nullptr, sh);
+    pp_status st = check_ws(ws, ws_bytes, need.bytes);
+    if (st != PP_OK) return st;
+    const k2b::Layout L = k2b::layout(ws, sh);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    // the union's edges
+    k2b::GatherArgs ga;
+    ga.n = n_graphs;
+    uint64_t eo = 0, to = 0;
+    uint32_t vb = 0;
+    k2::BatchCtx bc;
+    bc.vb.n = n_graphs;
+    for (uint32_t g = 0; g < n_graphs; ++g) {
+        ga.us[g] = u_sorted[g];
+        ga.vs[g] = v_sorted[g];
+        ga.eoff[g] = eo;
+        ga.vbase[g] = vb;
+        ga.toff[g] = to;
+        ga.scale[g] = scale[g];
+        bc.vb.vbase[g] = vb;
+        eo += M[g];
+        to += ceil_div(M[g], k2b::TILE);
+        vb += 1u << scale[g];
+    }
+    ga.eoff[n_graphs] = eo;
+    ga.vbase[n_graphs] = vb;
+    ga.toff[n_graphs] = to;
+    bc.vb.vbase[n_graphs] = vb;
+    if (to) {
+        k2b::gather_kernel<<<(unsigned)to, 256, 0, s>>>(ga, L.U, L.V);
+        count_launch();
+    }
+    // Kernel 2 on the union
+    bc.vkey[0] = L.vkey[0];
+    bc.vkey[1] = L.vkey[1];
+    bc.dmaxkeys = L.dmaxkeys;
+    bc.gcount = L.gcount;
+    cudaMemsetAsync(L.dmaxkeys, 0, k2b::MAX_G * sizeof(unsigned long long), s);
+    cudaMemsetAsync(L.gcount, 0, 2 * k2b::MAX_G * sizeof(unsigned long long), s);
+    st = k2::run(L.U, L.V, sh.Mtot, sh.S, rule, &L.ug, L.k2, s, &bc);
+    if (st != PP_OK) return st;
+    // each graph's outputs
+    k2b::SplitArgs sa;
+    sa.n = n_graphs;
+    sa.S = sh.S;
+    sa.cmaxU = (uint32_t)((1ull << (32 - sh.S)) - 1);
+    uint64_t vt = 0;
+    for (uint32_t g = 0; g <= n_graphs; ++g) {
+        sa.vbase[g] = bc.vb.vbase[g];
+        sa.vtoff[g] = vt;
+        if (g < n_graphs) {
+            vt += ceil_div(1ull << scale[g], k2b::TILE);
+            sa.out[g] = gs[g];
+        }
+    }
+    sa.colptr = L.ug.colptr;
+    sa.rowc = L.ug.rowc;
+    sa.ovf_key = L.ug.ovf_key;
+    sa.ovf_cnt = L.ug.ovf_cnt;
+    sa.d_in = L.ug.d_in;
+    sa.d_out = L.ug.d_out;
+    sa.inv32 = L.ug.inv_dout32;
+    sa.inv64 = L.ug.inv_dout64;
+    sa.info = L.ug.info;
+    sa.perm = L.ug.perm;
+    sa.iperm = L.ug.iperm;
+    sa.row_nent = L.k2.row_nent;
+    sa.dmaxkeys = L.dmaxkeys;
+    sa.gcount = L.gcount;
+    const int sms = sm_count();
+    k2b::split_vertex_kernel<<<(unsigned)vt, 256, 0, s>>>(sa);
+    k2b::split_entry_kernel<<<(unsigned)std::max<uint64_t>(1, std::min<uint64_t>(ceil_div(sh.nvert, 8), 32ull * sms)),
+                              256, 0, s>>>(sa);
+    k2b::split_ovf_kernel<<<(unsigned)ceil_div(n_graphs, 128), 128, 0, s>>>(sa);
+    k2b::split_info_kernel<<<n_graphs, 256, 0, s>>>(sa);
+    count_launch(4);
     return launch_status();
 }

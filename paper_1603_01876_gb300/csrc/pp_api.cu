@@ -224,6 +224,76 @@ extern "C" pp_status pp_pagerank_batched_capture(const pp_graph *gs, uint32_t n_
     return st;
 }
 
+namespace {
+bool batch_sizes(uint32_t n, const pp_graph *gs, uint64_t *M, uint32_t *scale) {
+    if (!gs || n < 1 || n > PP_BATCH_MAX_GRAPHS) return false;
+    for (uint32_t g = 0; g < n; ++g) {
+        M[g] = gs[g].M;
+        scale[g] = gs[g].scale;
+    }
+    return true;
+}
+}  // namespace
+
+extern "C" pp_status pp_pipeline_batched_workspace(uint32_t n_graphs, const pp_graph *gs, uint32_t nrhs,
+                                                   uint32_t iters, size_t *bytes) {
+    uint64_t M[PP_BATCH_MAX_GRAPHS];
+    uint32_t scale[PP_BATCH_MAX_GRAPHS];
+    if (!bytes || !batch_sizes(n_graphs, gs, M, scale)) return PP_ERR_INVALID_ARG;
+    size_t b1 = 0, b2 = 0, b3 = 0;
+    pp_status st = pp_sort_edges_batched_workspace(n_graphs, M, scale, &b1);
+    if (st == PP_OK) st = pp_build_filter_normalize_batched_workspace(n_graphs, M, scale, &b2);
+    if (st == PP_OK) st = pp_pagerank_batched_workspace(gs, n_graphs, nrhs, iters, &b3);
+    if (st != PP_OK) return st;
+    *bytes = std::max(b1, std::max(b2, b3));
+    return PP_OK;
+}
+
+extern "C" pp_status pp_pipeline_batched_capture(uint32_t n_graphs, const uint32_t *const *u,
+                                                 const uint32_t *const *v, uint32_t *const *u_sorted,
+                                                 uint32_t *const *v_sorted, pp_supernode_rule rule, const pp_graph *gs,
+                                                 const double *r0, uint32_t nrhs, uint32_t iters, double c,
+                                                 float *r_out, void *ws, size_t ws_bytes, void *stream,
+                                                 pp_exec **exec) {
+    if (!exec) return PP_ERR_INVALID_ARG;
+    *exec = nullptr;
+    uint64_t M[PP_BATCH_MAX_GRAPHS];
+    uint32_t scale[PP_BATCH_MAX_GRAPHS];
+    if (!batch_sizes(n_graphs, gs, M, scale) || !u_sorted || !v_sorted) return PP_ERR_INVALID_ARG;
+    size_t need = 0;
+    pp_status st = pp_pipeline_batched_workspace(n_graphs, gs, nrhs, iters, &need);
+    if (st != PP_OK) return st;
+    st = check_ws(ws, ws_bytes, need);
+    if (st != PP_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool own = s == nullptr;
+    if (own && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return PP_ERR_CUDA;
+    st = PP_ERR_CUDA;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+        const uint64_t before = g_launches.load();
+        st = pp_sort_edges_batched(n_graphs, u, v, M, scale, u_sorted, v_sorted, ws, ws_bytes, s);
+        if (st == PP_OK)
+            st = pp_build_filter_normalize_batched(n_graphs, u_sorted, v_sorted, rule, gs, ws, ws_bytes, s);
+        if (st == PP_OK) st = pp_pagerank_batched(gs, n_graphs, r0, nrhs, iters, c, r_out, ws, ws_bytes, s);
+        const uint64_t kernels = g_launches.load() - before;
+        g_launches.fetch_sub(kernels);  // recorded, not launched
+        const cudaError_t e = cudaStreamEndCapture(s, &graph);
+        if (st == PP_OK && (e != cudaSuccess || !graph)) st = PP_ERR_CUDA;
+        if (st == PP_OK) {
+            cudaGraphExec_t ge = nullptr;
+            if (cudaGraphInstantiate(&ge, graph, 0) == cudaSuccess)
+                *exec = new pp_exec{ge, kernels};
+            else
+                st = PP_ERR_CUDA;
+        }
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (st != PP_OK) cudaGetLastError();
+    if (own) cudaStreamDestroy(s);
+    return st;
+}
+
 extern "C" pp_status pp_exec_launch(pp_exec *exec, void *stream) {
     if (!exec) return PP_ERR_INVALID_ARG;
     if (cudaGraphLaunch(exec->exec, static_cast<cudaStream_t>(stream)) != cudaSuccess) return PP_ERR_CUDA;
