@@ -573,9 +573,12 @@ def run_k3_only(args):
 
 
 def run_batched(dev, steps=3, warmup=1, nrhs=32, n_graphs=64, lo=12, hi=18):
-    """Batched Kernel 3: 64 Kronecker graphs of scales drawn from 12..18, 32
-    start vectors each, one SpMM kernel per iteration (binary32), against the
-    2048 single-vector binary64 runs of the plain path on the same GPU."""
+    """The batched configuration: 64 Kronecker graphs of scales drawn from
+    12..18, each with 32 start vectors.  Kernels 1 and 2 for all graphs at
+    once (one set of launches), Kernel 3 as one SpMM launch per iteration
+    (binary32), timed per stage and as one CUDA-graph replay of the whole
+    pipeline; against 64 sequential single-graph pipelines (Kernels 1 and 2,
+    then the 32 start vectors as 32 binary64 runs) on the same GPU."""
     import numpy as np
     import torch
 
@@ -583,87 +586,104 @@ def run_batched(dev, steps=3, warmup=1, nrhs=32, n_graphs=64, lo=12, hi=18):
     import paper_1603_01876_gb300 as pp
 
     scales = kernel0.batch_scales(n_graphs, lo, hi, seed=SEED)
-    graphs = []
-    for g, s in enumerate(scales):
-        u, v = kernel0.edges_device(s, SEED, graph=g, device=dev)
-        us, vs = pp.sort_edges(u, v, s)
-        graphs.append(pp.build_filter_normalize(us, vs, s))
-    r0 = np.concatenate([np.stack([kernel0.r0_host(1 << s, SEED, graph=g, rhs=j) for j in range(nrhs)], axis=1)
-                         for g, s in enumerate(scales)])
+    us, vs = [], []
+    for g, sc in enumerate(scales):
+        u, v = kernel0.edges_device(sc, SEED, graph=g, device=dev)
+        us.append(u)
+        vs.append(v)
+    r0 = np.concatenate([np.stack([kernel0.r0_host(1 << sc, SEED, graph=g, rhs=j) for j in range(nrhs)], axis=1)
+                         for g, sc in enumerate(scales)])
     r0d = torch.from_numpy(r0).to(dev)
+    edges = int(sum(u.numel() for u in us))
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, n=steps, w=warmup):
+        for _ in range(w):
+            fn()
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record(stream)
+        for _ in range(n):
+            fn()
+        e[1].record(stream)
+        torch.cuda.synchronize()
+        return e[0].elapsed_time(e[1]) / n
+
+    # the stages with stream launches, in buffers reused between steps
+    sorted_b = pp.sort_edges_batched(us, vs, scales)
+    graphs = pp.build_filter_normalize_batched(sorted_b, scales)
     out = pp.pagerank_batched(graphs, r0d, nrhs, ITERS, DAMPING)
-    for _ in range(warmup):
-        pp.pagerank_batched(graphs, r0d, nrhs, ITERS, DAMPING, out=out)
     torch.cuda.synchronize()
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    e[0].record()
-    for _ in range(steps):
-        pp.pagerank_batched(graphs, r0d, nrhs, ITERS, DAMPING, out=out)
-    e[1].record()
-    torch.cuda.synchronize()
-    ms_stream = e[0].elapsed_time(e[1]) / steps
-    # the set-up alone (0 iterations), for the iteration kernel's roofline
+    k1_ms = timed(lambda: pp.sort_edges_batched(us, vs, scales, outs=sorted_b))
+    k2_ms = timed(lambda: pp.build_filter_normalize_batched(sorted_b, scales, graphs=graphs))
+    k3_ms = timed(lambda: pp.pagerank_batched(graphs, r0d, nrhs, ITERS, DAMPING, out=out))
     out0 = torch.empty_like(out)
-    pp.pagerank_batched(graphs, r0d, nrhs, 0, DAMPING, out=out0)
-    torch.cuda.synchronize()
-    e[0].record()
-    for _ in range(steps):
-        pp.pagerank_batched(graphs, r0d, nrhs, 0, DAMPING, out=out0)
-    e[1].record()
-    torch.cuda.synchronize()
-    ms_setup = e[0].elapsed_time(e[1]) / steps
+    k3_setup_ms = timed(lambda: pp.pagerank_batched(graphs, r0d, nrhs, 0, DAMPING, out=out0))
     del out0
+    # Kernel 3 alone and the whole pipeline, each recorded once as a CUDA graph and replayed
+    ex3 = pp.BatchedExec(graphs, r0d, nrhs, ITERS, DAMPING, out=out)
+    k3_graph_ms = timed(ex3.launch)
+    ex3.close()
+    exp = pp.BatchedPipelineExec(us, vs, scales, r0d, nrhs, ITERS, DAMPING)
+    pipe_ms = timed(exp.launch)
+    pipe_out = exp.out
+    same = bool(torch.equal(pipe_out, out))
+    exp.close()
+    # the sequential single-graph pipelines: Kernels 1-2 per graph, then 32 binary64 runs each
+    row = np.cumsum([0] + [1 << sc for sc in scales])
+    cols = [[r0d[row[g]:row[g + 1], j].contiguous() for j in range(nrhs)] for g in range(n_graphs)]
+    ref = torch.empty(int(row[-1]), nrhs, dtype=torch.float64, device=dev)
+    ws = torch.empty(max(max(pp.workspace_bytes("sort", gr.M, gr.scale), pp.workspace_bytes("build", gr.M, gr.scale),
+                             pp.workspace_bytes("pagerank", gr.M, gr.scale, ITERS, "fp64")) for gr in graphs),
+                     dtype=torch.uint8, device=dev)
+    seq_sorted = [(torch.empty_like(u), torch.empty_like(v)) for u, v in zip(us, vs)]
+    seq_graphs = [pp.Graph(u.numel(), sc, dev) for u, sc in zip(us, scales)]
+
+    def seq_k12():
+        for g, sc in enumerate(scales):
+            pp.sort_edges(us[g], vs[g], sc, out=seq_sorted[g], workspace=ws)
+            pp.build_filter_normalize(seq_sorted[g][0], seq_sorted[g][1], sc, graph=seq_graphs[g], workspace=ws)
+
+    def seq_k3():
+        for g in range(n_graphs):
+            for j in range(nrhs):
+                ref[row[g]:row[g + 1], j] = pp.pagerank(seq_graphs[g], cols[g][j], ITERS, DAMPING, "fp64",
+                                                        workspace=ws)
+
+    seq_k12_ms = timed(seq_k12, n=1, w=1)
+    seq_k3_ms = timed(seq_k3, n=1, w=0)
+    d = (out.double() - ref).abs()
+    l1 = max(float((d[row[g]:row[g + 1], j].sum() / ref[row[g]:row[g + 1], j].abs().sum()))
+             for g in range(n_graphs) for j in range(nrhs))
+    nz = ref != 0
+    # the iteration kernel's roofline: per iteration the packed entries, column
+    # ends, 1/d_out and the nrhs-wide rows of X gathered once and written once
     nnzs = [nnz_of(gr) for gr in graphs]
-    # per iteration: packed entries, column ends, 1/d_out, and the nrhs-wide rows
-    # of X gathered once and written once, binary32
     b_iter = sum(4 * z + 4 * (gr.N + 1) + 4 * gr.N + 2 * 4 * nrhs * gr.N for z, gr in zip(nnzs, graphs))
-    iter_ms = (ms_stream - ms_setup) / ITERS
+    iter_ms = (k3_ms - k3_setup_ms) / ITERS
     peak, peak_kind = _peaks()
     roof = {"bound": "hbm", "kernel": "k3b iterate_vec_kernel (one launch per iteration over all graphs)",
             "achieved": b_iter / (iter_ms * 1e-3) / 1e9, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
             "frac": b_iter / (iter_ms * 1e-3) / 1e9 / peak,
             "per_launch": {"bytes": b_iter, "ms": iter_ms,
-                           "how": "(stage time with stream launches - same call with 0 iterations) / iterations; "
-                                  "bytes: 4 nnz + 8 N + 8 nrhs N per graph (entries, column ends, 1/d_out, the "
-                                  "nrhs-wide rows gathered once and written once)"}}
-    # the stage captured once as a CUDA graph and replayed (the headline batched number)
-    ex = pp.BatchedExec(graphs, r0d, nrhs, ITERS, DAMPING, out=out)
-    for _ in range(warmup):
-        ex.launch()
-    torch.cuda.synchronize()
-    e[0].record()
-    for _ in range(steps):
-        ex.launch()
-    e[1].record()
-    torch.cuda.synchronize()
-    ms_b = e[0].elapsed_time(e[1]) / steps
-    ex.close()
-    # the same 2048 runs one after another, binary64, single-vector path
-    row = np.cumsum([0] + [1 << s for s in scales])
-    cols = [[r0d[row[g]:row[g + 1], j].contiguous() for j in range(nrhs)] for g in range(n_graphs)]
-    ref = torch.empty(int(row[-1]), nrhs, dtype=torch.float64, device=dev)
-    ws = torch.empty(max(pp.workspace_bytes("pagerank", gr.M, gr.scale, ITERS, "fp64") for gr in graphs),
-                     dtype=torch.uint8, device=dev)
-    torch.cuda.synchronize()
-    e[0].record()
-    for g in range(n_graphs):
-        for j in range(nrhs):
-            ref[row[g]:row[g + 1], j] = pp.pagerank(graphs[g], cols[g][j], ITERS, DAMPING, "fp64", workspace=ws)
-    e[1].record()
-    torch.cuda.synchronize()
-    ms_s = e[0].elapsed_time(e[1])
-    d = (out.double() - ref).abs()
-    l1 = max(float((d[row[g]:row[g + 1], j].sum() / ref[row[g]:row[g + 1], j].abs().sum()))
-             for g in range(n_graphs) for j in range(nrhs))
-    nz = ref != 0
-    edges = int(sum(gr.M for gr in graphs))
+                           "how": "(Kernel 3 stage, stream launches - the same call with 0 iterations) / "
+                                  "iterations; bytes: 4 nnz + 8 N + 8 nrhs N per graph (entries, column ends, "
+                                  "1/d_out, the nrhs-wide rows gathered once and written once)"}}
+    seq_ms = seq_k12_ms + seq_k3_ms
     return {"graphs": n_graphs, "scales": "%d..%d" % (lo, hi), "start_vectors": nrhs, "edges": edges,
-            "ms": ms_b, "launch": "one CUDA graph replay per stage", "ms_stream_launches": ms_stream,
-            "edges_per_s": ITERS * edges * nrhs / (ms_b * 1e-3),
-            "sequential_fp64_ms": ms_s, "sequential_fp64_edges_per_s": ITERS * edges * nrhs / (ms_s * 1e-3),
-            "speedup_vs_sequential_fp64": ms_s / ms_b, "max_l1_err_vs_fp64": l1,
-            "max_rel_err_vs_fp64": float((d[nz] / ref[nz].abs()).max()), "roofline": roof,
-            "device_error": pp.last_device_error()}
+            "pipeline_ms": pipe_ms, "launch": "Kernels 1-3 recorded once as one CUDA graph and replayed",
+            "pipeline_edge_vectors_per_s": ITERS * edges * nrhs / (pipe_ms * 1e-3),
+            "pipeline_equals_stage_calls": same,
+            "stages": {"k1_sort_ms": k1_ms, "k1_edges_per_s": edges / (k1_ms * 1e-3),
+                       "k2_filter_ms": k2_ms, "k2_edges_per_s": edges / (k2_ms * 1e-3),
+                       "k3_pagerank_ms": k3_ms, "k3_graph_replay_ms": k3_graph_ms,
+                       "k3_edge_vectors_per_s": ITERS * edges * nrhs / (k3_ms * 1e-3)},
+            "sequential": {"k1_k2_ms": seq_k12_ms, "k3_fp64_ms": seq_k3_ms, "total_ms": seq_ms,
+                           "what": "64 single-graph Kernel 1 + Kernel 2 calls, then 2048 single-vector binary64 "
+                                   "Kernel 3 runs"},
+            "speedup_vs_sequential": seq_ms / pipe_ms,
+            "max_l1_err_vs_fp64": l1, "max_rel_err_vs_fp64": float((d[nz] / ref[nz].abs()).max()),
+            "roofline": roof, "device_error": pp.last_device_error()}
 
 
 def cpu_baseline(scale, seed, max_seconds=20.0, sample_div=16):
@@ -749,7 +769,7 @@ def main():
     ap.add_argument("--no-files", action="store_true", help="skip the edge-file (Kernel 1 with files) section")
     ap.add_argument("--tune", action="append", default=[], metavar="KEY=VALUE",
                     help="set a library tuning knob before running (repeatable)")
-    ap.add_argument("--stage", choices=["all", "k3", "batched"], default="all",
+    ap.add_argument("--stage", choices=["all", "k3", "gather-ceiling", "batched"], default="all",
                     help="k3: time Kernel 3 alone (profiling aid); the default times the whole pipeline")
     ap.add_argument("--tuning", default="default",
                     help="autotuner result to apply (JSON from paper_1603_01876_gb300.tune; 'none' to skip)")
@@ -765,7 +785,8 @@ def main():
         for kv in args.tune:
             k, v = kv.split("=")
             pp.set_tuning(k, int(v))
-    if args.stage == "k3":
+    if args.stage in ("k3", "gather-ceiling"):
+        # Kernel 3 alone, with the gather ceiling of an iteration on the same graph
         run_k3_only(args)
     elif args.stage == "batched":
         import torch
