@@ -778,7 +778,7 @@ def main():
     if args.impl == "ours" and args.tuning != "none":
         from paper_1603_01876_gb300 import tune
 
-        args.tuned = tune.apply(tune.DEFAULT_PATH if args.tuning == "default" else args.tuning)
+        args.tuned = tune.apply(tune.DEFAULT_PATH if args.tuning == "default" else args.tuning, scale=args.scale)
     if args.tune:
         import paper_1603_01876_gb300 as pp
 

@@ -7,10 +7,11 @@ unroll depth and the register budget, are measured on the GPU at hand: each sett
 warm-up) and the fastest setting is kept.  The single-vector search is a
 coordinate descent over the knobs (two rounds), the batched one a full grid.
 
-    python -m paper_1603_01876_gb300.tune --scale 24 --out paper_1603_01876_gb300/tuning/gb300.json
+    python -m paper_1603_01876_gb300.tune --scales 20,24,26 --out paper_1603_01876_gb300/tuning/gb300.json
 
-apply(path) sets the stored knobs in the library, if the file was measured on
-a GPU of the same name.  Every setting gives results within the stated
+The file keeps one entry per searched scale.  apply(path, scale=S) sets the
+knobs of the entry for scale S (the nearest searched scale at or below it)
+in the library, if the file was measured on a GPU of the same name.  Every setting gives results within the stated
 tolerances; the thresholds only change the order of some column sums.
 """
 import argparse
@@ -119,9 +120,28 @@ def tune_batched(graphs, r0, nrhs, iters=20, c=0.85, reps=3, warmup=1, knobs=Non
     return {"knobs": best, "ms": best_ms, "trials": len(list(itertools.product(*knobs.values())))}
 
 
-def apply(path=DEFAULT_PATH, device=None):
-    """Set the knobs stored in `path` if it was measured on this GPU's model;
-    returns the knobs set (empty if the file is missing or for another GPU)."""
+def entry_for_scale(data, scale):
+    """The stored single-graph entry for this scale: the exact scale if it was
+    searched, else the nearest searched scale below it (the smallest one for
+    smaller graphs)."""
+    single = data.get("single", {})
+    if "knobs" in single:  # a file with one entry
+        return single
+    scales = sorted(int(k) for k in single)
+    if not scales:
+        return {}
+    below = [x for x in scales if x <= scale] if scale is not None else []
+    pick = below[-1] if below else (scales[0] if scale is not None else max(scales))
+    if scale is None and 24 in scales:
+        pick = 24
+    return single[str(pick)]
+
+
+def apply(path=DEFAULT_PATH, device=None, scale=None):
+    """Set the knobs stored in `path` for graphs of this scale (the entry of
+    the nearest searched scale; scale None: the scale-24 entry), if the file
+    was measured on this GPU's model; returns the knobs set (empty if the
+    file is missing or for another GPU)."""
     import torch
 
     import paper_1603_01876_gb300 as pp
@@ -133,12 +153,26 @@ def apply(path=DEFAULT_PATH, device=None):
     name = torch.cuda.get_device_name(device)
     if data.get("device") != name:
         return {}
-    knobs = {}
-    for part in ("single", "batched"):
-        knobs.update(data.get(part, {}).get("knobs", {}))
+    knobs = dict(entry_for_scale(data, scale).get("knobs", {}))
+    knobs.update(data.get("batched", {}).get("knobs", {}))
     for k, v in knobs.items():
         pp.set_tuning(k, v)
     return knobs
+
+
+def _graph(scale, seed, dev):
+    import torch
+
+    import kernel0
+    import paper_1603_01876_gb300 as pp
+
+    u, v = kernel0.edges_device(scale, seed, device=dev)
+    us, vs = pp.sort_edges(u, v, scale)
+    del u, v
+    g = pp.build_filter_normalize(us, vs, scale, "lowest")
+    del us, vs
+    torch.cuda.empty_cache()
+    return g, torch.from_numpy(kernel0.r0_host(1 << scale, seed)).to(dev)
 
 
 def main(argv=None):
@@ -148,7 +182,7 @@ def main(argv=None):
     import paper_1603_01876_gb300 as pp
 
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("--scale", type=int, default=24)
+    ap.add_argument("--scales", default="20,24,26", help="graph scales to search, comma-separated")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--no-batched", action="store_true")
@@ -156,23 +190,22 @@ def main(argv=None):
     args = ap.parse_args(argv)
     dev = torch.device("cuda", 0)
     t0 = time.time()
-    N, M = 1 << args.scale, 16 << args.scale
-    u, v = kernel0.edges_device(args.scale, args.seed, device=dev)
-    us, vs = pp.sort_edges(u, v, args.scale)
-    del u, v
-    g = pp.build_filter_normalize(us, vs, args.scale, "lowest")
-    del us, vs
-    torch.cuda.empty_cache()
-    r0 = torch.from_numpy(kernel0.r0_host(N, args.seed)).to(dev)
-    result = {"device": torch.cuda.get_device_name(dev), "scale": args.scale, "edges": M, "iters": 20}
-    print("single-vector Kernel 3, binary32, scale %d" % args.scale)
-    result["single"] = tune_single(g, r0, reps=args.reps)
-    print("single-vector Kernel 3, binary64 unroll")
-    f64 = tune_single(g, r0, dtype="fp64", reps=max(1, args.reps - 1), knobs={"k3_unroll_f64": [4, 8]})
-    result["single"]["knobs"]["k3_unroll_f64"] = f64["knobs"]["k3_unroll_f64"]
-    result["single"]["ms_fp64"] = f64["ms"]
-    del g
-    torch.cuda.empty_cache()
+    result = {"device": torch.cuda.get_device_name(dev), "iters": 20, "single": {}}
+    for scale in [int(x) for x in args.scales.split(",")]:
+        g, r0 = _graph(scale, args.seed, dev)
+        print("single-vector Kernel 3, binary32, scale %d" % scale)
+        ent = tune_single(g, r0, reps=args.reps)
+        print("single-vector Kernel 3, binary64 unroll, scale %d" % scale)
+        shared = {k: v for k, v in ent["knobs"].items() if k != "k3_unroll_f32"}
+        f64 = _with_knobs(pp, shared, lambda: tune_single(g, r0, dtype="fp64", reps=max(1, args.reps - 1),
+                                                          knobs={"k3_unroll_f64": [4, 8]}))
+        ent["knobs"]["k3_unroll_f64"] = f64["knobs"]["k3_unroll_f64"]
+        ms = {"fp32": ent.pop("ms"), "fp64": f64["ms"]}
+        ent["ms_20_iterations"] = ms
+        ent["edges"] = g.M
+        result["single"][str(scale)] = ent
+        del g, r0
+        torch.cuda.empty_cache()
     if not args.no_batched:
         print("batched Kernel 3: 64 graphs of scales 12..18, 32 start vectors")
         scales = kernel0.batch_scales(64, 12, 18, seed=args.seed)

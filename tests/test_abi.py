@@ -111,18 +111,33 @@ def test_stored_tuning_file_is_accepted():
 
     with open(tune.DEFAULT_PATH) as f:
         data = json.load(f)
-    knobs = {}
-    for part in ("single", "batched"):
-        knobs.update(data[part]["knobs"])
+    entries = [data["single"]] if "knobs" in data["single"] else list(data["single"].values())
+    entries.append(data["batched"])
     searched = dict(tune.SINGLE_KNOBS, **tune.BATCH_KNOBS, k3_unroll_f64=[4, 8])
-    assert set(knobs) <= set(searched), set(knobs) - set(searched)
-    for k, values in searched.items():
-        old = pp.get_tuning(k)
-        try:
-            for v in values:
-                pp.set_tuning(k, v)
-            if k in knobs:
-                pp.set_tuning(k, knobs[k])
-                assert pp.get_tuning(k) == knobs[k]
-        finally:
-            pp.set_tuning(k, old)
+    for ent in entries:
+        knobs = ent["knobs"]
+        assert set(knobs) <= set(searched), set(knobs) - set(searched)
+        for k, values in searched.items():
+            old = pp.get_tuning(k)
+            try:
+                for v in values:
+                    pp.set_tuning(k, v)
+                if k in knobs:
+                    pp.set_tuning(k, knobs[k])
+                    assert pp.get_tuning(k) == knobs[k]
+            finally:
+                pp.set_tuning(k, old)
+
+
+def test_tuning_entry_for_scale():
+    """The stored entry applied to a graph is that of its scale, else of the
+    nearest searched scale below it (the smallest for smaller graphs)."""
+    from paper_1603_01876_gb300 import tune
+
+    data = {"single": {"20": {"knobs": {"a": 20}}, "24": {"knobs": {"a": 24}}, "26": {"knobs": {"a": 26}}}}
+    assert tune.entry_for_scale(data, 24)["knobs"]["a"] == 24
+    assert tune.entry_for_scale(data, 25)["knobs"]["a"] == 24
+    assert tune.entry_for_scale(data, 27)["knobs"]["a"] == 26
+    assert tune.entry_for_scale(data, 12)["knobs"]["a"] == 20
+    assert tune.entry_for_scale(data, None)["knobs"]["a"] == 24
+    assert tune.entry_for_scale({"single": {"knobs": {"a": 1}}}, 20)["knobs"]["a"] == 1

@@ -68,7 +68,7 @@ def fullsize(request):
     from paper_1603_01876_gb300 import tune
 
     saved = {k: pp.get_tuning(k) for k in list(tune.SINGLE_KNOBS) + list(tune.BATCH_KNOBS) + ["k3_unroll_f64"]}
-    tuned = tune.apply()
+    tuned = tune.apply(scale=scale)
     N, M = 1 << scale, 16 << scale
     dev = torch.device("cuda", 0)
     u, v = kernel0.edges_device(scale, SEED, device=dev)
