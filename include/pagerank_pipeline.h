@@ -227,6 +227,40 @@ pp_status pp_build_filter_normalize_batched(uint32_t n_graphs, const uint32_t *c
                                             void *stream);
 
 /*
+ * The local steps of the row-decomposed form of Kernels 1-3 (the paper's
+ * parallel implementations, Sec. IV-B to IV-D: each process owns a range of
+ * start vertices, i.e. of rows); the collectives between the steps are the
+ * caller's.
+ *
+ * pp_range_counts: counts[p] = the edges of u_sorted (M start vertices in
+ *   nondecreasing order) that lie in [bounds[p], bounds[p+1]), p < parts
+ *   (bounds: device uint32[parts+1]; counts: device uint64[parts]) -- the
+ *   split sizes of Kernel 1's exchange by start vertex range.
+ * pp_in_degree: d_in[v] = number of the M edges ending in v (device
+ *   uint32[2^scale], overwritten) -- the part of d_in = sum(A,1) that a
+ *   share of the rows contributes (Sec. IV-C step 2); an end vertex >= N
+ *   sets PP_DEV_RANGE and is skipped.
+ * pp_build_filter_normalize_rows: Kernel 2 on edges that hold every edge of
+ *   their start vertices (a share of the rows), with the in-degree of every
+ *   column of the whole graph supplied (d_in_all, device uint32[2^scale]):
+ *   the supernode and leaf filters and g->d_in use it, d_out and the matrix
+ *   are this share's.  Otherwise as pp_build_filter_normalize (same
+ *   workspace).
+ * pp_rank_update: r[i] = a * y[i] + b for i < n (binary64 or binary32 by
+ *   dtype), and *r_sum (device double) = the sum of the new r[i] in binary64
+ *   (a fixed order); r may equal y.  Workspace: 2048 bytes.
+ */
+pp_status pp_range_counts(const uint32_t *u_sorted, uint64_t M, const uint32_t *bounds, uint32_t parts,
+                          uint64_t *counts, void *stream);
+pp_status pp_in_degree(const uint32_t *v, uint64_t M, uint32_t scale, uint32_t *d_in, void *stream);
+pp_status pp_build_filter_normalize_rows(const uint32_t *u_sorted, const uint32_t *v_sorted, uint64_t M,
+                                         uint32_t scale, pp_supernode_rule rule, const uint32_t *d_in_all,
+                                         const pp_graph *g, void *workspace, size_t workspace_bytes,
+                                         void *stream);
+pp_status pp_rank_update(const void *y, uint64_t n, double a, double b, void *r, double *r_sum, pp_dtype dtype,
+                         void *workspace, size_t workspace_bytes, void *stream);
+
+/*
  * Kernel 2's filtered matrix A (Sec. IV-C step 4, A(i,:) = A(i,:) ./ d_out(i))
  * in compressed-row form, in vertex order: row u holds the entries of start
  * vertex u with their end vertices ascending.

@@ -86,6 +86,11 @@ def _lib():
             "pp_export_csr": [ctypes.POINTER(CGraph), vp, vp, vp, vp, vp, u64, vp, ctypes.c_size_t, vp],
             "pp_exec_destroy": [vp],
             "pp_gather_probe": [vp, u64, u32, vp, vp, vp],
+            "pp_range_counts": [vp, u64, vp, u32, vp, vp],
+            "pp_in_degree": [vp, u64, u32, vp, vp],
+            "pp_build_filter_normalize_rows": [vp, vp, u64, u32, i32, vp, ctypes.POINTER(CGraph), vp, ctypes.c_size_t,
+                                               vp],
+            "pp_rank_update": [vp, u64, dbl, dbl, vp, vp, i32, vp, ctypes.c_size_t, vp],
             "pp_sort_edges_batched_workspace": [u32, vp, vp, sz],
             "pp_sort_edges_batched": [u32, vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp],
             "pp_build_filter_normalize_batched_workspace": [u32, vp, vp, sz],
@@ -295,6 +300,48 @@ def gather_probe(graph, x, out, n=None, stream=None):
 
 
 BATCH_MAX_GRAPHS, BATCH_MAX_RHS = 128, 32
+
+
+def range_counts(us, bounds, stream=None):
+    """Edges of the sorted list us whose start vertex lies in each
+    [bounds[p], bounds[p+1]) (pp_range_counts); int64 device tensor."""
+    parts = bounds.numel() - 1
+    counts = torch.empty(parts, dtype=torch.int64, device=us.device)
+    _check("pp_range_counts", _lib().pp_range_counts(_ptr(us), us.numel(), _ptr(bounds), parts, _ptr(counts),
+                                                     _stream(stream, us.device)))
+    return counts
+
+
+def in_degree(vs, scale, out=None, stream=None):
+    """In-degree of an edge list, int32[2^scale] (pp_in_degree)."""
+    out = out if out is not None else torch.empty(1 << scale, dtype=torch.int32, device=vs.device)
+    _check("pp_in_degree", _lib().pp_in_degree(_ptr(vs), vs.numel(), scale, _ptr(out), _stream(stream, vs.device)))
+    return out
+
+
+def build_filter_normalize_rows(us, vs, scale, d_in_all, rule="lowest", graph=None, workspace=None, stream=None):
+    """Kernel 2 on a share of a graph's rows with the in-degree of every
+    column supplied (pp_build_filter_normalize_rows)."""
+    M = us.numel()
+    dev = us.device
+    g = graph if graph is not None else Graph(M, scale, dev)
+    need = workspace_bytes("build", M, scale)
+    ws = workspace if workspace is not None and workspace.numel() >= need else _workspace(need, dev)
+    st = _lib().pp_build_filter_normalize_rows(_ptr(us), _ptr(vs), M, scale, RULES[rule], _ptr(d_in_all),
+                                               ctypes.byref(g.c), _ptr(ws), ws.numel(), _stream(stream, dev))
+    _check("pp_build_filter_normalize_rows", st)
+    return g
+
+
+def rank_update(y, a, b, r, workspace=None, stream=None):
+    """r = a * y + b elementwise (pp_rank_update, binary64 or binary32 by
+    dtype); returns sum(r) as a float64 device tensor of one element."""
+    dt = {torch.float64: 0, torch.float32: 1}[y.dtype]
+    out = torch.empty(1, dtype=torch.float64, device=y.device)
+    ws = workspace if workspace is not None and workspace.numel() >= 2048 else _workspace(2048, y.device)
+    _check("pp_rank_update", _lib().pp_rank_update(_ptr(y), y.numel(), float(a), float(b), _ptr(r), _ptr(out), dt,
+                                                   _ptr(ws), ws.numel(), _stream(stream, y.device)))
+    return out
 
 
 def _ptr_array(tensors):

@@ -882,8 +882,16 @@ struct BatchCtx {
 };
 
 // Kernel 2 on sorted (us, vs) into g; a batch runs it on the union of its graphs.
+// The in-degree the column filters test: the graph's own, or (d_in_all) one
+// supplied for every column when this call holds only some rows of a graph.
+__global__ void __launch_bounds__(256) set_d_in_kernel(unsigned long long *deg, const uint32_t *d_in_all, uint32_t N) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x)
+        deg[v] = (deg[v] & 0xffffffff00000000ull) | d_in_all[v];
+}
+
 inline pp_status run(const uint32_t *us, const uint32_t *vs, uint64_t M, uint32_t scale, pp_supernode_rule rule,
-                     const pp_graph *g, const Layout &L, cudaStream_t s, const BatchCtx *bc) {
+                     const pp_graph *g, const Layout &L, cudaStream_t s, const BatchCtx *bc,
+                     const uint32_t *d_in_all = nullptr) {
     const uint32_t N = 1u << scale;
     const uint32_t cmax = (uint32_t)((1ull << (32 - scale)) - 1);
     const int P = k2::num_passes(scale);
@@ -966,6 +974,10 @@ inline pp_status run(const uint32_t *us, const uint32_t *vs, uint64_t M, uint32_
                                                  L.deg);
         count_launch();
     }
+    if (d_in_all) {
+        k2::set_d_in_kernel<<<ngrid, 256, 0, s>>>(L.deg, d_in_all, N);
+        count_launch();
+    }
     if (!bc)
         k2::dmax_kernel<<<ngrid, 256, 0, s>>>(L.deg, N, g->d_in, L.dmaxkey);
     else
@@ -1016,6 +1028,23 @@ extern "C" pp_status pp_build_filter_normalize(const uint32_t *us, const uint32_
     if (st != PP_OK) return st;
     const k2::Layout L = k2::layout(ws, M, scale);
     return k2::run(us, vs, M, scale, rule, g, L, static_cast<cudaStream_t>(stream), nullptr);
+}
+
+extern "C" pp_status pp_build_filter_normalize_rows(const uint32_t *us, const uint32_t *vs, uint64_t M,
+                                                    uint32_t scale, pp_supernode_rule rule, const uint32_t *d_in_all,
+                                                    const pp_graph *g, void *ws, size_t ws_bytes, void *stream) {
+    if (scale < 1 || scale > 27 || M > (1ull << 31) || !g || !d_in_all) return PP_ERR_INVALID_ARG;
+    if (rule != PP_SUPERNODE_LOWEST && rule != PP_SUPERNODE_ALL_TIES) return PP_ERR_INVALID_ARG;
+    if (g->scale != scale || g->M != M) return PP_ERR_INVALID_ARG;
+    if (!g->colptr || !g->rowc || !g->ovf_key || !g->ovf_cnt || !g->d_in || !g->d_out || !g->info || !g->perm ||
+        !g->iperm)
+        return PP_ERR_INVALID_ARG;
+    if (M && (!us || !vs)) return PP_ERR_INVALID_ARG;
+    const k2::Layout need = k2::layout(nullptr, M, scale);
+    pp_status st = check_ws(ws, ws_bytes, need.bytes);
+    if (st != PP_OK) return st;
+    const k2::Layout L = k2::layout(ws, M, scale);
+    return k2::run(us, vs, M, scale, rule, g, L, static_cast<cudaStream_t>(stream), nullptr, d_in_all);
 }
 
 // ---------------------------------------------------------------------------

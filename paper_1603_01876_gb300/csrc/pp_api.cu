@@ -13,6 +13,7 @@ uint32_t k3_fetch_error(cudaStream_t s);
 uint32_t k3b_fetch_error(cudaStream_t s);
 uint32_t tsv_fetch_error(cudaStream_t s);
 uint32_t kx_fetch_error(cudaStream_t s);
+uint32_t kr_fetch_error(cudaStream_t s);
 }  // namespace pp
 
 namespace pp {
@@ -84,8 +85,8 @@ extern "C" pp_status pp_last_device_error(void *stream, uint32_t *code) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (cudaStreamSynchronize(s) != cudaSuccess) return PP_ERR_CUDA;
     uint32_t w = 0;
-    const uint32_t parts[6] = {k1_fetch_error(s), k2_fetch_error(s), k3_fetch_error(s), k3b_fetch_error(s),
-                               tsv_fetch_error(s), kx_fetch_error(s)};
+    const uint32_t parts[7] = {k1_fetch_error(s), k2_fetch_error(s), k3_fetch_error(s), k3b_fetch_error(s),
+                               tsv_fetch_error(s), kx_fetch_error(s), kr_fetch_error(s)};
     for (uint32_t p : parts) {
         if (p == 0xffffffffu) return PP_ERR_CUDA;
         w |= p;
