@@ -449,6 +449,10 @@ def run_ours(args):
                                  "gbs": k3_bytes_per_iter(nnz, N, "fp16") * iters / k3_h / 1e6},
             "k3_iteration": {"ms": iter_ms, "setup_ms": k3_setup},
         },
+        "binary64_step": {"ms": med(k1) + med(k2) + k3_64,
+                          "edges_per_s": job_rate(M, world, med(k1) + med(k2) + k3_64),
+                          "how": "Kernels 1 and 2 of the timed steps plus Kernel 3 in binary64 (the paper's "
+                                 "language-default precision), each timed with CUDA events"},
         "k3_variants": variants,
         "k1_files": files,
         "accuracy": {"fp32_vs_gpu_fp64_l1": l1_fp32, "fp32_vs_gpu_fp64_max_rel": maxrel_fp32,
