@@ -65,6 +65,8 @@ typedef enum {
 #define PP_DEV_TIMEOUT 2u /* a bounded cross-block wait expired; outputs are invalid */
 #define PP_DEV_PARSE 4u   /* edge-file text was malformed (pp_parse_tsv) */
 #define PP_DEV_CAPACITY 8u /* an output array was too short for the result (pp_export_csr) */
+#define PP_DEV_BOUNDS 16u  /* checked build only: an index read or computed by a kernel
+                              was outside the array it addresses; outputs are invalid */
 
 /* Slots of pp_graph.info (device uint64[PP_INFO_LEN]), written by Kernel 2. */
 #define PP_INFO_NNZ0 0       /* nonzeros of A before the column filters */
@@ -437,6 +439,18 @@ pp_status pp_gather_probe(const uint32_t *rowc, uint64_t n, uint32_t scale, cons
  * PP_DEV_* bit set) of the current device in *code.  Returns PP_ERR_DEVICE if
  * the word was non-zero, PP_ERR_CUDA if synchronisation failed, else PP_OK. */
 pp_status pp_last_device_error(void *stream, uint32_t *code);
+
+/* How this library was compiled: PP_BUILD_CHECKED is set in the bounds-checked
+ * build (libpp_checked.so), whose kernels compare every index they read from
+ * memory, or compute from what they read, with the length of the array it
+ * addresses; an index out of range records PP_DEV_BOUNDS and the access goes
+ * to element 0 of that array instead (no trap).  Same entry points and
+ * results as libpp.so, somewhat slower.  Every call also opens an NVTX range
+ * named after it unless the library was built with -DPP_NO_NVTX
+ * (PP_BUILD_NVTX). */
+#define PP_BUILD_CHECKED 1u
+#define PP_BUILD_NVTX 2u
+uint32_t pp_build_flags(void);
 
 /* A short English description of a status code (static storage). */
 const char *pp_status_string(pp_status status);

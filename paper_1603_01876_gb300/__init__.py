@@ -20,6 +20,10 @@ import torch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpp.so")
+# The bounds-checked build of the same sources (PP_DEV_BOUNDS instead of an
+# out-of-range access); PP_LIBRARY=checked in the environment selects it.
+LIB_PATHS = {"default": LIB_PATH, "checked": os.path.join(HERE, "libpp_checked.so")}
+BUILD_CHECKED, BUILD_NVTX = 1, 2
 
 PP_OK, PP_ERR_INVALID_ARG, PP_ERR_WORKSPACE, PP_ERR_CUDA, PP_ERR_DEVICE = range(5)
 DTYPES = {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3}
@@ -27,7 +31,7 @@ RULES = {"lowest": 0, "all_ties": 1}
 INFO = {"nnz0": 0, "nnz": 1, "dmax": 2, "vmax": 3, "ties": 4, "novf": 5, "supernodes": 6}
 INFO_LEN = 8
 GRAPH_ARRAYS = 11
-DEV_RANGE, DEV_TIMEOUT, DEV_PARSE, DEV_CAPACITY = 1, 2, 4, 8
+DEV_RANGE, DEV_TIMEOUT, DEV_PARSE, DEV_CAPACITY, DEV_BOUNDS = 1, 2, 4, 8, 16
 
 
 class PPError(RuntimeError):
@@ -47,15 +51,32 @@ class CGraph(ctypes.Structure):
     ]
 
 
-_L = None
+_LIBS = {}
+_ACTIVE = os.environ.get("PP_LIBRARY", "default")
+
+
+def use_library(kind):
+    """Selects the library later calls go through: "default" (libpp.so) or
+    "checked" (libpp_checked.so); returns the previous choice.  Graphs and
+    workspaces are plain device memory and may be passed between the two;
+    tuning knobs are kept per library."""
+    global _ACTIVE
+    if kind not in LIB_PATHS:
+        raise ValueError("unknown library %r" % (kind,))
+    prev, _ACTIVE = _ACTIVE, kind
+    return prev
 
 
 def _lib():
-    global _L
-    if _L is None:
-        if not os.path.exists(LIB_PATH):
-            raise ImportError("libpp.so is not built (run __graft_entry__.build()); there is no CPU fallback")
-        L = ctypes.CDLL(LIB_PATH)
+    L = _LIBS.get(_ACTIVE)
+    if L is None:
+        path = LIB_PATHS.get(_ACTIVE)
+        if path is None:
+            raise ImportError("PP_LIBRARY=%r names no library (default or checked)" % (_ACTIVE,))
+        if not os.path.exists(path):
+            raise ImportError("%s is not built (run __graft_entry__.build()); there is no CPU fallback"
+                              % os.path.basename(path))
+        L = ctypes.CDLL(path)
         vp, u32, u64, sz = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.POINTER(ctypes.c_size_t)
         i32, dbl = ctypes.c_int, ctypes.c_double
         sig = {
@@ -111,12 +132,19 @@ def _lib():
         L.pp_get_tuning.restype = ctypes.c_int
         L.pp_launch_count.argtypes = []
         L.pp_launch_count.restype = ctypes.c_uint64
-        _L = L
-    return _L
+        L.pp_build_flags.argtypes = []
+        L.pp_build_flags.restype = ctypes.c_uint32
+        _LIBS[_ACTIVE] = L
+    return L
 
 
 def lib():
     return _lib()
+
+
+def build_flags():
+    """BUILD_CHECKED | BUILD_NVTX bits of the library in use."""
+    return int(_lib().pp_build_flags())
 
 
 def _check(fn, st):
@@ -203,21 +231,25 @@ def workspace_bytes(kind, M, scale, iters=20, dtype="fp32"):
 class Graph:
     """Kernel 2's output (device tensors) and the C struct that points at them."""
 
-    def __init__(self, M, scale, device):
+    def __init__(self, M, scale, device, alloc=None):
+        """alloc(n, dtype) -> device tensor of n elements, if given, provides
+        the arrays (e.g. placed inside larger buffers)."""
         lens = graph_lengths(M, scale)
         i32, i64 = torch.int32, torch.int64
+        new = alloc or (lambda n, dt: torch.empty(n, dtype=dt, device=device))
         self.M, self.scale, self.N = M, scale, 1 << scale
-        self.colptr = torch.empty(lens[0], dtype=i32, device=device)
-        self.rowc = torch.empty(lens[1], dtype=i32, device=device)
-        self.ovf_key = torch.empty(lens[2], dtype=i64, device=device)
-        self.ovf_cnt = torch.empty(lens[3], dtype=i32, device=device)
-        self.d_in = torch.empty(lens[4], dtype=i32, device=device)
-        self.d_out = torch.empty(lens[5], dtype=i32, device=device)
-        self.inv_dout32 = torch.empty(lens[6], dtype=torch.float32, device=device)
-        self.inv_dout64 = torch.empty(lens[7], dtype=torch.float64, device=device)
-        self.info = torch.zeros(lens[8], dtype=i64, device=device)
-        self.perm = torch.empty(lens[9], dtype=i32, device=device)
-        self.iperm = torch.empty(lens[10], dtype=i32, device=device)
+        self.colptr = new(lens[0], i32)
+        self.rowc = new(lens[1], i32)
+        self.ovf_key = new(lens[2], i64)
+        self.ovf_cnt = new(lens[3], i32)
+        self.d_in = new(lens[4], i32)
+        self.d_out = new(lens[5], i32)
+        self.inv_dout32 = new(lens[6], torch.float32)
+        self.inv_dout64 = new(lens[7], torch.float64)
+        self.info = new(lens[8], i64)
+        self.info.zero_()
+        self.perm = new(lens[9], i32)
+        self.iperm = new(lens[10], i32)
         self.c = CGraph(scale, 0, M, self.colptr.data_ptr(), self.rowc.data_ptr(), self.ovf_key.data_ptr(),
                         self.ovf_cnt.data_ptr(), self.d_in.data_ptr(), self.d_out.data_ptr(),
                         self.inv_dout32.data_ptr(), self.inv_dout64.data_ptr(), self.info.data_ptr(),

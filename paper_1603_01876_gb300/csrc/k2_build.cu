@@ -261,10 +261,13 @@ __global__ void __launch_bounds__(UQ_THREADS, 3) unique_kernel(UniqueArgs a) {
             if (!(valid >> j & 1u)) continue;
             const uint32_t u = (uint32_t)(k[j] >> 32), v = (uint32_t)k[j];
             const uint32_t field = c >= a.cmax ? a.cmax : c;
-            s_out[lpos + lpos / 16] = ((unsigned long long)v << 32) | (u | (field << a.scale));
+            const uint32_t lp = pp_idx(lpos, (uint32_t)UQ_TILE);
+            s_out[lp + lp / 16] = ((unsigned long long)v << 32) | (u | (field << a.scale));
             if (c >= a.cmax) {
-                a.ovf_key[epos] = ((uint64_t)u << 32) | v;
-                a.ovf_cnt[epos] = c;
+                // the overflow table holds M / cmax + 1 entries
+                const uint64_t eo = pp_idx(epos, a.M / a.cmax + 1);
+                a.ovf_key[eo] = ((uint64_t)u << 32) | v;
+                a.ovf_cnt[eo] = c;
                 ++epos;
             }
             for (int p = 0; p < a.npasses; ++p) atomicAdd(&s_hist[p][(v >> (8 * p)) & (os::RADIX - 1)], 1u);
@@ -279,7 +282,8 @@ __global__ void __launch_bounds__(UQ_THREADS, 3) unique_kernel(UniqueArgs a) {
             for (uint32_t i = tid; i < n_out; i += UQ_THREADS) {
                 const unsigned long long w = s_out[i + i / 16];
                 const uint32_t u = (uint32_t)w & umask;
-                a.ent[first + i + __ldg(a.delta + u)] = (w & ~(unsigned long long)umask) | __ldg(a.perm + u);
+                a.ent[pp_idx((uint32_t)(first + i + __ldg(a.delta + u)), a.M)] =
+                    (w & ~(unsigned long long)umask) | __ldg(a.perm + u);
             }
         }
         __syncthreads();  // shared scratch is reused by the next tile
@@ -374,7 +378,7 @@ __global__ void __launch_bounds__(SC_THREADS) offsets_kernel(OffArgs a) {
         who[j] = 0;
         cnt[j] = 0;
         if (p < a.N) {
-            who[j] = a.iperm ? a.iperm[p] : (uint32_t)p;
+            who[j] = a.iperm ? pp_idx(a.iperm[p], a.N) : (uint32_t)p;
             cnt[j] = a.row_nent[who[j]];
         }
         sum += cnt[j];
@@ -427,7 +431,7 @@ __global__ void __launch_bounds__(256) colscan_kernel(const unsigned long long *
         for (int j = 0; j < CS_ITEMS; ++j) {
             if (i0 + j < n) {
                 const unsigned long long e = s[tid * (CS_ITEMS + 1) + j];
-                const uint32_t v = (uint32_t)(e >> 32), w = (uint32_t)e;
+                const uint32_t v = pp_idx((uint32_t)(e >> 32), umask + 1ull), w = (uint32_t)e;
                 uint32_t c = w >> scale;
                 if (c == cmax) c = ovf_lookup(ovf_key, ovf_cnt, novf, ((uint64_t)iperm[w & umask] << 32) | v);
                 if (v != col) {
@@ -465,19 +469,21 @@ __global__ void __launch_bounds__(256) compact_kernel(const unsigned long long *
 #pragma unroll
         for (int q = 0; q < CP_ITEMS; ++q) e[q] = (b + 256 * q < n) ? ent[b + 256 * q] : 0ull;
 #pragma unroll
-        for (int q = 0; q < CP_ITEMS; ++q) sv[q] = (b + 256 * q < n) ? vstart[(uint32_t)(e[q] >> 32)] : 0u;
+        for (int q = 0; q < CP_ITEMS; ++q)
+            sv[q] = (b + 256 * q < n) ? vstart[pp_idx((uint32_t)(e[q] >> 32), umask + 1ull)] : 0u;
 #pragma unroll
         for (int q = 0; q < CP_ITEMS; ++q) {
             const uint64_t i = b + 256 * q;
             if (i >= n) break;
-            const uint32_t v = (uint32_t)(e[q] >> 32), w = (uint32_t)e[q];
+            const uint32_t v = pp_idx((uint32_t)(e[q] >> 32), umask + 1ull), w = (uint32_t)e[q];
             if (sv[q] & KILL_BIT) {
-                const uint32_t u = iperm[w & umask];
+                const uint32_t u = pp_idx(iperm[w & umask], umask + 1ull);
                 uint32_t c = w >> scale;
                 if (c == cmax) c = ovf_lookup(ovf_key, ovf_cnt, novf, ((uint64_t)u << 32) | v);
                 atomicSub(&d_out[u], c);
             } else {
-                rowc[__ldg(colptr + __ldg(perm + v)) + ((uint32_t)i - sv[q])] = w;
+                // rowc holds nnz <= nnz0 = n words
+                rowc[pp_idx(__ldg(colptr + pp_idx(__ldg(perm + v), umask + 1ull)) + ((uint32_t)i - sv[q]), n)] = w;
             }
         }
     }
@@ -682,7 +688,7 @@ __global__ void __launch_bounds__(SC_THREADS) pos_scan_kernel(PosArgs a) {
     for (int j = 0; j < SC_ITEMS; ++j) {
         kept[j] = 0;
         if (p0 + j < a.N) {
-            const uint32_t v = a.iperm[p0 + j];
+            const uint32_t v = pp_idx(a.iperm[p0 + j], a.N);
             kept[j] = (a.vstart[v] & KILL_BIT) ? 0u : (uint32_t)(a.deg[v] >> 32);
         }
         sum += kept[j];
@@ -743,10 +749,11 @@ struct VertexSrc {
 };
 struct PermDst {
     uint32_t *perm, *iperm;
+    uint32_t N;
     __device__ __forceinline__ void store(uint64_t pos, uint32_t k, uint32_t) const {
         const uint32_t u = k & ((1u << VKEY_SHIFT) - 1u);
         iperm[pos] = u;
-        perm[u] = (uint32_t)pos;
+        perm[pp_idx(u, N)] = (uint32_t)pos;
     }
 };
 
@@ -780,10 +787,11 @@ struct VKeyDst {
 };
 struct PermDst64 {
     uint32_t *perm, *iperm;
+    uint32_t N;
     __device__ __forceinline__ void store(uint64_t pos, unsigned long long key, uint32_t) const {
         const uint32_t u = (uint32_t)key;
         iperm[pos] = u;
-        perm[u] = (uint32_t)pos;
+        perm[pp_idx(u, N)] = (uint32_t)pos;
     }
 };
 
@@ -928,7 +936,7 @@ inline pp_status run(const uint32_t *us, const uint32_t *vs, uint64_t M, uint32_
                                                       static_cast<uint32_t *>(L.vsort.status[0]),
                                                       vtiles * os::RADIX * vword / 4);
         count_launch();
-        os::launch_pass<uint32_t>(L.vsort, 0, 1, k2::VertexSrc{g->d_out}, k2::PermDst{g->perm, g->iperm}, nullptr, N,
+        os::launch_pass<uint32_t>(L.vsort, 0, 1, k2::VertexSrc{g->d_out}, k2::PermDst{g->perm, g->iperm, N}, nullptr, N,
                                   s, k2::VKEY_SHIFT);
     } else {
         // graph-major: (graph, bucket) in two 8-bit passes over bits 32..47 of the vertex keys
@@ -940,7 +948,7 @@ inline pp_status run(const uint32_t *us, const uint32_t *vs, uint64_t M, uint32_
         os::launch_pass<unsigned long long>(L.vsort, 0, 2, k2::VKeySrc{bc->vkey[0]}, k2::VKeyDst{bc->vkey[1]}, nullptr,
                                             N, s, 32u);
         os::launch_pass<unsigned long long>(L.vsort, 1, 2, k2::VKeySrc{bc->vkey[1]},
-                                            k2::PermDst64{g->perm, g->iperm}, nullptr, N, s, 32u);
+                                            k2::PermDst64{g->perm, g->iperm, N}, nullptr, N, s, 32u);
     }
     if (M) {
         // each row's first entry in vertex order, then in position order
@@ -1016,6 +1024,7 @@ inline pp_status run(const uint32_t *us, const uint32_t *vs, uint64_t M, uint32_
 extern "C" pp_status pp_build_filter_normalize(const uint32_t *us, const uint32_t *vs, uint64_t M,
                                                uint32_t scale, pp_supernode_rule rule, const pp_graph *g,
                                                void *ws, size_t ws_bytes, void *stream) {
+    PP_RANGE("pp_build_filter_normalize");
     if (scale < 1 || scale > 27 || M > (1ull << 31) || !g) return PP_ERR_INVALID_ARG;
     if (rule != PP_SUPERNODE_LOWEST && rule != PP_SUPERNODE_ALL_TIES) return PP_ERR_INVALID_ARG;
     if (g->scale != scale || g->M != M) return PP_ERR_INVALID_ARG;
@@ -1033,6 +1042,7 @@ extern "C" pp_status pp_build_filter_normalize(const uint32_t *us, const uint32_
 extern "C" pp_status pp_build_filter_normalize_rows(const uint32_t *us, const uint32_t *vs, uint64_t M,
                                                     uint32_t scale, pp_supernode_rule rule, const uint32_t *d_in_all,
                                                     const pp_graph *g, void *ws, size_t ws_bytes, void *stream) {
+    PP_RANGE("pp_build_filter_normalize_rows");
     if (scale < 1 || scale > 27 || M > (1ull << 31) || !g || !d_in_all) return PP_ERR_INVALID_ARG;
     if (rule != PP_SUPERNODE_LOWEST && rule != PP_SUPERNODE_ALL_TIES) return PP_ERR_INVALID_ARG;
     if (g->scale != scale || g->M != M) return PP_ERR_INVALID_ARG;
@@ -1172,13 +1182,14 @@ __global__ void __launch_bounds__(256) split_entry_kernel(SplitArgs a) {
         const uint32_t base = a.vbase[g], sg = a.out[g].scale;
         const uint32_t cmaxg = (uint32_t)((1ull << (32 - sg)) - 1);
         const uint32_t s = a.colptr[q], e = a.colptr[q + 1], d0 = s - a.colptr[base];
-        uint32_t *dst = a.out[g].rowc + d0;
+        uint32_t *dst = a.out[g].rowc;
+        const uint64_t mg = a.out[g].M ? a.out[g].M : 1, mu = a.info[PP_INFO_NNZ];
         for (uint32_t k = lane; k < e - s; k += 32) {
-            const uint32_t w = a.rowc[s + k];
+            const uint32_t w = a.rowc[pp_idx(s + k, mu)];
             const uint32_t pos = w & umaskU;
             uint32_t c = w >> a.S;
             if (c == a.cmaxU) c = ovf_find(a.ovf_key, a.ovf_cnt, novf, ((uint64_t)a.iperm[pos] << 32) | a.iperm[q]);
-            dst[k] = ((c >= cmaxg ? cmaxg : c) << sg) | (pos - base);
+            dst[pp_idx(d0 + k, mg)] = ((c >= cmaxg ? cmaxg : c) << sg) | (pos - base);
         }
     }
 }
@@ -1204,8 +1215,9 @@ __global__ void __launch_bounds__(128) split_ovf_kernel(SplitArgs a) {
     for (uint64_t i = lo; i < novf && (uint32_t)(a.ovf_key[i] >> 32) < end; ++i) {
         if (a.ovf_cnt[i] < cmaxg) continue;
         const uint64_t key = a.ovf_key[i];
-        a.out[g].ovf_key[k] = ((uint64_t)((uint32_t)(key >> 32) - base) << 32) | (uint32_t)((uint32_t)key - base);
-        a.out[g].ovf_cnt[k] = a.ovf_cnt[i];
+        const uint64_t ko = pp_idx(k, a.out[g].M / cmaxg + 1);  // the graph's table length
+        a.out[g].ovf_key[ko] = ((uint64_t)((uint32_t)(key >> 32) - base) << 32) | (uint32_t)((uint32_t)key - base);
+        a.out[g].ovf_cnt[ko] = a.ovf_cnt[i];
         ++k;
     }
     a.out[g].info[PP_INFO_NOVF] = k;
@@ -1310,6 +1322,7 @@ extern "C" pp_status pp_build_filter_normalize_batched(uint32_t n_graphs, const 
                                                        const uint32_t *const *v_sorted, pp_supernode_rule rule,
                                                        const pp_graph *gs, void *ws, size_t ws_bytes,
                                                        void *stream) {
+    PP_RANGE("pp_build_filter_normalize_batched");
     if (!gs || !u_sorted || !v_sorted || n_graphs < 1 || n_graphs > (uint32_t)k2b::MAX_G) return PP_ERR_INVALID_ARG;
     if (rule != PP_SUPERNODE_LOWEST && rule != PP_SUPERNODE_ALL_TIES) return PP_ERR_INVALID_ARG;
     uint64_t M[k2b::MAX_G];

@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) col_len_kernel(const uint32_t *c
     for (int j = 0; j < SCAN_ITEMS; ++j) {
         const uint64_t v = v0 + j;
         if (v < N) {
-            const uint32_t p = __ldg(perm + v);
+            const uint32_t p = pp_idx(__ldg(perm + v), N);
             const uint32_t l = __ldg(colptr + p + 1) - __ldg(colptr + p);
             len[v] = l;
             sum += l;
@@ -97,14 +97,16 @@ __global__ void __launch_bounds__(SCAN_THREADS) col_off_kernel(uint32_t *len, ui
 // field << scale | v), written from the vertex's first word on.
 __global__ void __launch_bounds__(256) emit_kernel(const uint32_t *colptr, const uint32_t *rowc, const uint32_t *perm,
                                                    const uint32_t *iperm, uint32_t N, uint32_t scale,
-                                                   const uint32_t *voff, uint64_t *words) {
+                                                   const uint32_t *voff, const uint64_t *info, uint64_t *words) {
     const int lane = threadIdx.x & 31;
     const uint32_t umask = (1u << scale) - 1u;
     const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x / 32);
     for (uint64_t v = (uint64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); v < N; v += nw) {
-        const uint32_t p = __ldg(perm + v);
-        const uint32_t s = __ldg(colptr + p), len = __ldg(colptr + p + 1) - s;
+        const uint32_t p = pp_idx(__ldg(perm + v), N);
+        const uint32_t s = __ldg(colptr + p);
         const uint64_t o = __ldg(voff + v);
+        // rowc and words both hold nnz entries
+        const uint32_t len = pp_len(o, pp_len(s, __ldg(colptr + p + 1) - s, info[PP_INFO_NNZ]), info[PP_INFO_NNZ]);
         for (uint32_t k = lane; k < len; k += 32) {
             const uint32_t w = __ldg(rowc + s + k);
             const uint32_t u = __ldg(iperm + (w & umask));
@@ -152,7 +154,7 @@ __global__ void __launch_bounds__(256) finish_kernel(FinishArgs a) {
         for (uint64_t u = gtid; u <= a.N; u += stride) a.rowptr[u] = 0;
     for (uint64_t i = gtid; i < nnz; i += stride) {
         const uint64_t w = a.words[i];
-        const uint32_t u = (uint32_t)(w >> 32), lo = (uint32_t)w;
+        const uint32_t u = pp_idx((uint32_t)(w >> 32), a.N), lo = (uint32_t)w;
         const uint32_t v = lo & umask;
         if (room) {
             uint32_t c = lo >> a.scale;
@@ -207,6 +209,7 @@ extern "C" pp_status pp_export_csr_workspace(uint64_t M, uint32_t scale, size_t 
 extern "C" pp_status pp_export_csr(const pp_graph *g, uint64_t *rowptr, uint32_t *col, uint32_t *cnt,
                                    double *val64, float *val32, uint64_t cap, void *ws, size_t ws_bytes,
                                    void *stream) {
+    PP_RANGE("pp_export_csr");
     if (!g || !rowptr || (cap > 0 && (!col || !cnt))) return PP_ERR_INVALID_ARG;
     if (g->scale < 1 || g->scale > 27 || g->M > (1ull << 31)) return PP_ERR_INVALID_ARG;
     if (!g->colptr || !g->rowc || !g->ovf_key || !g->ovf_cnt || !g->d_out || !g->info || !g->perm || !g->iperm)
@@ -222,7 +225,7 @@ extern "C" pp_status pp_export_csr(const pp_graph *g, uint64_t *rowptr, uint32_t
     kx::tile_scan_kernel<<<1, kx::TOP_THREADS, 0, s>>>(L.tile_sum, ntiles);
     kx::col_off_kernel<<<ntiles, kx::SCAN_THREADS, 0, s>>>(L.voff, N, L.tile_sum);
     const unsigned egrid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(ceil_div(N, 8), 64ull * sm_count()));
-    kx::emit_kernel<<<egrid, 256, 0, s>>>(g->colptr, g->rowc, g->perm, g->iperm, N, g->scale, L.voff, L.words[0]);
+    kx::emit_kernel<<<egrid, 256, 0, s>>>(g->colptr, g->rowc, g->perm, g->iperm, N, g->scale, L.voff, g->info, L.words[0]);
     count_launch(4);
     // stable sort of the words by u (bits 32 .. 32 + scale), nnz of them
     const uint64_t *n_dev = g->info + PP_INFO_NNZ;

@@ -66,7 +66,8 @@ struct BG {
 
 struct Desc {
     BG g[MAXG];
-    uint32_t ng, nrhs, iters, pad;
+    uint32_t ng, nrhs, iters;
+    uint32_t item_cap;  // entries of the item arrays (bounds of the checked build)
     uint32_t shortmax;  // columns longer than this are cut into chunks (power of two)
     uint32_t chunk;     // entries of a long column per work item
     uint64_t rows;  // rows of all graphs together
@@ -181,7 +182,7 @@ __global__ void __launch_bounds__(256) normalize_kernel(const __grid_constant__ 
         const double rnorm = 1.0 / w.norm[g * 32 + lane];  // a multiply per element, not a division
         for (uint64_t p = r_begin + warp; p < r_end; p += WARPS) {
             // storage position p holds vertex v; r0 and r_out are in vertex order
-            const uint32_t v = __ldg(G.iperm + p);
+            const uint32_t v = pp_idx(__ldg(G.iperm + p), G.N);
             const uint64_t at = (G.row0 + v) * d.nrhs + lane;
             const float r = (float)(r0[at] * rnorm);
             fx_add(acc, r, 1);
@@ -271,8 +272,9 @@ __global__ void __launch_bounds__(PLAN_THREADS) plan_kernel(const __grid_constan
     for (int j = 0; j < PLAN_ITEMS; ++j) {
         if (!(bmask >> j & 1u)) continue;
         const uint64_t gc = c0 + j;
-        w.bound[bi] = (uint32_t)gc;
-        w.bound_item[bi] = ii;
+        const uint32_t bo = pp_idx(bi, d.rows);
+        w.bound[bo] = (uint32_t)gc;
+        w.bound_item[bo] = ii;
         const int g = graph_of(d, gc);
         const uint32_t v = (uint32_t)(gc - d.g[g].row0);
         if (v == 0) w.first_item[g] = ii;
@@ -294,16 +296,18 @@ __global__ void __launch_bounds__(256) plan_items_kernel(const __grid_constant__
             const uint32_t nc = (e - s + d.chunk - 1) / d.chunk;
             for (uint32_t k = 0; k < nc; ++k) {
                 const uint32_t cs = s + k * d.chunk;
-                w.item[o + k] = make_uint4(v | LONG_FLAG, o, cs, min(d.chunk, e - cs) | (nc << 12));
-                w.item_g[o + k] = (uint8_t)g;
-                w.ticket[o + k] = 0;
+                const uint32_t oi = pp_idx(o + k, d.item_cap);
+                w.item[oi] = make_uint4(v | LONG_FLAG, o, cs, min(d.chunk, e - cs) | (nc << 12));
+                w.item_g[oi] = (uint8_t)g;
+                w.ticket[oi] = 0;
             }
         } else {
             // the tile runs to the next boundary of the same graph, or to the graph's end
             uint32_t c1 = G.N;
             if (i + 1 < nb && w.bound[i + 1] < G.row0 + G.N) c1 = (uint32_t)(w.bound[i + 1] - G.row0);
-            w.item[o] = make_uint4(v, c1 - v, s, __ldg(G.colptr + c1) - s);
-            w.item_g[o] = (uint8_t)g;
+            const uint32_t oi = pp_idx(o, d.item_cap);
+            w.item[oi] = make_uint4(v, c1 - v, s, __ldg(G.colptr + c1) - s);
+            w.item_g[oi] = (uint8_t)g;
         }
     }
 }
@@ -331,7 +335,7 @@ __global__ void __launch_bounds__(THREADS) iterate_kernel(const __grid_constant_
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool active = lane < (int)d.nrhs;
     const uint32_t nrhs = d.nrhs;
-    const uint32_t n_items = w.ctl[0];
+    const uint32_t n_items = pp_len(0, w.ctl[0], d.item_cap);
     const uint32_t nwarps = gridDim.x * WARPS;
     const float cc = (float)d.c;
     const uint64_t keep = policy_evict_last(), stream = policy_evict_first();
@@ -346,7 +350,7 @@ __global__ void __launch_bounds__(THREADS) iterate_kernel(const __grid_constant_
     int E = 1;
     for (uint32_t item = blockIdx.x * WARPS + warp; item < n_items; item += nwarps) {
         const uint4 it = __ldg(w.item + item);
-        const int g = __ldg(w.item_g + item);
+        const int g = pp_idx((int)__ldg(w.item_g + item), (int)d.ng);
         if (g != cur) {
             if (cur >= 0 && active && (acc.hi | acc.lo)) fx_atomic_add(acc_next + 2 * (cur * 32 + lane), acc);
             acc = Fx128{0, 0};
@@ -366,15 +370,18 @@ __global__ void __launch_bounds__(THREADS) iterate_kernel(const __grid_constant_
         // col is a column position (vertex iperm[col]); r_out is in vertex order
         auto epi = [&](uint32_t col, float y, float invc) {
             if (!active) return;
+            col = pp_idx(col, G.N);
             const float r = cc * y + tele;
-            if (LAST) ro[(uint64_t)__ldg(G.iperm + col) * nrhs + lane] = r;
+            if (LAST) ro[(uint64_t)pp_idx(__ldg(G.iperm + col), G.N) * nrhs + lane] = r;
             st_hint(xo + (uint64_t)col * nrhs + lane, r * invc, keep);
             fx_add(acc, r, E);
         };
         const uint32_t e0 = it.z;
         if (it.x & LONG_FLAG) {
-            const uint32_t col = it.x & ~LONG_FLAG, first = it.y;
-            const uint32_t nent = it.w & 0xfffu, nchunks = it.w >> 12;
+            const uint32_t col = pp_idx(it.x & ~LONG_FLAG, G.N), first = it.y;
+            const uint32_t nent = pp_len(e0, it.w & 0xfffu, G.info[PP_INFO_NNZ]);
+            // 0 (checked build) when the column's items leave the item arrays: then summed as one chunk
+            const uint32_t nchunks = pp_len(first, it.w >> 12, d.item_cap);
             KSum y{0.f, 0.f};
             for (uint32_t b = 0; b < nent; b += 32) {
                 const uint32_t mine = b + lane < nent ? ld_stream_u32(G.rowc + e0 + b + lane, stream) : 0u;
@@ -401,7 +408,7 @@ __global__ void __launch_bounds__(THREADS) iterate_kernel(const __grid_constant_
                     }
                 }
             }
-            if (nchunks == 1) {
+            if (nchunks <= 1) {
                 epi(col, y.s, invp[col]);
             } else {
                 // the warp finishing the column's last chunk adds the chunk sums in order
@@ -421,7 +428,8 @@ __global__ void __launch_bounds__(THREADS) iterate_kernel(const __grid_constant_
                 }
             }
         } else {
-            const uint32_t c0 = it.x, ncol = it.y, nent = it.w;
+            const uint32_t c0 = it.x, ncol = pp_len(c0, pp_len(0, it.y, TILE_COLS), G.N);
+            const uint32_t nent = pp_len(e0, pp_len(0, it.w, TILE_ENTRIES), G.info[PP_INFO_NNZ]);
             if (lane < (int)ncol) cp[lane] = ld_stream_u32(G.colptr + c0 + lane, stream) - e0;
             if (lane == 0) cp[ncol] = nent;
             const float myinv = lane < (int)ncol ? invp[c0 + lane] : 0.f;
@@ -446,13 +454,13 @@ __global__ void __launch_bounds__(THREADS) iterate_kernel(const __grid_constant_
                             epi(c0 + ci, y.s, __shfl_sync(0xffffffffu, myinv, ci));
                             y = KSum{0.f, 0.f};
                             ++ci;
-                            next_end = cp[ci + 1];
+                            next_end = cp[pp_idx(ci + 1, ncol + 1)];
                         }
                         uint32_t cf = wk[m] >> G.scale;
                         if (cf == G.cmax)
                             cf = ovf_lookup(G.ovf_key, G.ovf_cnt, G.info[PP_INFO_NOVF],
                                             ((uint64_t)__ldg(G.iperm + (wk[m] & umask)) << 32) |
-                                                __ldg(G.iperm + c0 + ci));
+                                                __ldg(G.iperm + pp_idx(c0 + ci, G.N)));
                         y.add((float)cf * xv[m]);
                     }
                 }
@@ -539,7 +547,7 @@ __global__ void __launch_bounds__(THREADS) iterate_vec_kernel(const __grid_const
     __shared__ uint32_t s_cp[WARPS][TILE_COLS + 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int quad = lane & 7, slot = lane >> 3;
-    const uint32_t n_items = w.ctl[0];
+    const uint32_t n_items = pp_len(0, w.ctl[0], d.item_cap);
     const uint32_t nwarps = gridDim.x * WARPS;
     const float cc = (float)d.c;
     const uint64_t keep = policy_evict_last(), stream = policy_evict_first();
@@ -554,7 +562,7 @@ __global__ void __launch_bounds__(THREADS) iterate_vec_kernel(const __grid_const
     int E = 1;
     for (uint32_t item = blockIdx.x * WARPS + warp; item < n_items; item += nwarps) {
         const uint4 it = __ldg(w.item + item);
-        const int g = __ldg(w.item_g + item);
+        const int g = pp_idx((int)__ldg(w.item_g + item), (int)d.ng);
         if (g != cur) {
             if (cur >= 0 && (acc.hi | acc.lo)) fx_atomic_add(acc_next + 2 * (cur * 32 + lane), acc);
             acc = Fx128{0, 0};
@@ -572,15 +580,18 @@ __global__ void __launch_bounds__(THREADS) iterate_vec_kernel(const __grid_const
         const float *invp = w.invp + G.row0;
         // col is a column position (vertex iperm[col]); r_out is in vertex order; lane = vector
         auto epi = [&](uint32_t col, float y, float invc) {
+            col = pp_idx(col, G.N);
             const float r = cc * y + tele;
-            if (LAST) ro[(uint64_t)__ldg(G.iperm + col) * 32u + lane] = r;
+            if (LAST) ro[(uint64_t)pp_idx(__ldg(G.iperm + col), G.N) * 32u + lane] = r;
             st_hint(xo + (uint64_t)col * 32u + lane, r * invc, keep);
             fx_add(acc, r, E);
         };
         const uint32_t e0 = it.z;
         if (it.x & LONG_FLAG) {
-            const uint32_t col = it.x & ~LONG_FLAG, first = it.y;
-            const uint32_t nent = it.w & 0xfffu, nchunks = it.w >> 12;
+            const uint32_t col = pp_idx(it.x & ~LONG_FLAG, G.N), first = it.y;
+            const uint32_t nent = pp_len(e0, it.w & 0xfffu, G.info[PP_INFO_NNZ]);
+            // 0 (checked build) when the column's items leave the item arrays: then summed as one chunk
+            const uint32_t nchunks = pp_len(first, it.w >> 12, d.item_cap);
             KSum4 ks{};
             for (uint32_t b = 0; b < nent; b += TILE_ENTRIES) {
                 const uint32_t n = min((uint32_t)TILE_ENTRIES, nent - b);
@@ -590,7 +601,7 @@ __global__ void __launch_bounds__(THREADS) iterate_vec_kernel(const __grid_const
                 __syncwarp();
             }
             const float y = vec_total(ks, lane);
-            if (nchunks == 1) {
+            if (nchunks <= 1) {
                 epi(col, y, invp[col]);
             } else {
                 // the warp finishing the column's last chunk adds the chunk sums in order
@@ -609,7 +620,8 @@ __global__ void __launch_bounds__(THREADS) iterate_vec_kernel(const __grid_const
                 }
             }
         } else {
-            const uint32_t c0 = it.x, ncol = it.y, nent = it.w;
+            const uint32_t c0 = it.x, ncol = pp_len(c0, pp_len(0, it.y, TILE_COLS), G.N);
+            const uint32_t nent = pp_len(e0, pp_len(0, it.w, TILE_ENTRIES), G.info[PP_INFO_NNZ]);
             if (lane < (int)ncol) cp[lane] = ld_stream_u32(G.colptr + c0 + lane, stream) - e0;
             if (lane == 0) cp[ncol] = nent;
             const float myinv = lane < (int)ncol ? invp[c0 + lane] : 0.f;
@@ -617,7 +629,8 @@ __global__ void __launch_bounds__(THREADS) iterate_vec_kernel(const __grid_const
             __syncwarp();
             for (uint32_t ci = 0; ci < ncol; ++ci) {
                 KSum4 ks{};
-                vec_accumulate(G, rowc_s, cp[ci], cp[ci + 1], xg, c0 + ci, slot, quad, keep, ks);
+                const uint32_t lo = cp[ci], hi = lo + pp_len(lo, cp[ci + 1] - lo, nent);
+                vec_accumulate(G, rowc_s, lo, hi, xg, c0 + ci, slot, quad, keep, ks);
                 epi(c0 + ci, vec_total(ks, lane), __shfl_sync(0xffffffffu, myinv, ci));
             }
             __syncwarp();
@@ -707,6 +720,7 @@ extern "C" pp_status pp_pagerank_batched_workspace(const pp_graph *gs, uint32_t 
 extern "C" pp_status pp_pagerank_batched(const pp_graph *gs, uint32_t n_graphs, const double *r0, uint32_t nrhs,
                                          uint32_t iters, double c, float *r_out, void *ws, size_t ws_bytes,
                                          void *stream) {
+    PP_RANGE("pp_pagerank_batched");
     uint64_t rows, edges;
     if (!batch_args_ok(gs, n_graphs, nrhs) || !k3b::batch_sizes(gs, n_graphs, rows, edges) || !r0 || !r_out ||
         !(c >= 0.0 && c <= 1.0))
@@ -739,6 +753,7 @@ extern "C" pp_status pp_pagerank_batched(const pp_graph *gs, uint32_t n_graphs, 
         blk0 += G.nblk;
     }
     d.ng = n_graphs;
+    d.item_cap = (uint32_t)k3b::max_items(n_graphs, rows, edges);
     d.nrhs = nrhs;
     d.iters = iters;
     d.rows = rows;

@@ -154,6 +154,9 @@ struct Args {
     unsigned long long *dmass;       // [2 * FX_SLOTS * (iters + 1)] sum of r over dangling rows, per iterate
     unsigned long long *delta;       // [2 * FX_SLOTS * (iters + 1)] norm(r_k - r_(k-1), 1), per iterate
     uint32_t *state;                 // [0] converged, [1] iterations run
+    // array lengths the checked build tests indices against
+    uint32_t item_cap, slice_cap;    // entries of item / chunk_sum / ticket; of meta (slot: 32 per slice)
+    uint64_t sell_cap;               // words of sell
 };
 
 __device__ __forceinline__ uint32_t ovf_lookup(const uint64_t *keys, const uint32_t *cnts, uint64_t n,
@@ -280,7 +283,7 @@ __global__ void __launch_bounds__(WIN_THREADS) window_fill_kernel(Args a) {
     __shared__ uint32_t sc[40];
     const uint32_t W = 1u << a.wbits, p0 = blockIdx.x << a.wbits;
     const uint4 off = a.woff[blockIdx.x];
-    const uint32_t ns = a.wcnt[blockIdx.x].x;
+    const uint32_t ns = pp_len(off.x, a.wcnt[blockIdx.x].x, a.slice_cap);
     const uint32_t L = a.shortmax;
     for (uint32_t i = threadIdx.x; i <= L; i += blockDim.x) next[i] = 0;
     if (threadIdx.x == 0) {
@@ -314,14 +317,15 @@ __global__ void __launch_bounds__(WIN_THREADS) window_fill_kernel(Args a) {
             const uint32_t o = atomicAdd(&s_item, nc);
             for (uint32_t k = 0; k < nc; ++k) {
                 const uint32_t cs = s + k * a.chunk;
-                a.item[o + k] = make_uint4(p | LONG_FLAG, o, cs, min(a.chunk, s + len - cs) | (nc << NENT_BITS));
-                a.ticket[o + k] = 0;
+                const uint32_t oi = pp_idx(o + k, a.item_cap);
+                a.item[oi] = make_uint4(p | LONG_FLAG, o, cs, min(a.chunk, s + len - cs) | (nc << NENT_BITS));
+                a.ticket[oi] = 0;
             }
         } else if (len == 0) {
-            a.elist[atomicAdd(&s_empty, 1u)] = p;
+            a.elist[pp_idx(atomicAdd(&s_empty, 1u), a.N)] = p;
         } else {
             const uint32_t rank = atomicAdd(&next[len], 1u);
-            slot[rank] = (len << SLOT_LEN_SHIFT) | i;
+            slot[pp_idx(rank, 32u * ns)] = (len << SLOT_LEN_SHIFT) | i;
         }
     }
     __syncthreads();
@@ -365,9 +369,11 @@ __global__ void __launch_bounds__(WIN_THREADS) window_fill_kernel(Args a) {
     for (uint32_t t = warp; t < ns; t += WIN_THREADS / 32) {
         const uint32_t o = slot[32 * t + lane];
         if (o == SLOT_NONE) continue;
-        const uint32_t len = o >> SLOT_LEN_SHIFT, p = p0 + (o & ((1u << SLOT_LEN_SHIFT) - 1));
-        const uint32_t *src = a.rowc + __ldg(a.colptr + p);
-        uint32_t *dst = a.sell + 32ull * a.meta[off.x + t].x + lane;
+        const uint32_t p = pp_idx(p0 + (o & ((1u << SLOT_LEN_SHIFT) - 1)), a.N);
+        const uint32_t s0 = __ldg(a.colptr + p), sb = a.meta[off.x + t].x;
+        const uint32_t len = pp_len(32ull * sb, pp_len(s0, o >> SLOT_LEN_SHIFT, a.info[PP_INFO_NNZ]), a.sell_cap, 32);
+        const uint32_t *src = a.rowc + s0;
+        uint32_t *dst = a.sell + 32ull * sb + lane;
         for (uint32_t k = 0; k < len; ++k) dst[32ull * k] = __ldg(src + k);
     }
 }
@@ -386,12 +392,12 @@ __global__ void __launch_bounds__(256) order_inv_kernel(Args a, const TA *inv) {
         TA v = TA(0);
         if (o != SLOT_NONE) {
             const uint32_t win = a.meta[q / 32].y >> META_LEN_BITS;
-            v = inv[a.iperm[(win << a.wbits) + (o & ((1u << SLOT_LEN_SHIFT) - 1))]];
+            v = inv[pp_idx(a.iperm[pp_idx((win << a.wbits) + (o & ((1u << SLOT_LEN_SHIFT) - 1)), a.N)], a.N)];
         }
         invs[q] = v;
     }
     for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nempty; q += stride)
-        einv[q] = inv[a.iperm[a.elist[q]]];
+        einv[q] = inv[pp_idx(a.iperm[pp_idx(a.elist[q], a.N)], a.N)];
 }
 
 // Reset the per-call counters and sum |r0|.
@@ -439,7 +445,7 @@ __global__ void __launch_bounds__(256) normalize_kernel(Args a, const double *r0
         double q[R];
         TA iv[R];
 #pragma unroll
-        for (int k = 0; k < R; ++k) v[k] = p0 + k * stride < a.N ? a.iperm[p0 + k * stride] : 0u;
+        for (int k = 0; k < R; ++k) v[k] = p0 + k * stride < a.N ? pp_idx(a.iperm[p0 + k * stride], a.N) : 0u;
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             const bool in = p0 + k * stride < a.N;
@@ -519,10 +525,12 @@ struct Epilogue {
     const TA *rb_in;
     TA *rb_out;
     uint32_t flags;
+    uint32_t N;
     // col is a column position (vertex iperm[col])
     __device__ __forceinline__ void operator()(uint32_t col, TA y, TA inv_col, Sums &acc) const {
+        col = pp_idx(col, N);
         const TA r = cc * y + tele;
-        if (LAST && !EXT) r_out[__ldg(iperm + col)] = (TO)r;
+        if (LAST && !EXT) r_out[pp_idx(__ldg(iperm + col), N)] = (TO)r;
         st_x(x_out + col, Scaled<TS>::value ? from_acc<TS>(r * inv_col * xscale) : from_acc<TS>(r * inv_col));
         fx_add(acc.s, r, E);
         if (EXT) {
@@ -621,7 +629,8 @@ __global__ void __launch_bounds__(THREADS, MINB)
                                               a.iperm,
                                               rb_in,
                                               rb_out,
-                                              a.flags};
+                                              a.flags,
+                                              a.N};
     Sums acc{{0, 0}, {0, 0}, {0, 0}};
     const uint32_t nwarps = gridDim.x * NW;
 
@@ -650,8 +659,10 @@ __global__ void __launch_bounds__(THREADS, MINB)
         const uint4 it = cur.d;
         if (item < n_chunks) {
             // ---- one chunk of a long column: coalesced entries, a group of gathers in flight per lane
-            const uint32_t col = it.x & ~LONG_FLAG, first = it.y, e0 = it.z;
-            const uint32_t nent = it.w & ((1u << NENT_BITS) - 1), nchunks = it.w >> NENT_BITS;
+            const uint32_t col = pp_idx(it.x & ~LONG_FLAG, a.N), first = it.y, e0 = it.z;
+            const uint32_t nent = pp_len(e0, it.w & ((1u << NENT_BITS) - 1), a.info[PP_INFO_NNZ]);
+            // 0 (checked build) when the column's items leave the item arrays: then summed as one chunk
+            const uint32_t nchunks = pp_len(first, it.w >> NENT_BITS, a.item_cap);
             ColSum<TA> part;
             // the entries of step s + 1 are loaded while the gathers of step s are in flight
             const uint32_t *rw = a.rowc + e0 + lane;
@@ -681,7 +692,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
             }
             const TA y = part.warp_total(E);
             if (lane == 0) {
-                if (nchunks == 1) {
+                if (nchunks <= 1) {
                     epi(col, y, __ldg(inv + col), acc);
                 } else {
                     // the warp finishing the column's last chunk adds the chunk sums in order
@@ -707,8 +718,8 @@ __global__ void __launch_bounds__(THREADS, MINB)
             const uint32_t slen = it.y & ((1u << META_LEN_BITS) - 1), win = it.y >> META_LEN_BITS;
             const uint32_t o = it.z;
             const bool valid = o != SLOT_NONE;
-            const uint32_t len = valid ? (o >> SLOT_LEN_SHIFT) : 0u;
-            const uint32_t col = (win << a.wbits) + (o & ((1u << SLOT_LEN_SHIFT) - 1));
+            const uint32_t len = valid ? pp_len(32ull * it.x, o >> SLOT_LEN_SHIFT, a.sell_cap, 32) : 0u;
+            const uint32_t col = pp_idx_if(valid, (win << a.wbits) + (o & ((1u << SLOT_LEN_SHIFT) - 1)), a.N);
             const TA myinv = cur.iv;
             const uint32_t *src = a.sell + 32ull * it.x + lane;
             ColSum<TA> y;
@@ -758,7 +769,7 @@ __global__ void __launch_bounds__(256) finish_kernel(Args a, const TA *rb0, cons
     const uint32_t k = ld_relaxed_u32(a.state) ? a.state[1] : a.iters;
     const TA *rb = (k & 1) ? rb1 : rb0;
     for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.N; p += (uint64_t)gridDim.x * blockDim.x)
-        r_out[a.iperm[p]] = (TO)rb[p];
+        r_out[pp_idx(a.iperm[p], a.N)] = (TO)rb[p];
     if (iters_done && blockIdx.x == 0 && threadIdx.x == 0) *iters_done = k;
 }
 
@@ -809,7 +820,7 @@ struct Layout {
     unsigned long long *dmass, *delta;
     uint32_t *state;
     uint32_t wbits, nwin;
-    uint64_t max_slices;
+    uint64_t max_slices, max_items, sell_words;
     size_t bytes;
 };
 
@@ -840,7 +851,9 @@ inline Layout layout(void *ws, uint64_t M, uint32_t scale, uint32_t iters, pp_dt
     L.invs = c.take<char>(32 * max_slices * (dt == PP_FP64 ? 8 : 4));
     L.elist = c.take<uint32_t>(N);
     L.einv = c.take<char>(N * (dt == PP_FP64 ? 8 : 4));
-    L.sell = c.take<uint32_t>(M + (uint64_t)L.nwin * 32 * SHORTMAX_MAX);
+    L.max_items = max_items;
+    L.sell_words = M + (uint64_t)L.nwin * 32 * SHORTMAX_MAX;
+    L.sell = c.take<uint32_t>(L.sell_words);
     L.item = c.take<uint4>(max_items);
     L.chunk_sum = c.take<double>(max_items);
     L.ticket = c.take<uint32_t>(max_items);
@@ -939,6 +952,9 @@ pp_status run_unroll(const pp_graph *g, const double *r0, uint32_t iters, double
     a.ipart = L.ipart;
     a.ctl = L.ctl;
     a.c = c;
+    a.item_cap = (uint32_t)L.max_items;
+    a.slice_cap = (uint32_t)L.max_slices;
+    a.sell_cap = L.sell_words;
     auto *k_mid = iterate_kernel<TS, TA, TO, false, UNROLL, MINB, EXT>;
     auto *k_last = iterate_kernel<TS, TA, TO, !EXT, UNROLL, MINB, EXT>;
     constexpr int NT = THREADS;
@@ -1080,6 +1096,7 @@ using namespace pp;
 
 extern "C" pp_status pp_gather_probe(const uint32_t *rowc, uint64_t n, uint32_t scale, const float *x, float *out,
                                      void *stream) {
+    PP_RANGE("pp_gather_probe");
     if (scale < 1 || scale > 27 || (n && (!rowc || !x)) || !out) return PP_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     static PerDevice occ_dev;
@@ -1104,6 +1121,7 @@ extern "C" pp_status pp_pagerank_workspace(uint64_t M, uint32_t scale, uint32_t 
 
 extern "C" pp_status pp_pagerank(const pp_graph *g, const double *r0, uint32_t iters, double c, pp_dtype dt,
                                  void *r_out, double *r_l1, void *ws, size_t ws_bytes, void *stream) {
+    PP_RANGE("pp_pagerank");
     if (!g || !r0 || !r_out || (int)dt < 0 || (int)dt > 3) return PP_ERR_INVALID_ARG;
     if (g->scale < 1 || g->scale > 27 || g->M > (1ull << 31) || !(c >= 0.0 && c <= 1.0)) return PP_ERR_INVALID_ARG;
     if (!g->colptr || !g->rowc || !g->ovf_key || !g->ovf_cnt || !g->info || !g->perm || !g->iperm)
@@ -1137,6 +1155,7 @@ extern "C" pp_status pp_pagerank_ex_workspace(uint64_t M, uint32_t scale, uint32
 extern "C" pp_status pp_pagerank_ex(const pp_graph *g, const double *r0, uint32_t iters, double c, pp_dtype dt,
                                     uint32_t flags, double tol, void *r_out, double *r_l1, uint32_t *iters_done,
                                     void *ws, size_t ws_bytes, void *stream) {
+    PP_RANGE("pp_pagerank_ex");
     if (!g || !r0 || !r_out || (int)dt < 0 || (int)dt > 3) return PP_ERR_INVALID_ARG;
     if (g->scale < 1 || g->scale > 27 || g->M > (1ull << 31) || !(c >= 0.0 && c <= 1.0)) return PP_ERR_INVALID_ARG;
     if (flags & ~(uint32_t)(PP_K3_DANGLING | PP_K3_CONVERGE)) return PP_ERR_INVALID_ARG;

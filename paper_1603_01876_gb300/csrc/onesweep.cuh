@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(THREADS, PASS_MINB) pass_kernel(Src src, Dst d
     for (int i = 0; i < ITEMS; ++i) {
         if (i < nv) {
             const uint32_t d = (uint32_t)(keys[i] >> ctl.shift) & (RADIX - 1);
-            s_keys[s_whist[warp][d] + ((rank[i / 3] >> (10 * (i % 3))) & 1023u)] = keys[i];
+            s_keys[pp_idx(s_whist[warp][d] + ((rank[i / 3] >> (10 * (i % 3))) & 1023u), TILE)] = keys[i];
         }
     }
     __syncthreads();
@@ -202,7 +202,8 @@ __global__ void __launch_bounds__(THREADS, PASS_MINB) pass_kernel(Src src, Dst d
     for (uint32_t j = tid; j < nvalid; j += THREADS) {
         const KeyT k = s_keys[j];
         const uint32_t d = (uint32_t)(k >> ctl.shift) & (RADIX - 1);
-        dst.store((uint64_t)(uint32_t)(s_gbase[d] + j), k, 0u);
+        // htotal: the keys this pass places, the length of the output
+        dst.store(pp_idx((uint64_t)(uint32_t)(s_gbase[d] + j), (uint64_t)htotal), k, 0u);
     }
 }
 

@@ -70,6 +70,17 @@ extern "C" pp_status pp_get_tuning(const char *key, int64_t *value) {
 
 extern "C" uint64_t pp_launch_count(void) { return g_launches.load(); }
 
+extern "C" uint32_t pp_build_flags(void) {
+    uint32_t f = 0;
+#ifdef PP_CHECKED
+    f |= PP_BUILD_CHECKED;
+#endif
+#ifndef PP_NO_NVTX
+    f |= PP_BUILD_NVTX;
+#endif
+    return f;
+}
+
 extern "C" const char *pp_status_string(pp_status st) {
     switch (st) {
         case PP_OK: return "ok";
@@ -82,6 +93,7 @@ extern "C" const char *pp_status_string(pp_status st) {
 }
 
 extern "C" pp_status pp_last_device_error(void *stream, uint32_t *code) {
+    PP_RANGE("pp_last_device_error");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (cudaStreamSynchronize(s) != cudaSuccess) return PP_ERR_CUDA;
     uint32_t w = 0;
@@ -158,6 +170,7 @@ extern "C" pp_status pp_pipeline_host(const uint32_t *u_host, const uint32_t *v_
                                       uint32_t scale, const double *r0_host, uint32_t iters, double c,
                                       pp_dtype dt, pp_supernode_rule rule, void *r_out_host,
                                       uint64_t *info_host, void *ws, size_t ws_bytes, void *stream) {
+    PP_RANGE("pp_pipeline_host");
     if (scale < 1 || scale > 27 || M > (1ull << 31) || (int)dt < 0 || (int)dt > 3) return PP_ERR_INVALID_ARG;
     if ((M && (!u_host || !v_host)) || !r0_host || !r_out_host) return PP_ERR_INVALID_ARG;
     const PipeLayout need = pipe_layout(nullptr, M, scale, iters, dt);
@@ -196,6 +209,7 @@ struct pp_exec {
 extern "C" pp_status pp_pagerank_batched_capture(const pp_graph *gs, uint32_t n_graphs, const double *r0,
                                                  uint32_t nrhs, uint32_t iters, double c, float *r_out, void *ws,
                                                  size_t ws_bytes, void *stream, pp_exec **exec) {
+    PP_RANGE("pp_pagerank_batched_capture");
     if (!exec) return PP_ERR_INVALID_ARG;
     *exec = nullptr;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -256,6 +270,7 @@ extern "C" pp_status pp_pipeline_batched_capture(uint32_t n_graphs, const uint32
                                                  const double *r0, uint32_t nrhs, uint32_t iters, double c,
                                                  float *r_out, void *ws, size_t ws_bytes, void *stream,
                                                  pp_exec **exec) {
+    PP_RANGE("pp_pipeline_batched_capture");
     if (!exec) return PP_ERR_INVALID_ARG;
     *exec = nullptr;
     uint64_t M[PP_BATCH_MAX_GRAPHS];
@@ -296,6 +311,7 @@ extern "C" pp_status pp_pipeline_batched_capture(uint32_t n_graphs, const uint32
 }
 
 extern "C" pp_status pp_exec_launch(pp_exec *exec, void *stream) {
+    PP_RANGE("pp_exec_launch");
     if (!exec) return PP_ERR_INVALID_ARG;
     if (cudaGraphLaunch(exec->exec, static_cast<cudaStream_t>(stream)) != cudaSuccess) return PP_ERR_CUDA;
     count_launch(exec->kernels);

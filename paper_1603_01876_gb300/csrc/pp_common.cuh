@@ -6,6 +6,10 @@
 
 #include <atomic>
 
+#ifndef PP_NO_NVTX
+#include <nvtx3/nvToolsExt.h>
+#endif
+
 #include "../../include/pagerank_pipeline.h"
 
 // One device error word per translation unit (each .cu file gets its own
@@ -13,9 +17,70 @@
 static __device__ uint32_t pp_err_word;
 static __device__ __forceinline__ void pp_set_error(uint32_t bits) { atomicOr(&pp_err_word, bits); }
 
+// Index checks of the checked build (-DPP_CHECKED, libpp_checked.so).
+// pp_idx(i, n) wraps every index that a kernel read from memory or computed
+// from what it read, n being the length of the array addressed: it is i when
+// i < n; otherwise it records PP_DEV_BOUNDS and gives 0, so that the access
+// stays inside the array (the result is then invalid; nothing traps).  In the
+// normal build it is i itself.
+template <typename I, typename N>
+static __device__ __forceinline__ I pp_idx(I i, N n) {
+#ifdef PP_CHECKED
+    if ((unsigned long long)i < (unsigned long long)n) return i;
+    pp_set_error(PP_DEV_BOUNDS);
+    return I(0);
+#else
+    (void)n;
+    return i;
+#endif
+}
+// pp_idx for an index that is only used when `on` holds (0 otherwise when checked).
+template <typename I, typename N>
+static __device__ __forceinline__ I pp_idx_if(bool on, I i, N n) {
+#ifdef PP_CHECKED
+    return on ? pp_idx(i, n) : I(0);
+#else
+    (void)on;
+    (void)n;
+    return i;
+#endif
+}
+// A run of `len` items of `unit` elements from element `start` of an array
+// of n: len when it fits; otherwise PP_DEV_BOUNDS and 0 (checked build).
+template <typename L>
+static __device__ __forceinline__ L pp_len(unsigned long long start, L len, unsigned long long n,
+                                           unsigned long long unit = 1) {
+#ifdef PP_CHECKED
+    if (start <= n && (unsigned long long)len * unit <= n - start) return len;
+    pp_set_error(PP_DEV_BOUNDS);
+    return L(0);
+#else
+    (void)start;
+    (void)n;
+    (void)unit;
+    return len;
+#endif
+}
+
 namespace pp {
 
 // ------------------------------------------------------------------ host side
+
+// An NVTX range around one C-ABI call, named after the call: profilers show
+// the call on their timeline and can select its kernels (ncu --nvtx
+// --nvtx-include "pp_pagerank/").  Without an attached tool a push and a pop
+// cost a few nanoseconds; -DPP_NO_NVTX leaves them out.
+struct Range {
+#ifndef PP_NO_NVTX
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+#else
+    explicit Range(const char *) {}
+#endif
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
+#define PP_RANGE(name) ::pp::Range pp_call_range_(name)
 
 // Number of kernels enqueued by the library (pp_launch_count).
 extern std::atomic<uint64_t> g_launches;

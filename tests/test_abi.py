@@ -21,6 +21,7 @@ def declared_functions(header):
 
 
 @pytest.mark.parametrize("header,lib", [("pagerank_pipeline.h", "paper_1603_01876_gb300/libpp.so"),
+                                        ("pagerank_pipeline.h", "paper_1603_01876_gb300/libpp_checked.so"),
                                         ("kernel0.h", "kernel0/libkernel0.so")])
 def test_every_declared_symbol_is_exported(header, lib):
     names = declared_functions(header)
@@ -78,10 +79,30 @@ def test_host_side_argument_errors():
 def test_binding_fails_loudly_without_library(monkeypatch):
     import paper_1603_01876_gb300 as pp
 
-    monkeypatch.setattr(pp, "LIB_PATH", "/nonexistent/libpp.so")
-    monkeypatch.setattr(pp, "_L", None)
+    monkeypatch.setattr(pp, "LIB_PATHS", {"default": "/nonexistent/libpp.so", "checked": "/nonexistent/x.so"})
+    monkeypatch.setattr(pp, "_LIBS", {})
     with pytest.raises(ImportError):
         pp.lib()
+    monkeypatch.setattr(pp, "_ACTIVE", "checked")
+    with pytest.raises(ImportError):
+        pp.lib()
+
+
+def test_build_flags_of_both_libraries():
+    """libpp.so is the plain build, libpp_checked.so the bounds-checked one;
+    both open NVTX ranges.  Selecting a library changes which one the
+    binding calls."""
+    import paper_1603_01876_gb300 as pp
+
+    prev = pp.use_library("default")
+    try:
+        assert pp.build_flags() == pp.BUILD_NVTX
+        pp.use_library("checked")
+        assert pp.build_flags() == pp.BUILD_CHECKED | pp.BUILD_NVTX
+        with pytest.raises(ValueError):
+            pp.use_library("fast")
+    finally:
+        pp.use_library(prev)
 
 
 def test_tuning_knobs():
