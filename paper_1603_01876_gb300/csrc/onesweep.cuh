@@ -4,11 +4,14 @@
 // "Onesweep: A Faster Least Significant Digit Radix Sort for GPUs", 2022):
 // an up-front pass counts the digits of every pass at once; each scatter pass
 // then takes tiles in the order blocks start, ranks the tile's keys with a
-// warp-level multisplit (match.any + popc) into warp-private shared-memory
-// counters, publishes the tile's per-digit counts, and finds its global
-// offset per digit by a decoupled look-back over earlier tiles' published
-// counts.  Keys are staged in shared memory in sorted order, so each digit's
-// run is written to global memory with consecutive addresses.
+// warp-level multisplit into warp-private shared-memory counters, publishes
+// the tile's per-digit counts, stages the keys in shared memory in digit
+// order, and only then finds its global offset per digit by a decoupled
+// look-back over earlier tiles' published counts, so the staging overlaps
+// the wait; each digit's run is written to global memory with consecutive
+// addresses.  The multisplit finds the lanes of a warp holding equal digits
+// with one warp vote per digit bit (eight votes are cheaper on this GPU than
+// one match.any).
 //
 // Look-back waits poll with a bound (kSpinLimit): a wait that expires records
 // PP_DEV_TIMEOUT in the device error word and the kernel carries on, so no
@@ -16,8 +19,8 @@
 // blocks already own, so the bound is never reached in a correct run.
 //
 // Sources and sinks are small functors so that the same pass kernel packs
-// (u, v) into a key on the first pass of Kernel 1, unpacks on its last pass,
-// and filters columns on the first pass of Kernel 2's transpose.
+// (u, v) into a key on the first pass of Kernel 1 and unpacks on its last
+// pass, or writes Kernel 2's permutation from its vertex keys.
 #pragma once
 
 #include "pp_common.cuh"
@@ -64,9 +67,10 @@ struct PassCtl {
 // Status words are 32-bit while every count fits in 30 bits.
 inline bool wide_status(uint64_t n_max) { return n_max >= (1ull << 30); }
 
-// Blocks per SM the registers are budgeted for: five (the most the 42 KB of
-// shared memory allows with 64-bit keys) beat three without spills on GB300.
-constexpr int PASS_MINB = 5;
+// Blocks per SM the registers are budgeted for: four (64 registers, room for
+// the digits held in registers) beat five (48 registers, the most the 42 KB of
+// shared memory allows with 64-bit keys) on GB300.
+constexpr int PASS_MINB = 4;
 
 template <typename KeyT, typename StatT, class Src, class Dst>
 __global__ void __launch_bounds__(THREADS, PASS_MINB) pass_kernel(Src src, Dst dst, PassCtl ctl) {
@@ -100,6 +104,11 @@ __global__ void __launch_bounds__(THREADS, PASS_MINB) pass_kernel(Src src, Dst d
     const uint64_t first = base + lane;
     const uint64_t left = first < n ? (n - first + 31) / 32 : 0;
     const int nv = left < (uint64_t)ITEMS ? (int)left : ITEMS;
+    // the digits stay in registers, four to a word; the keys wait in shared memory
+    constexpr int DW = (ITEMS + 3) / 4;
+    uint32_t dig[DW];
+#pragma unroll
+    for (int q = 0; q < DW; ++q) dig[q] = 0;
     {
         KeyT keys[ITEMS];
         uint32_t unused;
@@ -108,27 +117,40 @@ __global__ void __launch_bounds__(THREADS, PASS_MINB) pass_kernel(Src src, Dst d
             keys[i] = 0;
             if (i < nv) src.load(base + (uint64_t)i * 32 + lane, keys[i], unused);
         }
-        // park the keys in shared memory (input order) while the tile is ranked and looks back
 #pragma unroll
-        for (int i = 0; i < ITEMS; ++i) s_keys[wbase + i * 32 + lane] = keys[i];
+        for (int i = 0; i < ITEMS; ++i) {
+            dig[i / 4] |= ((uint32_t)(keys[i] >> ctl.shift) & (RADIX - 1)) << (8 * (i % 4));
+            s_keys[wbase + i * 32 + lane] = keys[i];
+        }
     }
-    __syncwarp();
 
     // Warp-level multisplit: rank of each key among equal digits of its warp,
-    // kept three 10-bit ranks to a register (the digit is read again later).
+    // kept three 10-bit ranks to a register.  The lanes holding the same digit
+    // (and the same validity) are the AND of one vote per digit bit; the lowest
+    // of them adds the group to the warp's counter and hands the old count to
+    // the others.  Item i + 1's add is issued after item i's result has been
+    // handed on, so each counter sees the items in order.
     constexpr int RW = (ITEMS + 2) / 3;
     uint32_t rank[RW];
 #pragma unroll
     for (int q = 0; q < RW; ++q) rank[q] = 0;
+    const uint32_t lt = lanemask_lt();
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        const uint32_t d = i < nv ? (uint32_t)(s_keys[wbase + i * 32 + lane] >> ctl.shift) & (RADIX - 1) : RADIX;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t before = d < RADIX ? s_whist[warp][d] : 0u;
-        __syncwarp();
-        if (d < RADIX && (peers >> lane) == 1u) s_whist[warp][d] = before + __popc(peers);
-        __syncwarp();
-        rank[i / 3] |= (before + __popc(peers & lanemask_lt())) << (10 * (i % 3));
+        const bool ok = i < nv;
+        const uint32_t d = (dig[i / 4] >> (8 * (i % 4))) & (RADIX - 1);
+        uint32_t peers = __ballot_sync(0xffffffffu, ok);
+        if (!ok) peers = ~peers;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const uint32_t m = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? m : ~m;
+        }
+        const int leader = __ffs(peers) - 1;
+        uint32_t before = 0;
+        if (lane == leader && ok) before = atomicAdd(&s_whist[warp][d], (uint32_t)__popc(peers));
+        before = __shfl_sync(0xffffffffu, before, leader);
+        rank[i / 3] |= (before + __popc(peers & lt)) << (10 * (i % 3));
     }
     __syncthreads();
 
@@ -150,6 +172,22 @@ __global__ void __launch_bounds__(THREADS, PASS_MINB) pass_kernel(Src src, Dst d
     // staging offset of warp w's first key of digit tid (one lookup per key below)
 #pragma unroll
     for (int w = 0; w < WARPS; ++w) s_whist[w][tid] += bstart;
+
+    // Stage the tile in digit order, in place (every key is read before any is
+    // written), while earlier tiles finish publishing.
+    {
+        KeyT keys[ITEMS];
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) keys[i] = s_keys[wbase + i * 32 + lane];
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            if (i < nv) {
+                const uint32_t d = (dig[i / 4] >> (8 * (i % 4))) & (RADIX - 1);
+                s_keys[pp_idx(s_whist[warp][d] + ((rank[i / 3] >> (10 * (i % 3))) & 1023u), TILE)] = keys[i];
+            }
+        }
+    }
 
     // Decoupled look-back for this digit, four predecessors per round trip.
     StatT excl = 0;
@@ -183,19 +221,6 @@ __global__ void __launch_bounds__(THREADS, PASS_MINB) pass_kernel(Src src, Dst d
     }
     // every global index is below 2^31, so the offset arithmetic may wrap mod 2^32
     s_gbase[tid] = (uint32_t)((uint64_t)hexcl + (uint64_t)excl) - bstart;
-
-    // Stage the tile in digit order, in place: every key is read before any is written.
-    KeyT keys[ITEMS];
-#pragma unroll
-    for (int i = 0; i < ITEMS; ++i) keys[i] = s_keys[wbase + i * 32 + lane];
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-        if (i < nv) {
-            const uint32_t d = (uint32_t)(keys[i] >> ctl.shift) & (RADIX - 1);
-            s_keys[pp_idx(s_whist[warp][d] + ((rank[i / 3] >> (10 * (i % 3))) & 1023u), TILE)] = keys[i];
-        }
-    }
     __syncthreads();
 
     // Write each digit run to its global position.
