@@ -41,8 +41,8 @@ WORKLOAD = ("Kronecker graph, scale 24 (N=2^24, M=16N=268,435,456 edges, initiat
 # each stage's dominant kernel from one ncu capture (profiles/), valid while
 # its source file is unchanged.
 TRAFFIC = {
-    "k3_pagerank": {"source": "paper_1603_01876_gb300/csrc/k3_pagerank.cu", "sha": "9d1c868351ac3b56",
-                    "bytes_per_launch": 1328437000 + 39628800, "dtype": "fp32", "scale": 24,
+    "k3_pagerank": {"source": "paper_1603_01876_gb300/csrc/k3_pagerank.cu", "sha": "e9d664e1cec2346f",
+                    "bytes_per_launch": 1328286000 + 39170304, "dtype": "fp32", "scale": 24,
                     "capture": "profiles/k3_iterate_fp32_scale24.md"},
 }
 
@@ -577,6 +577,50 @@ def run_k3_only(args):
                       "device_error": pp.last_device_error()}))
 
 
+def run_k1_k2_only(args):
+    """Kernel 1 (--stage k1) or Kernel 2 (--stage k2) alone on the graph of
+    --scale, with its workspace allocated once: for per-kernel timing and
+    profiling (the launch order of one call: Kernel 1's histogram and its
+    passes; Kernel 2's kernels as listed in k2_build.cu)."""
+    import torch
+
+    import kernel0
+    import paper_1603_01876_gb300 as pp
+
+    dev = torch.device("cuda", 0)
+    scale = args.scale
+    M = 16 << scale
+    u, v = kernel0.edges_device(scale, SEED, device=dev)
+    us, vs = torch.empty_like(u), torch.empty_like(v)
+    if args.stage == "k1":
+        ws = torch.empty(pp.workspace_bytes("sort", M, scale), dtype=torch.uint8, device=dev)
+        call = lambda: pp.sort_edges(u, v, scale, out=(us, vs), workspace=ws)
+        nbytes = k1_bytes(M, scale)[0]
+    else:
+        pp.sort_edges(u, v, scale, out=(us, vs))
+        del u, v
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        ws = torch.empty(pp.workspace_bytes("build", M, scale), dtype=torch.uint8, device=dev)
+        g = pp.Graph(M, scale, dev)
+        call = lambda: pp.build_filter_normalize(us, vs, scale, "lowest", graph=g, workspace=ws)
+        call()
+        info = g.info_dict()
+        nbytes = k2_bytes(M, 1 << scale, info["nnz0"], info["nnz"], scale)
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e[0].record()
+    for _ in range(args.steps):
+        call()
+    e[1].record()
+    torch.cuda.synchronize()
+    ms = e[0].elapsed_time(e[1]) / args.steps
+    print(json.dumps({"stage": args.stage, "scale": scale, "edges": M, "ms": ms, "edges_per_s": M / (ms * 1e-3),
+                      "gbs": nbytes / ms / 1e6, "device_error": pp.last_device_error()}))
+
+
 def run_batched(dev, steps=3, warmup=1, nrhs=32, n_graphs=64, lo=12, hi=18):
     """The batched configuration: 64 Kronecker graphs of scales drawn from
     12..18, each with 32 start vectors.  Kernels 1 and 2 for all graphs at
@@ -774,8 +818,8 @@ def main():
     ap.add_argument("--no-files", action="store_true", help="skip the edge-file (Kernel 1 with files) section")
     ap.add_argument("--tune", action="append", default=[], metavar="KEY=VALUE",
                     help="set a library tuning knob before running (repeatable)")
-    ap.add_argument("--stage", choices=["all", "k3", "gather-ceiling", "batched"], default="all",
-                    help="k3: time Kernel 3 alone (profiling aid); the default times the whole pipeline")
+    ap.add_argument("--stage", choices=["all", "k1", "k2", "k3", "gather-ceiling", "batched"], default="all",
+                    help="k1 / k2 / k3: time one kernel alone (profiling aid); the default times the whole pipeline")
     ap.add_argument("--tuning", default="default",
                     help="autotuner result to apply (JSON from paper_1603_01876_gb300.tune; 'none' to skip)")
     args = ap.parse_args()
@@ -790,7 +834,9 @@ def main():
         for kv in args.tune:
             k, v = kv.split("=")
             pp.set_tuning(k, int(v))
-    if args.stage in ("k3", "gather-ceiling"):
+    if args.stage in ("k1", "k2"):
+        run_k1_k2_only(args)
+    elif args.stage in ("k3", "gather-ceiling"):
         # Kernel 3 alone, with the gather ceiling of an iteration on the same graph
         run_k3_only(args)
     elif args.stage == "batched":
