@@ -414,7 +414,10 @@ pp_status pp_parse_tsv(const char *text, uint64_t text_len, uint32_t *u, uint32_
  * Kernel 2's scalars into info_host[PP_INFO_LEN].  Every device buffer is
  * carved from `workspace` (size from pp_pipeline_workspace).  Host buffers
  * should be page-locked for the copies to be asynchronous; the results are
- * valid after the stream has been synchronised.
+ * valid after the stream has been synchronised.  The copy of r0, which only
+ * Kernel 3 reads, runs on a short-lived side stream while Kernels 1 and 2
+ * compute; Kernel 3 waits for it (the call creates and releases that stream
+ * and its events itself, so it cannot be recorded into a CUDA graph).
  */
 pp_status pp_pipeline_workspace(uint64_t M, uint32_t scale, uint32_t iters, pp_dtype dtype,
                                 size_t *bytes);

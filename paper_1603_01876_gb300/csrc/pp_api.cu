@@ -166,6 +166,33 @@ extern "C" pp_status pp_pipeline_workspace(uint64_t M, uint32_t scale, uint32_t 
     return PP_OK;
 }
 
+// A side stream that starts after the work already enqueued on `s`, and an
+// event marking the end of what is enqueued on it.  Destroying them while
+// their work is pending is allowed: the runtime releases them when it ends.
+struct SideCopy {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t start = nullptr, done = nullptr;
+    bool open(cudaStream_t s) {
+        if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&start, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventRecord(start, s) != cudaSuccess || cudaStreamWaitEvent(stream, start, 0) != cudaSuccess) {
+            close();
+            cudaGetLastError();
+            return false;
+        }
+        return true;
+    }
+    void close() {
+        if (start) cudaEventDestroy(start);
+        if (done) cudaEventDestroy(done);
+        if (stream) cudaStreamDestroy(stream);
+        start = done = nullptr;
+        stream = nullptr;
+    }
+    ~SideCopy() { close(); }
+};
+
 extern "C" pp_status pp_pipeline_host(const uint32_t *u_host, const uint32_t *v_host, uint64_t M,
                                       uint32_t scale, const double *r0_host, uint32_t iters, double c,
                                       pp_dtype dt, pp_supernode_rule rule, void *r_out_host,
@@ -183,11 +210,22 @@ extern "C" pp_status pp_pipeline_host(const uint32_t *u_host, const uint32_t *v_
         if (cudaMemcpyAsync(L.u, u_host, M * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) return PP_ERR_CUDA;
         if (cudaMemcpyAsync(L.v, v_host, M * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) return PP_ERR_CUDA;
     }
-    if (cudaMemcpyAsync(L.r0, r0_host, N * 8, cudaMemcpyHostToDevice, s) != cudaSuccess) return PP_ERR_CUDA;
+    // r0 is needed only by Kernel 3: its copy runs on a side stream while
+    // Kernels 1 and 2 compute (after the edge copies, which it would only
+    // slow down on the shared host link), and Kernel 3 waits for it.  The
+    // side stream and events are released once their work is done.
+    SideCopy side;
+    if (side.open(s)) {
+        if (cudaMemcpyAsync(L.r0, r0_host, N * 8, cudaMemcpyHostToDevice, side.stream) != cudaSuccess) return PP_ERR_CUDA;
+        if (cudaEventRecord(side.done, side.stream) != cudaSuccess) return PP_ERR_CUDA;
+    } else if (cudaMemcpyAsync(L.r0, r0_host, N * 8, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        return PP_ERR_CUDA;
+    }
     st = pp_sort_edges(L.u, L.v, M, scale, L.us, L.vs, L.scratch, L.scratch_bytes, stream);
     if (st != PP_OK) return st;
     st = pp_build_filter_normalize(L.us, L.vs, M, scale, rule, &L.g, L.scratch, L.scratch_bytes, stream);
     if (st != PP_OK) return st;
+    if (side.stream && cudaStreamWaitEvent(s, side.done, 0) != cudaSuccess) return PP_ERR_CUDA;
     st = pp_pagerank(&L.g, L.r0, iters, c, dt, L.r_out, nullptr, L.scratch, L.scratch_bytes, stream);
     if (st != PP_OK) return st;
     if (cudaMemcpyAsync(r_out_host, L.r_out, N * (dt == PP_FP64 ? 8 : 4), cudaMemcpyDeviceToHost, s) != cudaSuccess)

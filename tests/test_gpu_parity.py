@@ -141,3 +141,24 @@ def test_pipeline_host_matches_device_path(pp, k0):
         want = pp.pagerank(g, torch.from_numpy(r0).cuda(), 20, 0.85, dt).cpu()
         assert torch.equal(r, want)
         assert info.tolist()[:7] == g.info.cpu().tolist()[:7]
+
+
+def test_pipeline_host_back_to_back_calls_keep_their_start_vectors(pp, k0):
+    """Two host-buffer pipelines enqueued back to back on one stream with one
+    workspace and different start vectors: the second call's copy of r0 (on a
+    side stream during Kernels 1-2) must not overtake the first call's Kernel 3."""
+    import torch
+
+    scale = 16
+    u, v, ud, vd = _inputs(k0, scale, None, 43)
+    N = 1 << scale
+    uh = torch.from_numpy(u.view(np.int32)).pin_memory()
+    vh = torch.from_numpy(v.view(np.int32)).pin_memory()
+    r0s = [torch.from_numpy(k0.r0_host(N, s)).pin_memory() for s in (5, 6)]
+    ws = torch.empty(pp.workspace_bytes("pipeline", len(u), scale, 20, "fp32"), dtype=torch.uint8, device="cuda")
+    outs = [pp.pipeline_host(uh, vh, scale, r0, 20, 0.85, "fp32", workspace=ws)[0] for r0 in r0s]
+    torch.cuda.synchronize()
+    us, vs = pp.sort_edges(ud, vd, scale)
+    g = pp.build_filter_normalize(us, vs, scale)
+    for r0, got in zip(r0s, outs):
+        assert torch.equal(got, pp.pagerank(g, r0.cuda(), 20, 0.85, "fp32").cpu())
