@@ -414,10 +414,13 @@ pp_status pp_parse_tsv(const char *text, uint64_t text_len, uint32_t *u, uint32_
  * Kernel 2's scalars into info_host[PP_INFO_LEN].  Every device buffer is
  * carved from `workspace` (size from pp_pipeline_workspace).  Host buffers
  * should be page-locked for the copies to be asynchronous; the results are
- * valid after the stream has been synchronised.  The copy of r0, which only
- * Kernel 3 reads, runs on a short-lived side stream while Kernels 1 and 2
- * compute; Kernel 3 waits for it (the call creates and releases that stream
- * and its events itself, so it cannot be recorded into a CUDA graph).
+ * valid after the stream has been synchronised.  The copies run on a
+ * short-lived side stream (the call creates and releases it and its events
+ * itself, so it cannot be recorded into a CUDA graph): with 2*scale > 32 and
+ * M >= 2^20 the edge list crosses in four chunks and Kernel 1 sorts each
+ * chunk as soon as it has arrived, then merges the sorted chunks (the result
+ * is the sort pp_sort_edges gives); r0, which only Kernel 3 reads, is copied
+ * while Kernels 1 and 2 compute.
  */
 pp_status pp_pipeline_workspace(uint64_t M, uint32_t scale, uint32_t iters, pp_dtype dtype,
                                 size_t *bytes);

@@ -71,9 +71,12 @@ inline Layout layout(void *ws, uint64_t M, uint32_t scale) {
     return L;
 }
 
+// keys_out == nullptr: the last pass unpacks into (u_out, v_out); otherwise it
+// writes the sorted packed keys there (the chunked sort of the host-buffer
+// pipeline merges them afterwards).
 template <typename KeyT>
 void run(const uint32_t *u, const uint32_t *v, uint64_t M, uint32_t scale, uint32_t *u_out,
-         uint32_t *v_out, const Layout &L, cudaStream_t s) {
+         uint32_t *v_out, const Layout &L, cudaStream_t s, KeyT *keys_out = nullptr) {
     const int P = num_passes(scale);
     const size_t word = L.sort.wide ? 8 : 4;
     const uint64_t ntiles = ceil_div(M, os::TILE);
@@ -88,7 +91,10 @@ void run(const uint32_t *u, const uint32_t *v, uint64_t M, uint32_t scale, uint3
     const PackSrc<KeyT, false> pack{u, v, scale};
     const UnpackDst<KeyT> unpack{u_out, v_out, scale};
     if (P == 1) {
-        os::launch_pass<KeyT>(L.sort, 0, P, pack, unpack, nullptr, M, s);
+        if (keys_out)
+            os::launch_pass<KeyT>(L.sort, 0, P, pack, KeyDst<KeyT>{keys_out}, nullptr, M, s);
+        else
+            os::launch_pass<KeyT>(L.sort, 0, P, pack, unpack, nullptr, M, s);
         return;
     }
     os::launch_pass<KeyT>(L.sort, 0, P, pack, KeyDst<KeyT>{A}, nullptr, M, s);
@@ -98,10 +104,148 @@ void run(const uint32_t *u, const uint32_t *v, uint64_t M, uint32_t scale, uint3
         os::launch_pass<KeyT>(L.sort, p, P, KeySrc<KeyT>{in}, KeyDst<KeyT>{out}, nullptr, M, s);
     }
     KeyT *last_in = ((P - 1) & 1) ? A : B;
-    os::launch_pass<KeyT>(L.sort, P - 1, P, KeySrc<KeyT>{last_in}, unpack, nullptr, M, s);
+    if (keys_out)
+        os::launch_pass<KeyT>(L.sort, P - 1, P, KeySrc<KeyT>{last_in}, KeyDst<KeyT>{keys_out}, nullptr, M, s);
+    else
+        os::launch_pass<KeyT>(L.sort, P - 1, P, KeySrc<KeyT>{last_in}, unpack, nullptr, M, s);
 }
 
 }  // namespace k1
+
+// ---------------------------------------------------------------------------
+// Kernel 1 in chunks, for the host-buffer pipeline: each chunk of the edge
+// list is sorted into packed 64-bit keys as soon as its copy has arrived
+// (while the next chunk is still crossing the host link), and the sorted
+// chunks are merged pairwise.  The merged keys are the keys the single sort
+// produces (the order of equal keys cannot be told apart), so the output is
+// the same.  A merge follows the merge-path scheme (Green, McColl & Bader,
+// "GPU merge path", 2012): the output is cut into tiles, the split of each
+// tile boundary between the two inputs is found by a binary search along
+// the cross diagonal, and each tile is merged in shared memory.
+
+namespace k1m {
+
+constexpr int THREADS = 256;
+constexpr int ITEMS = 16;
+constexpr int TILE = THREADS * ITEMS;
+
+// Elements of a among the first k of the merge of a and b (a first on ties).
+__device__ __forceinline__ uint64_t corank(uint64_t k, const uint64_t *a, uint64_t na, const uint64_t *b,
+                                           uint64_t nb) {
+    uint64_t lo = k > nb ? k - nb : 0, hi = k < na ? k : na;
+    while (lo < hi) {
+        const uint64_t i = (lo + hi) >> 1;
+        if (__ldg(a + i) <= __ldg(b + (k - 1 - i)))
+            lo = i + 1;
+        else
+            hi = i;
+    }
+    return lo;
+}
+
+// split[t] = corank of output index min(t * TILE, na + nb), t = 0 .. tiles.
+__global__ void __launch_bounds__(256) split_kernel(const uint64_t *a, uint64_t na, const uint64_t *b, uint64_t nb,
+                                                    uint64_t tiles, uint64_t *split) {
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > tiles) return;
+    const uint64_t k = t * TILE < na + nb ? t * TILE : na + nb;
+    split[t] = corank(k, a, na, b, nb);
+}
+
+struct KeyOut {
+    uint64_t *k;
+    __device__ __forceinline__ void store(uint64_t i, uint64_t key) const { k[i] = key; }
+};
+struct UnpackOut {
+    uint32_t *u, *v;
+    uint32_t scale;
+    __device__ __forceinline__ void store(uint64_t i, uint64_t key) const {
+        u[i] = (uint32_t)(key >> scale);
+        v[i] = (uint32_t)(key & ((1ull << scale) - 1));
+    }
+};
+
+template <class Out>
+__global__ void __launch_bounds__(THREADS) merge_kernel(const uint64_t *a, uint64_t na, const uint64_t *b, uint64_t nb,
+                                                        const uint64_t *split, Out out) {
+    __shared__ uint64_t s[TILE];
+    const uint64_t n = na + nb;
+    const uint64_t k0 = (uint64_t)blockIdx.x * TILE, k1 = k0 + TILE < n ? k0 + TILE : n;
+    const uint64_t a0 = split[blockIdx.x], a1 = split[blockIdx.x + 1];
+    const uint64_t b0 = k0 - a0;
+    // la + lb = k1 - k0 <= TILE
+    const uint32_t la = (uint32_t)pp_len(0, a1 - a0, (uint64_t)TILE), total = (uint32_t)(k1 - k0);
+    const uint32_t lb = total - la;
+    for (uint32_t i = threadIdx.x; i < la; i += THREADS) s[i] = __ldg(a + a0 + i);
+    for (uint32_t i = threadIdx.x; i < lb; i += THREADS) s[pp_idx(la + i, (uint32_t)TILE)] = __ldg(b + b0 + i);
+    __syncthreads();
+    // thread t merges outputs [t * ITEMS, (t + 1) * ITEMS) of the tile
+    const uint32_t t0 = threadIdx.x * ITEMS;
+    uint64_t val[ITEMS];
+    if (t0 < total) {
+        uint32_t lo = t0 > lb ? t0 - lb : 0, hi = t0 < la ? t0 : la;
+        while (lo < hi) {
+            const uint32_t i = (lo + hi) >> 1;
+            if (s[i] <= s[la + (t0 - 1 - i)])
+                lo = i + 1;
+            else
+                hi = i;
+        }
+        uint32_t i = lo, j = t0 - lo;
+#pragma unroll
+        for (int q = 0; q < ITEMS; ++q) {
+            if (t0 + q < total) {
+                const bool take_a = j >= lb || (i < la && s[i] <= s[la + j]);
+                val[q] = take_a ? s[i++] : s[la + j++];
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < ITEMS; ++q)
+        if (t0 + q < total) s[t0 + q] = val[q];
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < total; i += THREADS) out.store(k0 + i, s[i]);
+}
+
+template <class Out>
+pp_status merge(const uint64_t *a, uint64_t na, const uint64_t *b, uint64_t nb, uint64_t *split, Out out,
+                cudaStream_t s) {
+    const uint64_t tiles = ceil_div(na + nb, TILE);
+    if (!tiles) return PP_OK;
+    split_kernel<<<(unsigned)ceil_div(tiles + 1, 256), 256, 0, s>>>(a, na, b, nb, tiles, split);
+    merge_kernel<Out><<<(unsigned)tiles, THREADS, 0, s>>>(a, na, b, nb, split, out);
+    count_launch(2);
+    return launch_status();
+}
+
+}  // namespace k1m
+
+size_t k1_chunk_workspace(uint64_t Mc, uint32_t scale) { return k1::layout(nullptr, Mc, scale).bytes; }
+
+size_t k1_merge_split_words(uint64_t n) { return ceil_div(n, k1m::TILE) + 1; }
+
+pp_status k1_sort_chunk_keys(const uint32_t *u, const uint32_t *v, uint64_t Mc, uint32_t scale, uint64_t *keys,
+                             void *ws, size_t ws_bytes, cudaStream_t s) {
+    if (2 * scale <= 32 || scale > 27) return PP_ERR_INVALID_ARG;  // 64-bit keys only
+    if (Mc == 0) return PP_OK;
+    const k1::Layout need = k1::layout(nullptr, Mc, scale);
+    pp_status st = check_ws(ws, ws_bytes, need.bytes);
+    if (st != PP_OK) return st;
+    k1::run<uint64_t>(u, v, Mc, scale, nullptr, nullptr, k1::layout(ws, Mc, scale), s, keys);
+    return launch_status();
+}
+
+pp_status k1_merge_keys(const uint64_t *a, uint64_t na, const uint64_t *b, uint64_t nb, uint64_t *out,
+                        uint64_t *split, cudaStream_t s) {
+    return k1m::merge(a, na, b, nb, split, k1m::KeyOut{out}, s);
+}
+
+pp_status k1_merge_unpack(const uint64_t *a, uint64_t na, const uint64_t *b, uint64_t nb, uint32_t scale,
+                          uint32_t *u_out, uint32_t *v_out, uint64_t *split, cudaStream_t s) {
+    return k1m::merge(a, na, b, nb, split, k1m::UnpackOut{u_out, v_out, scale}, s);
+}
+
 }  // namespace pp
 
 using namespace pp;

@@ -107,7 +107,26 @@ extern "C" pp_status pp_last_device_error(void *stream, uint32_t *code) {
     return w ? PP_ERR_DEVICE : PP_OK;
 }
 
+namespace pp {
+// Kernel 1 in chunks (k1_sort.cu), for the host-buffer pipeline.
+size_t k1_chunk_workspace(uint64_t Mc, uint32_t scale);
+size_t k1_merge_split_words(uint64_t n);
+pp_status k1_sort_chunk_keys(const uint32_t *u, const uint32_t *v, uint64_t Mc, uint32_t scale, uint64_t *keys,
+                             void *ws, size_t ws_bytes, cudaStream_t s);
+pp_status k1_merge_keys(const uint64_t *a, uint64_t na, const uint64_t *b, uint64_t nb, uint64_t *out,
+                        uint64_t *split, cudaStream_t s);
+pp_status k1_merge_unpack(const uint64_t *a, uint64_t na, const uint64_t *b, uint64_t nb, uint32_t scale,
+                          uint32_t *u_out, uint32_t *v_out, uint64_t *split, cudaStream_t s);
+}  // namespace pp
+
 namespace {
+
+// The host-buffer pipeline sorts the edge list in CHUNKS pieces while it
+// crosses the host link (64-bit keys, at least CHUNK_MIN_M edges).
+constexpr int CHUNKS = 4;
+constexpr uint64_t CHUNK_MIN_M = 1ull << 20;
+inline bool chunked(uint64_t M, uint32_t scale) { return 2 * scale > 32 && M >= CHUNK_MIN_M; }
+inline uint64_t chunk_begin(uint64_t M, int c) { return M * (uint64_t)c / CHUNKS; }
 
 struct PipeLayout {
     uint32_t *u, *v, *us, *vs;
@@ -116,6 +135,10 @@ struct PipeLayout {
     void *r_out;
     void *scratch;
     size_t scratch_bytes;
+    // the chunked sort, inside the scratch region (Kernels 2 and 3 reuse it after)
+    uint64_t *keys[2], *split;
+    void *chunk_ws;
+    size_t chunk_ws_bytes;
     size_t bytes;
 };
 
@@ -150,8 +173,27 @@ PipeLayout pipe_layout(void *ws, uint64_t M, uint32_t scale, uint32_t iters, pp_
     pp_sort_edges_workspace(M, scale, &b1);
     pp_build_filter_normalize_workspace(M, scale, &b2);
     pp_pagerank_workspace(M, scale, iters, dt, &b3);
-    L.scratch_bytes = std::max(b1, std::max(b2, b3));
+    // the chunked sort's buffers, carved from the start of the scratch region
+    Carver k(nullptr);
+    L.keys[0] = L.keys[1] = L.split = nullptr;
+    L.chunk_ws = nullptr;
+    L.chunk_ws_bytes = 0;
+    if (chunked(M, scale)) {
+        k.take<uint64_t>(M);
+        k.take<uint64_t>(M);
+        k.take<uint64_t>(k1_merge_split_words(M));
+        L.chunk_ws_bytes = k1_chunk_workspace(chunk_begin(M, 1) + 1, scale);
+        k.take<char>(L.chunk_ws_bytes);
+    }
+    L.scratch_bytes = std::max(std::max(b1, k.size()), std::max(b2, b3));
     L.scratch = c.take<char>(L.scratch_bytes);
+    if (L.scratch && chunked(M, scale)) {
+        Carver kc(L.scratch);
+        L.keys[0] = kc.take<uint64_t>(M);
+        L.keys[1] = kc.take<uint64_t>(M);
+        L.split = kc.take<uint64_t>(k1_merge_split_words(M));
+        L.chunk_ws = kc.take<char>(L.chunk_ws_bytes);
+    }
     L.bytes = c.size();
     return L;
 }
@@ -170,28 +212,59 @@ extern "C" pp_status pp_pipeline_workspace(uint64_t M, uint32_t scale, uint32_t 
 // event marking the end of what is enqueued on it.  Destroying them while
 // their work is pending is allowed: the runtime releases them when it ends.
 struct SideCopy {
+    static constexpr int EVENTS = CHUNKS + 1;
     cudaStream_t stream = nullptr;
-    cudaEvent_t start = nullptr, done = nullptr;
+    cudaEvent_t start = nullptr, done[EVENTS] = {};
     bool open(cudaStream_t s) {
-        if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&start, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventRecord(start, s) != cudaSuccess || cudaStreamWaitEvent(stream, start, 0) != cudaSuccess) {
+        bool ok = cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&start, cudaEventDisableTiming) == cudaSuccess;
+        for (int e = 0; e < EVENTS && ok; ++e) ok = cudaEventCreateWithFlags(&done[e], cudaEventDisableTiming) == cudaSuccess;
+        ok = ok && cudaEventRecord(start, s) == cudaSuccess && cudaStreamWaitEvent(stream, start, 0) == cudaSuccess;
+        if (!ok) {
             close();
             cudaGetLastError();
-            return false;
         }
-        return true;
+        return ok;
     }
     void close() {
         if (start) cudaEventDestroy(start);
-        if (done) cudaEventDestroy(done);
+        for (cudaEvent_t &e : done) {
+            if (e) cudaEventDestroy(e);
+            e = nullptr;
+        }
         if (stream) cudaStreamDestroy(stream);
-        start = done = nullptr;
+        start = nullptr;
         stream = nullptr;
     }
     ~SideCopy() { close(); }
 };
+
+// Kernel 1 of the host-buffer pipeline in chunks: chunk c's ids are copied
+// on the side stream (event done[c]); the main stream sorts each chunk into
+// packed keys once it has arrived, then merges the four sorted chunks in two
+// rounds, the last one writing the sorted (u, v).
+static pp_status sort_chunked(const PipeLayout &L, const uint32_t *u_host, const uint32_t *v_host, uint64_t M,
+                              uint32_t scale, SideCopy &side, cudaStream_t s) {
+    for (int c = 0; c < CHUNKS; ++c) {
+        const uint64_t b = chunk_begin(M, c), n = chunk_begin(M, c + 1) - b;
+        if (cudaMemcpyAsync(L.u + b, u_host + b, n * 4, cudaMemcpyHostToDevice, side.stream) != cudaSuccess ||
+            cudaMemcpyAsync(L.v + b, v_host + b, n * 4, cudaMemcpyHostToDevice, side.stream) != cudaSuccess ||
+            cudaEventRecord(side.done[c], side.stream) != cudaSuccess)
+            return PP_ERR_CUDA;
+    }
+    for (int c = 0; c < CHUNKS; ++c) {
+        const uint64_t b = chunk_begin(M, c), n = chunk_begin(M, c + 1) - b;
+        if (cudaStreamWaitEvent(s, side.done[c], 0) != cudaSuccess) return PP_ERR_CUDA;
+        pp_status st = k1_sort_chunk_keys(L.u + b, L.v + b, n, scale, L.keys[0] + b, L.chunk_ws, L.chunk_ws_bytes, s);
+        if (st != PP_OK) return st;
+    }
+    static_assert(CHUNKS == 4, "two merge rounds");
+    const uint64_t q1 = chunk_begin(M, 1), q2 = chunk_begin(M, 2), q3 = chunk_begin(M, 3);
+    pp_status st = k1_merge_keys(L.keys[0], q1, L.keys[0] + q1, q2 - q1, L.keys[1], L.split, s);
+    if (st == PP_OK) st = k1_merge_keys(L.keys[0] + q2, q3 - q2, L.keys[0] + q3, M - q3, L.keys[1] + q2, L.split, s);
+    if (st == PP_OK) st = k1_merge_unpack(L.keys[1], q2, L.keys[1] + q2, M - q2, scale, L.us, L.vs, L.split, s);
+    return st;
+}
 
 extern "C" pp_status pp_pipeline_host(const uint32_t *u_host, const uint32_t *v_host, uint64_t M,
                                       uint32_t scale, const double *r0_host, uint32_t iters, double c,
@@ -206,26 +279,36 @@ extern "C" pp_status pp_pipeline_host(const uint32_t *u_host, const uint32_t *v_
     const PipeLayout L = pipe_layout(ws, M, scale, iters, dt);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const uint64_t N = 1ull << scale;
-    if (M) {
-        if (cudaMemcpyAsync(L.u, u_host, M * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) return PP_ERR_CUDA;
-        if (cudaMemcpyAsync(L.v, v_host, M * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) return PP_ERR_CUDA;
-    }
-    // r0 is needed only by Kernel 3: its copy runs on a side stream while
-    // Kernels 1 and 2 compute (after the edge copies, which it would only
-    // slow down on the shared host link), and Kernel 3 waits for it.  The
-    // side stream and events are released once their work is done.
+    // The copies run on a side stream where one can be had: the edge list in
+    // chunks that Kernel 1 sorts as they arrive (large graphs), then r0, which
+    // only Kernel 3 reads, while Kernels 1 and 2 compute.  The side stream and
+    // its events are released once their work is done.
     SideCopy side;
-    if (side.open(s)) {
+    const bool split_copy = chunked(M, scale) && side.open(s);
+    if (split_copy) {
+        st = sort_chunked(L, u_host, v_host, M, scale, side, s);
+        if (st != PP_OK) return st;
+    } else {
+        if (M) {
+            if (cudaMemcpyAsync(L.u, u_host, M * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) return PP_ERR_CUDA;
+            if (cudaMemcpyAsync(L.v, v_host, M * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) return PP_ERR_CUDA;
+        }
+        side.open(s);  // after the edge copies, which the r0 copy would only slow down on the host link
+    }
+    const cudaEvent_t r0_done = side.stream ? side.done[CHUNKS] : nullptr;
+    if (r0_done) {
         if (cudaMemcpyAsync(L.r0, r0_host, N * 8, cudaMemcpyHostToDevice, side.stream) != cudaSuccess) return PP_ERR_CUDA;
-        if (cudaEventRecord(side.done, side.stream) != cudaSuccess) return PP_ERR_CUDA;
+        if (cudaEventRecord(r0_done, side.stream) != cudaSuccess) return PP_ERR_CUDA;
     } else if (cudaMemcpyAsync(L.r0, r0_host, N * 8, cudaMemcpyHostToDevice, s) != cudaSuccess) {
         return PP_ERR_CUDA;
     }
-    st = pp_sort_edges(L.u, L.v, M, scale, L.us, L.vs, L.scratch, L.scratch_bytes, stream);
-    if (st != PP_OK) return st;
+    if (!split_copy) {
+        st = pp_sort_edges(L.u, L.v, M, scale, L.us, L.vs, L.scratch, L.scratch_bytes, stream);
+        if (st != PP_OK) return st;
+    }
     st = pp_build_filter_normalize(L.us, L.vs, M, scale, rule, &L.g, L.scratch, L.scratch_bytes, stream);
     if (st != PP_OK) return st;
-    if (side.stream && cudaStreamWaitEvent(s, side.done, 0) != cudaSuccess) return PP_ERR_CUDA;
+    if (r0_done && cudaStreamWaitEvent(s, r0_done, 0) != cudaSuccess) return PP_ERR_CUDA;
     st = pp_pagerank(&L.g, L.r0, iters, c, dt, L.r_out, nullptr, L.scratch, L.scratch_bytes, stream);
     if (st != PP_OK) return st;
     if (cudaMemcpyAsync(r_out_host, L.r_out, N * (dt == PP_FP64 ? 8 : 4), cudaMemcpyDeviceToHost, s) != cudaSuccess)

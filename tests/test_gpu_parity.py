@@ -143,13 +143,36 @@ def test_pipeline_host_matches_device_path(pp, k0):
         assert info.tolist()[:7] == g.info.cpu().tolist()[:7]
 
 
-def test_pipeline_host_back_to_back_calls_keep_their_start_vectors(pp, k0):
-    """Two host-buffer pipelines enqueued back to back on one stream with one
-    workspace and different start vectors: the second call's copy of r0 (on a
-    side stream during Kernels 1-2) must not overtake the first call's Kernel 3."""
+@pytest.mark.parametrize("scale,M", [(16, None), (18, None), (18, 16 * (1 << 18) - 3), (20, None)])
+def test_pipeline_host_chunked_sort_matches_device_path(pp, k0, scale, M):
+    """From 2^20 edges with 64-bit keys the host-buffer pipeline sorts the
+    edge list in four chunks as they arrive and merges them: the sorted edges
+    (through Kernel 2's output), the scalars and the ranks equal the device
+    path's bit for bit, for ragged chunk boundaries too."""
     import torch
 
-    scale = 16
+    u, v, ud, vd = _inputs(k0, scale, M, 47)
+    N = 1 << scale
+    r0 = k0.r0_host(N, 47)
+    uh = torch.from_numpy(u.view(np.int32)).pin_memory()
+    vh = torch.from_numpy(v.view(np.int32)).pin_memory()
+    r0h = torch.from_numpy(r0).pin_memory()
+    r, info = pp.pipeline_host(uh, vh, scale, r0h, 20, 0.85, "fp32")
+    torch.cuda.synchronize()
+    us, vs = pp.sort_edges(ud, vd, scale)
+    g = pp.build_filter_normalize(us, vs, scale)
+    assert torch.equal(r, pp.pagerank(g, torch.from_numpy(r0).cuda(), 20, 0.85, "fp32").cpu())
+    assert info.tolist()[:7] == g.info.cpu().tolist()[:7]
+    assert pp.last_device_error() == 0
+
+
+@pytest.mark.parametrize("scale", [16, 18])
+def test_pipeline_host_back_to_back_calls_keep_their_start_vectors(pp, k0, scale):
+    """Two host-buffer pipelines enqueued back to back on one stream with one
+    workspace and different start vectors: the second call's copies (on a
+    side stream) must not overtake the first call's kernels."""
+    import torch
+
     u, v, ud, vd = _inputs(k0, scale, None, 43)
     N = 1 << scale
     uh = torch.from_numpy(u.view(np.int32)).pin_memory()
