@@ -446,6 +446,16 @@ pp_status pp_gather_probe(const uint32_t *rowc, uint64_t n, uint32_t scale, cons
  * the word was non-zero, PP_ERR_CUDA if synchronisation failed, else PP_OK. */
 pp_status pp_last_device_error(void *stream, uint32_t *code);
 
+/* Host-side fault injection, for testing how callers handle failures without
+ * making a GPU fail: the next `count` calls of the entry point named `call`
+ * (for example "pp_sort_edges"; "*" matches every entry point that enqueues
+ * work, and pp_last_device_error) return `status` at once, before checking
+ * their arguments, enqueueing anything or touching their outputs.  count 0
+ * disarms `call`.  Up to 16 names may be armed; process-wide, thread-safe.
+ * Returns PP_ERR_INVALID_ARG for a NULL or over-long name, for status PP_OK
+ * or out of range with count > 0, or when the table is full. */
+pp_status pp_inject_fault(const char *call, pp_status status, uint32_t count);
+
 /* How this library was compiled: PP_BUILD_CHECKED is set in the bounds-checked
  * build (libpp_checked.so), whose kernels compare every index they read from
  * memory, or compute from what they read, with the length of the array it

@@ -134,12 +134,20 @@ def _lib():
         L.pp_launch_count.restype = ctypes.c_uint64
         L.pp_build_flags.argtypes = []
         L.pp_build_flags.restype = ctypes.c_uint32
+        L.pp_inject_fault.argtypes = [ctypes.c_char_p, ctypes.c_int, ctypes.c_uint32]
+        L.pp_inject_fault.restype = ctypes.c_int
         _LIBS[_ACTIVE] = L
     return L
 
 
 def lib():
     return _lib()
+
+
+def inject_fault(call, status=PP_ERR_CUDA, count=1):
+    """Arms a host-side failure: the next `count` calls of the C entry point
+    `call` ("*": any) return `status` at once (count 0 disarms it)."""
+    _check("pp_inject_fault", _lib().pp_inject_fault(call.encode(), int(status), int(count)))
 
 
 def build_flags():

@@ -263,7 +263,7 @@ extern "C" pp_status pp_sort_edges_workspace(uint64_t M, uint32_t scale, size_t 
 extern "C" pp_status pp_sort_edges(const uint32_t *u, const uint32_t *v, uint64_t M, uint32_t scale,
                                    uint32_t *u_out, uint32_t *v_out, void *ws, size_t ws_bytes,
                                    void *stream) {
-    PP_RANGE("pp_sort_edges");
+    PP_ENTRY("pp_sort_edges");
     if (!k1_args_ok(M, scale)) return PP_ERR_INVALID_ARG;
     if (M == 0) return PP_OK;
     if (!u || !v || !u_out || !v_out) return PP_ERR_INVALID_ARG;
@@ -422,7 +422,7 @@ extern "C" pp_status pp_sort_edges_batched_workspace(uint32_t n_graphs, const ui
 extern "C" pp_status pp_sort_edges_batched(uint32_t n_graphs, const uint32_t *const *u, const uint32_t *const *v,
                                            const uint64_t *M, const uint32_t *scale, uint32_t *const *u_out,
                                            uint32_t *const *v_out, void *ws, size_t ws_bytes, void *stream) {
-    PP_RANGE("pp_sort_edges_batched");
+    PP_ENTRY("pp_sort_edges_batched");
     uint64_t Mtot;
     uint32_t S;
     if (!k1b::batch_shape(n_graphs, M, scale, &Mtot, &S) || !u || !v || !u_out || !v_out) return PP_ERR_INVALID_ARG;
@@ -547,7 +547,7 @@ pp_status static_scratch(void **out) {
 
 extern "C" pp_status pp_sort_edges_static(const uint32_t *u, const uint32_t *v, uint64_t M, uint32_t scale,
                                           uint32_t *u_out, uint32_t *v_out, void *stream) {
-    PP_RANGE("pp_sort_edges_static");
+    PP_ENTRY("pp_sort_edges_static");
     if (!k1_args_ok(M, scale) || M > kStaticMaxEdges) return PP_ERR_INVALID_ARG;
     if (M == 0) return PP_OK;
     if (!u || !v || !u_out || !v_out) return PP_ERR_INVALID_ARG;
@@ -597,7 +597,7 @@ SelftestLayout selftest_layout(void *ws) {
 
 extern "C" pp_status pp_selftest_lookback_timeout(uint32_t spin_limit, void *ws, size_t ws_bytes,
                                                   size_t *bytes_needed, void *stream) {
-    PP_RANGE("pp_selftest_lookback_timeout");
+    PP_ENTRY("pp_selftest_lookback_timeout");
     const size_t need = selftest_layout(nullptr).bytes;
     if (bytes_needed) *bytes_needed = need;
     if (!ws) return bytes_needed ? PP_OK : PP_ERR_INVALID_ARG;

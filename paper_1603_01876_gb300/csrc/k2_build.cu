@@ -1024,7 +1024,7 @@ inline pp_status run(const uint32_t *us, const uint32_t *vs, uint64_t M, uint32_
 extern "C" pp_status pp_build_filter_normalize(const uint32_t *us, const uint32_t *vs, uint64_t M,
                                                uint32_t scale, pp_supernode_rule rule, const pp_graph *g,
                                                void *ws, size_t ws_bytes, void *stream) {
-    PP_RANGE("pp_build_filter_normalize");
+    PP_ENTRY("pp_build_filter_normalize");
     if (scale < 1 || scale > 27 || M > (1ull << 31) || !g) return PP_ERR_INVALID_ARG;
     if (rule != PP_SUPERNODE_LOWEST && rule != PP_SUPERNODE_ALL_TIES) return PP_ERR_INVALID_ARG;
     if (g->scale != scale || g->M != M) return PP_ERR_INVALID_ARG;
@@ -1042,7 +1042,7 @@ extern "C" pp_status pp_build_filter_normalize(const uint32_t *us, const uint32_
 extern "C" pp_status pp_build_filter_normalize_rows(const uint32_t *us, const uint32_t *vs, uint64_t M,
                                                     uint32_t scale, pp_supernode_rule rule, const uint32_t *d_in_all,
                                                     const pp_graph *g, void *ws, size_t ws_bytes, void *stream) {
-    PP_RANGE("pp_build_filter_normalize_rows");
+    PP_ENTRY("pp_build_filter_normalize_rows");
     if (scale < 1 || scale > 27 || M > (1ull << 31) || !g || !d_in_all) return PP_ERR_INVALID_ARG;
     if (rule != PP_SUPERNODE_LOWEST && rule != PP_SUPERNODE_ALL_TIES) return PP_ERR_INVALID_ARG;
     if (g->scale != scale || g->M != M) return PP_ERR_INVALID_ARG;
@@ -1322,7 +1322,7 @@ extern "C" pp_status pp_build_filter_normalize_batched(uint32_t n_graphs, const 
                                                        const uint32_t *const *v_sorted, pp_supernode_rule rule,
                                                        const pp_graph *gs, void *ws, size_t ws_bytes,
                                                        void *stream) {
-    PP_RANGE("pp_build_filter_normalize_batched");
+    PP_ENTRY("pp_build_filter_normalize_batched");
     if (!gs || !u_sorted || !v_sorted || n_graphs < 1 || n_graphs > (uint32_t)k2b::MAX_G) return PP_ERR_INVALID_ARG;
     if (rule != PP_SUPERNODE_LOWEST && rule != PP_SUPERNODE_ALL_TIES) return PP_ERR_INVALID_ARG;
     uint64_t M[k2b::MAX_G];

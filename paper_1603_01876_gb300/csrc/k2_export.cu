@@ -209,7 +209,7 @@ extern "C" pp_status pp_export_csr_workspace(uint64_t M, uint32_t scale, size_t 
 extern "C" pp_status pp_export_csr(const pp_graph *g, uint64_t *rowptr, uint32_t *col, uint32_t *cnt,
                                    double *val64, float *val32, uint64_t cap, void *ws, size_t ws_bytes,
                                    void *stream) {
-    PP_RANGE("pp_export_csr");
+    PP_ENTRY("pp_export_csr");
     if (!g || !rowptr || (cap > 0 && (!col || !cnt))) return PP_ERR_INVALID_ARG;
     if (g->scale < 1 || g->scale > 27 || g->M > (1ull << 31)) return PP_ERR_INVALID_ARG;
     if (!g->colptr || !g->rowc || !g->ovf_key || !g->ovf_cnt || !g->d_out || !g->info || !g->perm || !g->iperm)

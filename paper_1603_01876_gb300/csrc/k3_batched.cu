@@ -720,7 +720,7 @@ extern "C" pp_status pp_pagerank_batched_workspace(const pp_graph *gs, uint32_t 
 extern "C" pp_status pp_pagerank_batched(const pp_graph *gs, uint32_t n_graphs, const double *r0, uint32_t nrhs,
                                          uint32_t iters, double c, float *r_out, void *ws, size_t ws_bytes,
                                          void *stream) {
-    PP_RANGE("pp_pagerank_batched");
+    PP_ENTRY("pp_pagerank_batched");
     uint64_t rows, edges;
     if (!batch_args_ok(gs, n_graphs, nrhs) || !k3b::batch_sizes(gs, n_graphs, rows, edges) || !r0 || !r_out ||
         !(c >= 0.0 && c <= 1.0))

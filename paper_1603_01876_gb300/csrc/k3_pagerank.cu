@@ -1096,7 +1096,7 @@ using namespace pp;
 
 extern "C" pp_status pp_gather_probe(const uint32_t *rowc, uint64_t n, uint32_t scale, const float *x, float *out,
                                      void *stream) {
-    PP_RANGE("pp_gather_probe");
+    PP_ENTRY("pp_gather_probe");
     if (scale < 1 || scale > 27 || (n && (!rowc || !x)) || !out) return PP_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     static PerDevice occ_dev;
@@ -1121,7 +1121,7 @@ extern "C" pp_status pp_pagerank_workspace(uint64_t M, uint32_t scale, uint32_t 
 
 extern "C" pp_status pp_pagerank(const pp_graph *g, const double *r0, uint32_t iters, double c, pp_dtype dt,
                                  void *r_out, double *r_l1, void *ws, size_t ws_bytes, void *stream) {
-    PP_RANGE("pp_pagerank");
+    PP_ENTRY("pp_pagerank");
     if (!g || !r0 || !r_out || (int)dt < 0 || (int)dt > 3) return PP_ERR_INVALID_ARG;
     if (g->scale < 1 || g->scale > 27 || g->M > (1ull << 31) || !(c >= 0.0 && c <= 1.0)) return PP_ERR_INVALID_ARG;
     if (!g->colptr || !g->rowc || !g->ovf_key || !g->ovf_cnt || !g->info || !g->perm || !g->iperm)
@@ -1155,7 +1155,7 @@ extern "C" pp_status pp_pagerank_ex_workspace(uint64_t M, uint32_t scale, uint32
 extern "C" pp_status pp_pagerank_ex(const pp_graph *g, const double *r0, uint32_t iters, double c, pp_dtype dt,
                                     uint32_t flags, double tol, void *r_out, double *r_l1, uint32_t *iters_done,
                                     void *ws, size_t ws_bytes, void *stream) {
-    PP_RANGE("pp_pagerank_ex");
+    PP_ENTRY("pp_pagerank_ex");
     if (!g || !r0 || !r_out || (int)dt < 0 || (int)dt > 3) return PP_ERR_INVALID_ARG;
     if (g->scale < 1 || g->scale > 27 || g->M > (1ull << 31) || !(c >= 0.0 && c <= 1.0)) return PP_ERR_INVALID_ARG;
     if (flags & ~(uint32_t)(PP_K3_DANGLING | PP_K3_CONVERGE)) return PP_ERR_INVALID_ARG;

@@ -86,7 +86,7 @@ using namespace pp;
 
 extern "C" pp_status pp_range_counts(const uint32_t *u_sorted, uint64_t M, const uint32_t *bounds, uint32_t parts,
                                      uint64_t *counts, void *stream) {
-    PP_RANGE("pp_range_counts");
+    PP_ENTRY("pp_range_counts");
     if (parts < 1 || !bounds || !counts || (M && !u_sorted)) return PP_ERR_INVALID_ARG;
     kr::range_counts_kernel<<<(parts + 127) / 128, 128, 0, static_cast<cudaStream_t>(stream)>>>(u_sorted, M, bounds,
                                                                                                 parts, counts);
@@ -95,7 +95,7 @@ extern "C" pp_status pp_range_counts(const uint32_t *u_sorted, uint64_t M, const
 }
 
 extern "C" pp_status pp_in_degree(const uint32_t *v, uint64_t M, uint32_t scale, uint32_t *d_in, void *stream) {
-    PP_RANGE("pp_in_degree");
+    PP_ENTRY("pp_in_degree");
     if (scale < 1 || scale > 27 || !d_in || (M && !v)) return PP_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const uint32_t N = 1u << scale;
@@ -110,7 +110,7 @@ extern "C" pp_status pp_in_degree(const uint32_t *v, uint64_t M, uint32_t scale,
 
 extern "C" pp_status pp_rank_update(const void *y, uint64_t n, double a, double b, void *r, double *r_sum,
                                     pp_dtype dtype, void *workspace, size_t workspace_bytes, void *stream) {
-    PP_RANGE("pp_rank_update");
+    PP_ENTRY("pp_rank_update");
     if ((n && (!y || !r)) || !r_sum || (dtype != PP_FP64 && dtype != PP_FP32)) return PP_ERR_INVALID_ARG;
     pp_status st = check_ws(workspace, workspace_bytes, kr::SUM_BLOCKS * sizeof(double));
     if (st != PP_OK) return st;

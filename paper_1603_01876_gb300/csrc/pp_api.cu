@@ -2,6 +2,7 @@
 // launch counter, and the host-buffer pipeline (Kernels 1-3 back to back).
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include "pp_common.cuh"
 
@@ -46,6 +47,32 @@ int64_t tuning(const char *key) {
     Knob *k = find_knob(key);
     return k ? k->value.load() : 0;
 }
+
+// Armed failures: the next `left` calls of entry point `name` ("*": any)
+// return `status`.
+namespace {
+struct Fault {
+    char name[64];
+    pp_status status;
+    uint32_t left;
+};
+constexpr int kMaxFaults = 16;
+Fault g_faults[kMaxFaults];
+std::mutex g_fault_mu;
+}  // namespace
+std::atomic<int> g_faults_armed{0};
+
+bool fault_hit(const char *name, pp_status *st) {
+    std::lock_guard<std::mutex> lock(g_fault_mu);
+    for (Fault &f : g_faults) {
+        if (f.left && (std::strcmp(f.name, name) == 0 || std::strcmp(f.name, "*") == 0)) {
+            *st = f.status;
+            if (--f.left == 0) g_faults_armed.fetch_sub(1, std::memory_order_relaxed);
+            return true;
+        }
+    }
+    return false;
+}
 }  // namespace pp
 
 using namespace pp;
@@ -70,6 +97,28 @@ extern "C" pp_status pp_get_tuning(const char *key, int64_t *value) {
 
 extern "C" uint64_t pp_launch_count(void) { return g_launches.load(); }
 
+extern "C" pp_status pp_inject_fault(const char *call, pp_status status, uint32_t count) {
+    if (!call || std::strlen(call) >= sizeof(((Fault *)nullptr)->name)) return PP_ERR_INVALID_ARG;
+    if (count && (status == PP_OK || (int)status < 0 || (int)status > PP_ERR_DEVICE)) return PP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_fault_mu);
+    Fault *slot = nullptr;
+    for (Fault &f : g_faults)
+        if (f.left && std::strcmp(f.name, call) == 0) slot = &f;
+    if (!slot && count)
+        for (Fault &f : g_faults)
+            if (!f.left) {
+                slot = &f;
+                break;
+            }
+    if (!slot) return count ? PP_ERR_INVALID_ARG : PP_OK;  // table full / nothing to clear
+    if (slot->left) g_faults_armed.fetch_sub(1, std::memory_order_relaxed);
+    std::strcpy(slot->name, call);
+    slot->status = status;
+    slot->left = count;
+    if (count) g_faults_armed.fetch_add(1, std::memory_order_relaxed);
+    return PP_OK;
+}
+
 extern "C" uint32_t pp_build_flags(void) {
     uint32_t f = 0;
 #ifdef PP_CHECKED
@@ -93,7 +142,7 @@ extern "C" const char *pp_status_string(pp_status st) {
 }
 
 extern "C" pp_status pp_last_device_error(void *stream, uint32_t *code) {
-    PP_RANGE("pp_last_device_error");
+    PP_ENTRY("pp_last_device_error");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (cudaStreamSynchronize(s) != cudaSuccess) return PP_ERR_CUDA;
     uint32_t w = 0;
@@ -270,7 +319,7 @@ extern "C" pp_status pp_pipeline_host(const uint32_t *u_host, const uint32_t *v_
                                       uint32_t scale, const double *r0_host, uint32_t iters, double c,
                                       pp_dtype dt, pp_supernode_rule rule, void *r_out_host,
                                       uint64_t *info_host, void *ws, size_t ws_bytes, void *stream) {
-    PP_RANGE("pp_pipeline_host");
+    PP_ENTRY("pp_pipeline_host");
     if (scale < 1 || scale > 27 || M > (1ull << 31) || (int)dt < 0 || (int)dt > 3) return PP_ERR_INVALID_ARG;
     if ((M && (!u_host || !v_host)) || !r0_host || !r_out_host) return PP_ERR_INVALID_ARG;
     const PipeLayout need = pipe_layout(nullptr, M, scale, iters, dt);
@@ -330,7 +379,7 @@ struct pp_exec {
 extern "C" pp_status pp_pagerank_batched_capture(const pp_graph *gs, uint32_t n_graphs, const double *r0,
                                                  uint32_t nrhs, uint32_t iters, double c, float *r_out, void *ws,
                                                  size_t ws_bytes, void *stream, pp_exec **exec) {
-    PP_RANGE("pp_pagerank_batched_capture");
+    PP_ENTRY("pp_pagerank_batched_capture");
     if (!exec) return PP_ERR_INVALID_ARG;
     *exec = nullptr;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -391,7 +440,7 @@ extern "C" pp_status pp_pipeline_batched_capture(uint32_t n_graphs, const uint32
                                                  const double *r0, uint32_t nrhs, uint32_t iters, double c,
                                                  float *r_out, void *ws, size_t ws_bytes, void *stream,
                                                  pp_exec **exec) {
-    PP_RANGE("pp_pipeline_batched_capture");
+    PP_ENTRY("pp_pipeline_batched_capture");
     if (!exec) return PP_ERR_INVALID_ARG;
     *exec = nullptr;
     uint64_t M[PP_BATCH_MAX_GRAPHS];
@@ -432,7 +481,7 @@ extern "C" pp_status pp_pipeline_batched_capture(uint32_t n_graphs, const uint32
 }
 
 extern "C" pp_status pp_exec_launch(pp_exec *exec, void *stream) {
-    PP_RANGE("pp_exec_launch");
+    PP_ENTRY("pp_exec_launch");
     if (!exec) return PP_ERR_INVALID_ARG;
     if (cudaGraphLaunch(exec->exec, static_cast<cudaStream_t>(stream)) != cudaSuccess) return PP_ERR_CUDA;
     count_launch(exec->kernels);

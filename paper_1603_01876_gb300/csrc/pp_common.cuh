@@ -82,6 +82,22 @@ struct Range {
 };
 #define PP_RANGE(name) ::pp::Range pp_call_range_(name)
 
+// Host-side fault injection (pp_inject_fault): true, with the status to
+// return, when a failure is armed for the entry point `name`.  One relaxed
+// load when nothing is armed.
+extern std::atomic<int> g_faults_armed;
+bool fault_hit(const char *name, pp_status *st);
+
+// The first statement of every entry point that enqueues work: its NVTX
+// range, then an armed failure returned before anything is checked or run.
+#define PP_ENTRY(name)                                                                      \
+    PP_RANGE(name);                                                                         \
+    do {                                                                                    \
+        pp_status pp_fault_st_;                                                             \
+        if (::pp::g_faults_armed.load(std::memory_order_relaxed) && ::pp::fault_hit(name, &pp_fault_st_)) \
+            return pp_fault_st_;                                                            \
+    } while (0)
+
 // Number of kernels enqueued by the library (pp_launch_count).
 extern std::atomic<uint64_t> g_launches;
 

@@ -380,7 +380,7 @@ extern "C" pp_status pp_format_tsv_workspace(uint64_t M, size_t *bytes) {
 
 extern "C" pp_status pp_format_tsv(const uint32_t *u, const uint32_t *v, uint64_t M, char *text, uint64_t text_cap,
                                    uint64_t *text_len, void *ws, size_t ws_bytes, void *stream) {
-    PP_RANGE("pp_format_tsv");
+    PP_ENTRY("pp_format_tsv");
     if (M > (1ull << 31) || !text_len || (M && (!u || !v || !text))) return PP_ERR_INVALID_ARG;
     if (text_cap < M * (uint64_t)PP_TSV_MAX_LINE) return PP_ERR_INVALID_ARG;
     const uint64_t tiles = tsv::format_tiles(M);
@@ -408,7 +408,7 @@ extern "C" pp_status pp_parse_tsv_workspace(uint64_t text_len, size_t *bytes) {
 
 extern "C" pp_status pp_parse_tsv(const char *text, uint64_t text_len, uint32_t *u, uint32_t *v, uint64_t m_cap,
                                   uint64_t *m_out, void *ws, size_t ws_bytes, void *stream) {
-    PP_RANGE("pp_parse_tsv");
+    PP_ENTRY("pp_parse_tsv");
     if (text_len > (1ull << 31) * (uint64_t)PP_TSV_MAX_LINE || !m_out || (text_len && !text) ||
         (m_cap && (!u || !v)))
         return PP_ERR_INVALID_ARG;
