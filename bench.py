@@ -484,7 +484,11 @@ def run_ours(args):
                         "run in a child process beside the GPU timing (or the cached result of an earlier such "
                         "run); `value` above is the bounded sample"}
     if rank == 0:
-        print(json.dumps(out))
+        line = json.dumps(out)
+        print(line)
+        if args.log:
+            with open(args.log, "a") as f:  # one run per line
+                f.write(line + "\n")
     if world > 1:
         torch.distributed.destroy_process_group()
 
@@ -829,6 +833,8 @@ def main():
                     help="set a library tuning knob before running (repeatable)")
     ap.add_argument("--stage", choices=["all", "k1", "k2", "k3", "gather-ceiling", "batched"], default="all",
                     help="k1 / k2 / k3: time one kernel alone (profiling aid); the default times the whole pipeline")
+    ap.add_argument("--log", default=None, metavar="FILE",
+                    help="also append the result line to FILE (JSON lines, one per run)")
     ap.add_argument("--tuning", default="default",
                     help="autotuner result to apply (JSON from paper_1603_01876_gb300.tune; 'none' to skip)")
     args = ap.parse_args()

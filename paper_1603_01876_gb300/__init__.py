@@ -613,3 +613,69 @@ def pipeline_host(u, v, scale, r0, iters=20, c=0.85, dtype="fp32", rule="lowest"
                                  _ptr(out), _ptr(info), _ptr(ws), ws.numel(), _stream(stream, ws.device))
     _check("pp_pipeline_host", st)
     return out, info
+
+
+# ------------------------------------------------------------------ tracing
+# CUDA events around each call of the kernels' entry points while a trace is
+# open: trace() records, per call, the device time between an event recorded
+# on the call's stream before it and one after it (the NVTX ranges of the
+# library name the same calls for external profilers).
+_TRACE = None
+_TRACED = ("sort_edges", "build_filter_normalize", "pagerank", "pagerank_ex", "export_csr", "sort_edges_batched",
+           "build_filter_normalize_batched", "pagerank_batched", "pipeline_host", "format_tsv", "parse_tsv",
+           "build_filter_normalize_rows", "rank_update", "range_counts", "in_degree")
+
+
+class Trace:
+    """The calls recorded by `with trace() as t:`; t.report() (after the
+    block) synchronises and lists (call, device ms) in call order."""
+
+    def __init__(self):
+        self.calls = []
+
+    def report(self):
+        if self.calls:
+            torch.cuda.synchronize()
+        return [(name, a.elapsed_time(b)) for name, a, b in self.calls]
+
+    def totals(self):
+        out = {}
+        for name, ms in self.report():
+            n, t = out.get(name, (0, 0.0))
+            out[name] = (n + 1, t + ms)
+        return out
+
+
+class trace:
+    def __enter__(self):
+        global _TRACE
+        self.prev, _TRACE = _TRACE, Trace()
+        return _TRACE
+
+    def __exit__(self, *exc):
+        global _TRACE
+        _TRACE = self.prev
+        return False
+
+
+def _traced(fn):
+    import functools
+
+    @functools.wraps(fn)
+    def wrapper(*args, **kwargs):
+        if _TRACE is None:
+            return fn(*args, **kwargs)
+        stream = kwargs.get("stream") or torch.cuda.current_stream()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        result = fn(*args, **kwargs)
+        b.record(stream)
+        _TRACE.calls.append((fn.__name__, a, b))
+        return result
+
+    return wrapper
+
+
+for _name in _TRACED:
+    globals()[_name] = _traced(globals()[_name])
+del _name
