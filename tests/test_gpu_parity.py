@@ -185,3 +185,33 @@ def test_pipeline_host_back_to_back_calls_keep_their_start_vectors(pp, k0, scale
     g = pp.build_filter_normalize(us, vs, scale)
     for r0, got in zip(r0s, outs):
         assert torch.equal(got, pp.pagerank(g, r0.cuda(), 20, 0.85, "fp32").cpu())
+
+
+# other seeds, scales between the fixed cases, and other edge factors (M = 2N
+# .. 64N: sparser graphs with more leaves and empty columns, denser ones with
+# more duplicate edges and longer columns)
+SWEEP = [(13, None, 101), (15, 5 * (1 << 15) + 3, 102), (16, 2 * (1 << 16), 103), (16, 64 * (1 << 16), 104),
+         (18, None, 105), (19, 4 * (1 << 19) - 1, 106), (21, None, 107), (22, None, 108)]
+
+
+@pytest.mark.parametrize("scale,M,seed", SWEEP, ids=["s%d_m%s_seed%d" % c for c in SWEEP])
+def test_sweep_parity(pp, k0, oracle_mod, scale, M, seed):
+    import torch
+
+    N = 1 << scale
+    u, v, ud, vd = _inputs(k0, scale, M, seed)
+    us, vs = pp.sort_edges(ud, vd, scale)
+    ous, ovs = oracle_mod.k1_sort(u, v)
+    assert np.array_equal(host_u32(us), ous) and np.array_equal(host_u32(vs), ovs)
+    del u, v
+    g = pp.build_filter_normalize(us, vs, scale)
+    R = oracle_mod.k2_filter(ous, ovs, N)
+    check_k2(pp, g, R)
+    r0 = k0.r0_host(N, seed)
+    want = oracle_mod.k3_pagerank(R, r0, 20, 0.85)
+    r0d = torch.from_numpy(r0).cuda()
+    for dt in ("fp64", "fp32"):
+        e = rank_errors(pp.pagerank(g, r0d, 20, 0.85, dt).cpu().numpy(), want)
+        l1, mr = TOL[dt]
+        assert e["l1"] <= l1 and e["max_rel"] <= mr, (dt, e)
+    assert pp.last_device_error() == 0
