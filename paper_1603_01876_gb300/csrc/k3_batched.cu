@@ -628,10 +628,15 @@ __global__ void __launch_bounds__(THREADS) iterate_vec_kernel(const __grid_const
             for (uint32_t k = lane; k < nent; k += 32) rowc_s[k] = ld_stream_u32(G.rowc + e0 + k, stream);
             __syncwarp();
             for (uint32_t ci = 0; ci < ncol; ++ci) {
-                KSum4 ks{};
                 const uint32_t lo = cp[ci], hi = lo + pp_len(lo, cp[ci + 1] - lo, nent);
+                const float invc = __shfl_sync(0xffffffffu, myinv, ci);
+                if (lo == hi) {  // a column without entries (most of them): y = 0, no reduction
+                    epi(c0 + ci, 0.f, invc);
+                    continue;
+                }
+                KSum4 ks{};
                 vec_accumulate(G, rowc_s, lo, hi, xg, c0 + ci, slot, quad, keep, ks);
-                epi(c0 + ci, vec_total(ks, lane), __shfl_sync(0xffffffffu, myinv, ci));
+                epi(c0 + ci, vec_total(ks, lane), invc);
             }
             __syncwarp();
         }
