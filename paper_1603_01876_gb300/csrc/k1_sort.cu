@@ -18,13 +18,25 @@ template <typename KeyT, bool CHECK>
 struct PackSrc {
     const uint32_t *u, *v;
     uint32_t scale;
+    bool vec;  // u and v are 16-byte aligned: four ids per load (see has_load4)
     __device__ __forceinline__ bool load(uint64_t i, KeyT &k, uint32_t &) const {
         const uint32_t a = __ldg(u + i), b = __ldg(v + i);
         if (CHECK && ((a | b) >> scale)) pp_set_error(PP_DEV_RANGE);
         k = ((KeyT)a << scale) | (KeyT)b;
         return true;
     }
+    __device__ __forceinline__ void load4(uint64_t i4, KeyT *k) const {
+        const uint4 a = __ldg(reinterpret_cast<const uint4 *>(u + i4));
+        const uint4 b = __ldg(reinterpret_cast<const uint4 *>(v + i4));
+        if (CHECK && ((a.x | a.y | a.z | a.w | b.x | b.y | b.z | b.w) >> scale)) pp_set_error(PP_DEV_RANGE);
+        k[0] = ((KeyT)a.x << scale) | (KeyT)b.x;
+        k[1] = ((KeyT)a.y << scale) | (KeyT)b.y;
+        k[2] = ((KeyT)a.z << scale) | (KeyT)b.z;
+        k[3] = ((KeyT)a.w << scale) | (KeyT)b.w;
+    }
 };
+
+inline bool aligned16(const void *a, const void *b) { return (((uintptr_t)a | (uintptr_t)b) & 15u) == 0; }
 
 template <typename KeyT>
 struct KeySrc {
@@ -82,13 +94,14 @@ void run(const uint32_t *u, const uint32_t *v, uint64_t M, uint32_t scale, uint3
     const uint64_t ntiles = ceil_div(M, os::TILE);
     cudaMemsetAsync(L.sort.hist, 0, os::kCtlBytes, s);
     const unsigned hgrid = (unsigned)std::min<uint64_t>(ceil_div(M, 256 * 8), (uint64_t)sm_count() * 8);
+    const bool vec = aligned16(u, v);
     os::hist_kernel<KeyT, PackSrc<KeyT, true>><<<hgrid ? hgrid : 1, 256, 0, s>>>(
-        PackSrc<KeyT, true>{u, v, scale}, nullptr, M, P, L.sort.hist,
+        PackSrc<KeyT, true>{u, v, scale, vec}, nullptr, M, P, L.sort.hist,
         static_cast<uint32_t *>(L.sort.status[0]), ntiles * os::RADIX * word / 4);
     count_launch();
     KeyT *A = static_cast<KeyT *>(L.keys[0]);
     KeyT *B = static_cast<KeyT *>(L.keys[1]);
-    const PackSrc<KeyT, false> pack{u, v, scale};
+    const PackSrc<KeyT, false> pack{u, v, scale, vec};
     const UnpackDst<KeyT> unpack{u_out, v_out, scale};
     if (P == 1) {
         if (keys_out)

@@ -23,6 +23,8 @@
 // pass, or writes Kernel 2's permutation from its vertex keys.
 #pragma once
 
+#include <type_traits>
+
 #include "pp_common.cuh"
 
 namespace pp {
@@ -63,6 +65,14 @@ struct PassCtl {
     uint64_t n_host;
     uint32_t spin_limit;    // empty polls before a look-back gives up
 };
+
+// A source with `load4(i4, k)` (four consecutive elements from i4, a multiple
+// of 4) and a `vec` flag (its arrays are 16-byte aligned) is read with
+// 16-byte loads where a whole tile is present.
+template <class S, class = void>
+struct has_load4 : std::false_type {};
+template <class S>
+struct has_load4<S, std::void_t<decltype(&S::load4)>> : std::true_type {};
 
 // Status words are 32-bit while every count fits in 30 bits.
 inline bool wide_status(uint64_t n_max) { return n_max >= (1ull << 30); }
@@ -112,10 +122,25 @@ __global__ void __launch_bounds__(THREADS, PASS_MINB) pass_kernel(Src src, Dst d
     {
         KeyT keys[ITEMS];
         uint32_t unused;
+        bool loaded = false;
+        if constexpr (has_load4<Src>::value) {
+            // Only the first pass reads such a source, and the first pass may take
+            // its input in any fixed order (the sort's result does not depend on
+            // it): item 4q + j of a lane is element 128 q + 4 lane + j of the warp's
+            // range, four ids per 16-byte load.  Whole warp ranges only, so that
+            // every element of a range is read by exactly one of the two layouts.
+            if (src.vec && base + (uint64_t)ITEMS * 32 <= n) {
 #pragma unroll
-        for (int i = 0; i < ITEMS; ++i) {
-            keys[i] = 0;
-            if (i < nv) src.load(base + (uint64_t)i * 32 + lane, keys[i], unused);
+                for (int q = 0; q < ITEMS / 4; ++q) src.load4(base + 128ull * q + 4ull * lane, &keys[4 * q]);
+                loaded = true;
+            }
+        }
+        if (!loaded) {
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                keys[i] = 0;
+                if (i < nv) src.load(base + (uint64_t)i * 32 + lane, keys[i], unused);
+            }
         }
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
@@ -243,7 +268,21 @@ __global__ void __launch_bounds__(256) hist_kernel(Src src, const uint64_t *n_de
     __syncthreads();
     const uint64_t n = n_dev ? *n_dev : n_host;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if constexpr (has_load4<Src>::value) {
+        if (src.vec) {  // whole groups of four with 16-byte loads, the rest below one by one
+            for (; 4 * i0 + 4 <= n; i0 += stride) {
+                KeyT k4[4];
+                src.load4(4 * i0, k4);
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    for (int p = 0; p < npasses; ++p)
+                        atomicAdd(&sh[p][(uint32_t)(k4[j] >> (shift0 + 8 * p)) & (RADIX - 1)], 1u);
+            }
+            i0 = (n & ~3ull) + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;  // the tail, one by one
+        }
+    }
+    for (uint64_t i = i0; i < n; i += stride) {
         KeyT k;
         uint32_t val;
         if (!src.load(i, k, val)) continue;

@@ -175,7 +175,8 @@ namespace {
 constexpr int CHUNKS = 4;
 constexpr uint64_t CHUNK_MIN_M = 1ull << 20;
 inline bool chunked(uint64_t M, uint32_t scale) { return 2 * scale > 32 && M >= CHUNK_MIN_M; }
-inline uint64_t chunk_begin(uint64_t M, int c) { return M * (uint64_t)c / CHUNKS; }
+// chunk boundaries on multiples of 4 ids, so that every chunk starts 16-byte aligned
+inline uint64_t chunk_begin(uint64_t M, int c) { return c >= CHUNKS ? M : (M * (uint64_t)c / CHUNKS) & ~3ull; }
 
 struct PipeLayout {
     uint32_t *u, *v, *us, *vs;
@@ -231,7 +232,7 @@ PipeLayout pipe_layout(void *ws, uint64_t M, uint32_t scale, uint32_t iters, pp_
         k.take<uint64_t>(M);
         k.take<uint64_t>(M);
         k.take<uint64_t>(k1_merge_split_words(M));
-        L.chunk_ws_bytes = k1_chunk_workspace(chunk_begin(M, 1) + 1, scale);
+        L.chunk_ws_bytes = k1_chunk_workspace(M / CHUNKS + 4, scale);  // the largest chunk (boundaries rounded to 4)
         k.take<char>(L.chunk_ws_bytes);
     }
     L.scratch_bytes = std::max(std::max(b1, k.size()), std::max(b2, b3));
