@@ -89,7 +89,7 @@ typedef enum {
  *   rowc[M]      entry e (e < nnz) packs the position perm[u] of its row u
  *                (= start vertex) in its low `scale` bits and the count
  *                A(u,v) in the high 32-scale bits; within a column the
- *                positions ascend.  A count >= 2^(32-scale)-1 is stored as the
+ *                rows' vertex ids u ascend.  A count >= 2^(32-scale)-1 is stored as the
  *                all-ones field and found in the overflow table.
  *   perm[N], iperm[N]  the storage order of rows and columns: vertices by
  *                decreasing floor(log2(out-degree before the column

@@ -1,21 +1,20 @@
 // Kernel 2 (Sec. IV-C): build, filter and normalise the adjacency matrix.
 //
-//   stats_kernel     per row of Kernel 1's sorted output: its edges (the
-//                    out-degree before filtering) and its distinct (u, v)
-//                    pairs (entries).
+//   unique_kernel    step 1: run-lengths of equal (u, v) in Kernel 1's sorted
+//                    output are the counts A(u,v); output offsets by a
+//                    decoupled look-back over tiles.  Each entry is written
+//                    as one 64-bit word (column << 32 | row | count << scale)
+//                    in vertex order, its column digits go to the
+//                    transpose's histograms, and each row's edges (the
+//                    out-degree before filtering) and entries are counted.
 //   relabel          rows ordered by decreasing floor(log2(out-degree)),
 //                    vertex id breaking ties (a one-pass radix sort of the
 //                    vertices): perm / iperm, the storage order of the rows
-//                    that Kernel 3 gathers from; two scans give each row's
-//                    first entry in vertex order and in position order.
-//   unique_kernel    step 1: run-lengths of equal (u, v) are the counts
-//                    A(u,v); output offsets by a decoupled look-back over
-//                    tiles.  Each entry is written as one 64-bit word
-//                    (column << 32 | row position | count << scale) at its
-//                    place in row-position order, and its column digits go
-//                    to the transpose's histograms.
-//   transpose        stable LSD radix sort of the entry words by column (row
-//                    positions stay ascending inside a column).
+//                    and columns that Kernel 3 gathers from.
+//   transpose        stable LSD radix sort of the entry words by column; the
+//                    first pass puts each row's position in place of its
+//                    vertex id (reading perm in ascending vertex order), and
+//                    inside a column the rows stay in vertex order.
 //   colscan_kernel   step 2: with the entries grouped by column, the entry
 //                    count and d_in = sum(A,1) of each column, one atomic per
 //                    run of a column inside a thread's stretch.
@@ -118,8 +117,8 @@ struct UniqueArgs {
     uint64_t *ovf_key;
     uint32_t *ovf_cnt;
     uint32_t n_vert;          // N
-    const uint32_t *delta;    // [N]: first entry of row u in position order minus in vertex order (mod 2^32)
-    const uint32_t *perm;     // [N]: row positions
+    uint32_t *d_out;          // [N] edges of each row (the out-degree before the filters), zero on entry
+    uint32_t *row_nent;       // [N] entries (distinct (u, v)) of each row, zero on entry
     uint32_t *hist;           // [npasses * 256] column digits, for the transpose
     int npasses;
     int vec;                  // us and vs are 16-byte aligned: load 4 ids at a time
@@ -141,7 +140,6 @@ __global__ void __launch_bounds__(UQ_THREADS, 3) unique_kernel(UniqueArgs a) {
     const int tid = threadIdx.x;
     for (int i = tid; i < os::MAX_PASSES * os::RADIX; i += UQ_THREADS) (&s_hist[0][0])[i] = 0;
     const uint64_t ntiles = uq_tiles(a.M);
-    const uint32_t umask = (a.scale >= 32) ? 0xffffffffu : ((1u << a.scale) - 1u);
     while (true) {
         if (tid == 0) s_tile = atomicAdd(a.tile_ctr, 1u);
         __syncthreads();
@@ -167,6 +165,33 @@ __global__ void __launch_bounds__(UQ_THREADS, 3) unique_kernel(UniqueArgs a) {
             for (int j = 0; j < UQ_ITEMS; ++j) k[j] = (my0 + j < a.M) ? edge_key(a.us, a.vs, my0 + j) : ~0ull;
         }
         const uint64_t knext = (my0 + UQ_ITEMS < a.M) ? edge_key(a.us, a.vs, my0 + UQ_ITEMS) : ~0ull;
+
+        // each row's edges (the out-degree before the filters) and entries,
+        // one atomic per array for each run of a row in this thread's edges;
+        // an edge with an id >= N is no edge of any row (reported below)
+        {
+            uint32_t row = 0xffffffffu, edges = 0, entries = 0;
+#pragma unroll
+            for (int j = 0; j < UQ_ITEMS; ++j) {
+                if (my0 + j >= a.M) break;
+                if ((k[j] >> 32) >= (uint64_t)a.n_vert || (uint32_t)k[j] >= a.n_vert) continue;
+                const uint32_t u = (uint32_t)(k[j] >> 32);
+                if (u != row) {
+                    if (edges) {
+                        atomicAdd(&a.d_out[row], edges);
+                        atomicAdd(&a.row_nent[row], entries);
+                    }
+                    row = u;
+                    edges = entries = 0;
+                }
+                ++edges;
+                entries += k[j] != (j + 1 < UQ_ITEMS ? k[j + 1] : knext);  // a run of equal (u, v) ends here
+            }
+            if (edges) {
+                atomicAdd(&a.d_out[row], edges);
+                atomicAdd(&a.row_nent[row], entries);
+            }
+        }
 
         // A run ends ("tail") where the next key differs.
         uint32_t tails = 0;
@@ -275,16 +300,10 @@ __global__ void __launch_bounds__(UQ_THREADS, 3) unique_kernel(UniqueArgs a) {
         }
         __syncthreads();
         {
-            // entry i of the tile (vertex order g = first + i) goes to g + delta[u]:
-            // a row's entries stay together, rows move to their positions
-            const uint32_t first = (uint32_t)(s_excl & 0xffffffffull);
+            // the tile's entries in vertex order, one coalesced run
+            const uint64_t first = s_excl & 0xffffffffull;
             const uint32_t n_out = (uint32_t)total;
-            for (uint32_t i = tid; i < n_out; i += UQ_THREADS) {
-                const unsigned long long w = s_out[i + i / 16];
-                const uint32_t u = (uint32_t)w & umask;
-                a.ent[pp_idx((uint32_t)(first + i + __ldg(a.delta + u)), a.M)] =
-                    (w & ~(unsigned long long)umask) | __ldg(a.perm + u);
-            }
+            for (uint32_t i = tid; i < n_out; i += UQ_THREADS) a.ent[pp_idx(first + i, a.M)] = s_out[i + i / 16];
         }
         __syncthreads();  // shared scratch is reused by the next tile
     }
@@ -292,111 +311,6 @@ __global__ void __launch_bounds__(UQ_THREADS, 3) unique_kernel(UniqueArgs a) {
     for (int i = tid; i < a.npasses * os::RADIX; i += UQ_THREADS) {
         const uint32_t c = (&s_hist[0][0])[i];
         if (c) atomicAdd(&a.hist[i], c);
-    }
-}
-
-// Edges (the out-degree before filtering) and entries (distinct (u, v)) of
-// every row, from Kernel 1's sorted output: each thread takes 16 consecutive
-// edges and adds each row's run with one atomic per array.
-__global__ void __launch_bounds__(256) stats_kernel(const uint32_t *us, const uint32_t *vs, uint64_t M,
-                                                    uint32_t umask, int vec, uint32_t *d_out, uint32_t *row_nent) {
-    constexpr int ITEMS = 16;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * ITEMS;
-    for (uint64_t i0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * ITEMS; i0 < M; i0 += stride) {
-        uint64_t k[ITEMS + 1];
-        if (vec && i0 + ITEMS <= M) {
-            // 16-byte loads (i0 is a multiple of 16 elements)
-            const uint4 *pu = reinterpret_cast<const uint4 *>(us + i0);
-            const uint4 *pv = reinterpret_cast<const uint4 *>(vs + i0);
-#pragma unroll
-            for (int q = 0; q < ITEMS / 4; ++q) {
-                const uint4 x = __ldg(pu + q), y = __ldg(pv + q);
-                k[4 * q + 0] = ((uint64_t)x.x << 32) | y.x;
-                k[4 * q + 1] = ((uint64_t)x.y << 32) | y.y;
-                k[4 * q + 2] = ((uint64_t)x.z << 32) | y.z;
-                k[4 * q + 3] = ((uint64_t)x.w << 32) | y.w;
-            }
-            k[ITEMS] = (i0 + ITEMS < M) ? edge_key(us, vs, i0 + ITEMS) : ~0ull;
-        } else {
-#pragma unroll
-            for (int j = 0; j <= ITEMS; ++j) k[j] = (i0 + j < M) ? edge_key(us, vs, i0 + j) : ~0ull;
-        }
-        uint32_t row = 0xffffffffu, edges = 0, entries = 0;
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            if (i0 + j >= M) break;
-            // an edge with an id >= N is no entry (the unique pass reports it)
-            if (((k[j] >> 32) | (k[j] & 0xffffffffull)) > (uint64_t)umask) continue;
-            const uint32_t u = (uint32_t)(k[j] >> 32);
-            if (u != row) {
-                if (edges) {
-                    atomicAdd(&d_out[row], edges);
-                    atomicAdd(&row_nent[row], entries);
-                }
-                row = u;
-                edges = entries = 0;
-            }
-            ++edges;
-            entries += k[j] != k[j + 1];  // a run of equal (u, v) ends here
-        }
-        if (edges) {
-            atomicAdd(&d_out[row], edges);
-            atomicAdd(&row_nent[row], entries);
-        }
-    }
-}
-
-// Exclusive scans of the rows' entry counts, in vertex order (uoff) and in
-// position order; delta[u] = (first entry of row u in position order) -
-// (first entry in vertex order), mod 2^32.  One look-back scan per kernel.
-struct OffArgs {
-    const uint32_t *row_nent;
-    const uint32_t *iperm;  // nullptr: vertex order
-    uint32_t N;
-    uint32_t *uoff;         // written in vertex order, read in position order
-    uint32_t *delta;
-    uint64_t *status;
-    uint32_t *tile_ctr;
-};
-
-__global__ void __launch_bounds__(SC_THREADS) offsets_kernel(OffArgs a) {
-    __shared__ uint32_t s_tile;
-    __shared__ uint64_t s_scan[40];
-    __shared__ uint64_t s_excl;
-    const int tid = threadIdx.x;
-    if (tid == 0) s_tile = atomicAdd(a.tile_ctr, 1u);
-    __syncthreads();
-    const uint64_t tile = s_tile;
-    const uint64_t ntiles = (a.N + SC_TILE - 1) / SC_TILE;
-    if (tile >= ntiles) return;
-    const uint64_t p0 = tile * SC_TILE + (uint64_t)tid * SC_ITEMS;
-    uint32_t cnt[SC_ITEMS], who[SC_ITEMS];
-    uint64_t sum = 0;
-#pragma unroll
-    for (int j = 0; j < SC_ITEMS; ++j) {
-        const uint64_t p = p0 + j;
-        who[j] = 0;
-        cnt[j] = 0;
-        if (p < a.N) {
-            who[j] = a.iperm ? pp_idx(a.iperm[p], a.N) : (uint32_t)p;
-            cnt[j] = a.row_nent[who[j]];
-        }
-        sum += cnt[j];
-    }
-    uint64_t total;
-    const uint64_t ex = block_exclusive_sum<uint64_t, SC_THREADS>(sum, s_scan, &total);
-    if (tid < 32) warp_tile_prefix(a.status, tile, total, &s_excl);
-    __syncthreads();
-    uint64_t run = s_excl + ex;
-#pragma unroll
-    for (int j = 0; j < SC_ITEMS; ++j) {
-        if (p0 + j < a.N) {
-            if (a.iperm)
-                a.delta[who[j]] = (uint32_t)run - a.uoff[who[j]];
-            else
-                a.uoff[who[j]] = (uint32_t)run;
-        }
-        run += cnt[j];
     }
 }
 
@@ -803,6 +717,19 @@ struct EntSrc {
         return true;
     }
 };
+// The first transpose pass reads the words in vertex order (as the unique
+// pass wrote them) and puts each row's position in place of its vertex id;
+// the reads of perm follow the ascending vertex ids.
+struct EntSrcPerm {
+    const unsigned long long *e;
+    const uint32_t *perm;
+    uint32_t umask;
+    __device__ __forceinline__ bool load(uint64_t i, unsigned long long &k, uint32_t &) const {
+        const unsigned long long w = e[i];
+        k = (w & ~(unsigned long long)umask) | __ldg(perm + pp_idx((uint32_t)w & umask, umask + 1ull));
+        return true;
+    }
+};
 struct EntDst {
     unsigned long long *e;
     __device__ __forceinline__ void store(uint64_t pos, unsigned long long k, uint32_t) const { e[pos] = k; }
@@ -813,9 +740,8 @@ struct Layout {
     unsigned long long *deg;
     uint32_t *shift;  // vstart: each column's first entry in the sorted words | KILL_BIT
     uint32_t *row_nent;
-    uint32_t *uoff, *delta;
-    uint64_t *uq_status, *sc_status, *off_status;
-    uint32_t *ctr;                // [0] unique, [1] mask scan, [2] vertex-order and [3] position-order offsets, [5] column pointers
+    uint64_t *uq_status, *sc_status;
+    uint32_t *ctr;                // tile counters: [0] unique, [1] mask scan, [5] column pointers
     unsigned long long *dmaxkey;  // follows ctr in one control block
     os::SortWs sort;   // the entry words: bucket pass + column passes
     os::SortWs vsort;  // the vertices by bucket
@@ -823,7 +749,7 @@ struct Layout {
 };
 
 inline int num_passes(uint32_t scale) { return (int)ceil_div(scale, 8u); }
-constexpr int CTR_WORDS = 8;  // tile counters [0..3], [5]; the 8-byte max key at [6..7]
+constexpr int CTR_WORDS = 8;  // tile counters [0], [1], [5]; the 8-byte max key at [6..7]
 
 inline Layout layout(void *ws, uint64_t M, uint32_t scale) {
     Carver c(ws);
@@ -835,11 +761,8 @@ inline Layout layout(void *ws, uint64_t M, uint32_t scale) {
     L.deg = c.take<unsigned long long>(N);
     L.shift = c.take<uint32_t>(N);
     L.row_nent = c.take<uint32_t>(N);
-    L.uoff = c.take<uint32_t>(N);
-    L.delta = c.take<uint32_t>(N);
     L.uq_status = c.take<uint64_t>(ceil_div(cap, UQ_TILE));
     L.sc_status = c.take<uint64_t>(2 * ceil_div(N, SC_TILE));
-    L.off_status = c.take<uint64_t>(2 * ceil_div(N, SC_TILE));
     L.ctr = c.take<uint32_t>(CTR_WORDS);
     L.dmaxkey = L.ctr ? reinterpret_cast<unsigned long long *>(L.ctr + 6) : nullptr;
     L.sort = os::carve_sort_ws(c, cap);
@@ -916,16 +839,23 @@ inline pp_status run(const uint32_t *us, const uint32_t *vs, uint64_t M, uint32_
     cudaMemsetAsync(L.vsort.hist, 0, os::kCtlBytes, s);
     cudaMemsetAsync(L.uq_status, 0, ceil_div(M ? M : 1, k2::UQ_TILE) * sizeof(uint64_t), s);
     cudaMemsetAsync(L.sc_status, 0, 2 * sc_tiles * sizeof(uint64_t), s);
-    cudaMemsetAsync(L.off_status, 0, 2 * sc_tiles * sizeof(uint64_t), s);
     cudaMemsetAsync(L.sort.status[0], 0, ceil_div(M ? M : 1, os::TILE) * os::RADIX * word, s);
 
     const unsigned ngrid = (unsigned)std::min<uint64_t>(ceil_div(N, 256), (uint64_t)sms * 8);
-    const uint32_t umask = N - 1;
     unsigned long long *sorted = L.ent[0];
     if (M) {
-        const unsigned sgrid = (unsigned)std::min<uint64_t>(ceil_div(M, 256 * 16), (uint64_t)sms * 8);
+        // step 1, entries in vertex order, with each row's edges and entries
+        static PerDevice uq_occ_dev;
+        const int uq_occ = (int)uq_occ_dev.get([] {
+            int o = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k2::unique_kernel, k2::UQ_THREADS, 0);
+            return (int64_t)(o < 1 ? 1 : o);
+        });
+        const unsigned ugrid = (unsigned)std::min<uint64_t>(ceil_div(M, k2::UQ_TILE), (uint64_t)sms * uq_occ);
         const int vec = (((uintptr_t)us | (uintptr_t)vs) & 15u) == 0;
-        k2::stats_kernel<<<sgrid, 256, 0, s>>>(us, vs, M, umask, vec, g->d_out, L.row_nent);
+        k2::UniqueArgs ua{us,          vs,         M,  scale, cmax, L.ent[0],    g->ovf_key, g->ovf_cnt, N,
+                          g->d_out, L.row_nent, L.sort.hist, P,   vec,  L.uq_status, L.ctr,      g->info};
+        k2::unique_kernel<<<ugrid, k2::UQ_THREADS, 0, s>>>(ua);
         count_launch();
     }
     // relabel: the vertices by row bucket (one pass), giving perm and iperm
@@ -951,28 +881,11 @@ inline pp_status run(const uint32_t *us, const uint32_t *vs, uint64_t M, uint32_
                                             k2::PermDst64{g->perm, g->iperm, N}, nullptr, N, s, 32u);
     }
     if (M) {
-        // each row's first entry in vertex order, then in position order
-        k2::offsets_kernel<<<(unsigned)sc_tiles, k2::SC_THREADS, 0, s>>>(
-            k2::OffArgs{L.row_nent, nullptr, N, L.uoff, L.delta, L.off_status, L.ctr + 2});
-        k2::offsets_kernel<<<(unsigned)sc_tiles, k2::SC_THREADS, 0, s>>>(
-            k2::OffArgs{L.row_nent, g->iperm, N, L.uoff, L.delta, L.off_status + sc_tiles, L.ctr + 3});
-        count_launch(2);
-        static PerDevice uq_occ_dev;
-        const int uq_occ = (int)uq_occ_dev.get([] {
-            int o = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k2::unique_kernel, k2::UQ_THREADS, 0);
-            return (int64_t)(o < 1 ? 1 : o);
-        });
-        const unsigned ugrid = (unsigned)std::min<uint64_t>(ceil_div(M, k2::UQ_TILE), (uint64_t)sms * uq_occ);
-        const int vec = (((uintptr_t)us | (uintptr_t)vs) & 15u) == 0;
-        k2::UniqueArgs ua{us,    vs,      M,       scale,       cmax, L.ent[0], g->ovf_key,  g->ovf_cnt,
-                          N,     L.delta, g->perm, L.sort.hist, P,    vec,      L.uq_status, L.ctr,
-                          g->info};
-        k2::unique_kernel<<<ugrid, k2::UQ_THREADS, 0, s>>>(ua);
-        count_launch();
         // transpose: every entry sorted by column, P passes over bits 32 .. 32+scale
         const uint64_t *n_dev = g->info + PP_INFO_NNZ0;
-        for (int p = 0; p < P; ++p) {
+        os::launch_pass<unsigned long long>(L.sort, 0, P, k2::EntSrcPerm{L.ent[0], g->perm, N - 1},
+                                            k2::EntDst{L.ent[1]}, n_dev, M, s, 32);
+        for (int p = 1; p < P; ++p) {
             os::launch_pass<unsigned long long>(L.sort, p, P, k2::EntSrc{L.ent[p & 1]},
                                                 k2::EntDst{L.ent[(p + 1) & 1]}, n_dev, M, s, 32);
         }

@@ -12,7 +12,7 @@ hold about 40 GB), and properties that hold at any size:
 - Kernel 2: d_in = sum(A,1) and d_out = sum(A,2) after the filter, the column
   pointers, nnz0, nnz, max(d_in), its lowest column and the tie count, all
   from bincounts of Kernel 1's output, bit for bit; 1/d_out bit for bit; rows
-  strictly ascending inside each column; the (u, v, count) entry set through
+  in strictly ascending vertex order inside each column; the (u, v, count) entry set through
   two independent 64-bit hashes of every entry.
 - Kernel 3: one binary64 step from the GPU's r after 19 iterations to its r
   after 20, recomputed in binary64 for sampled columns (Eq. 1 with the
@@ -143,7 +143,7 @@ def test_k2_structure_bit_exact(fullsize):
     del key, first, kept_edge, kept_entry, starts, runs, sel
     gu, gv, gc, colptr_dev, gpos = _decode_csc(g)
     same_col = gv[1:] == gv[:-1]  # same vertex <=> same column position
-    assert bool((gpos[1:][same_col] > gpos[:-1][same_col]).all()), "row positions not ascending in a column"
+    assert bool((gu[1:][same_col] > gu[:-1][same_col]).all()), "rows not in ascending vertex order in a column"
     assert _hashes(gu, gv, gc, S) == want
     del gu, gv, gc, gpos
     # Kernel 2's row order: by bucket of the edge count before the filter, then id

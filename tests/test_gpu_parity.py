@@ -47,9 +47,10 @@ def check_k2(pp, g, R):
     gu, gv, gc, (cu, cv, colptr) = gpu_triples(g)
     ou, ov, oc = oracle_triples(R)
     assert np.array_equal(gu, ou) and np.array_equal(gv, ov) and np.array_equal(gc, oc)
-    # row positions strictly ascend inside each column (the compressed-column layout)
+    # inside each column the rows' vertex ids strictly ascend (the compressed-column layout)
+    rows = host_u32(g.iperm)[: g.N][cu]
     same_col = cv[1:] == cv[:-1]
-    assert (cu[1:][same_col] > cu[:-1][same_col]).all()
+    assert (rows[1:][same_col] > rows[:-1][same_col]).all()
     d = R["d_out"]
     want32 = np.where(d > 0, np.float32(1) / np.maximum(d, 1).astype(np.float32), np.float32(0))
     want64 = np.where(d > 0, 1.0 / np.maximum(d, 1).astype(np.float64), 0.0)
