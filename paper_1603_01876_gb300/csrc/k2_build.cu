@@ -725,9 +725,11 @@ struct EntSrcPerm {
     const uint32_t *perm;
     uint32_t umask;
     __device__ __forceinline__ bool load(uint64_t i, unsigned long long &k, uint32_t &) const {
-        const unsigned long long w = e[i];
-        k = (w & ~(unsigned long long)umask) | __ldg(perm + pp_idx((uint32_t)w & umask, umask + 1ull));
+        k = e[i];
         return true;
+    }
+    __device__ __forceinline__ unsigned long long map(unsigned long long w) const {
+        return (w & ~(unsigned long long)umask) | __ldg(perm + pp_idx((uint32_t)w & umask, umask + 1ull));
     }
 };
 struct EntDst {

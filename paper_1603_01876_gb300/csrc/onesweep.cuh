@@ -74,6 +74,14 @@ struct has_load4 : std::false_type {};
 template <class S>
 struct has_load4<S, std::void_t<decltype(&S::load4)>> : std::true_type {};
 
+// A source with `map(k)` has each loaded key passed through it once all of a
+// thread's keys are loaded, so that a second, dependent load per key (a
+// table lookup) is issued for all of them together.
+template <class S, class = void>
+struct has_map : std::false_type {};
+template <class S>
+struct has_map<S, std::void_t<decltype(&S::map)>> : std::true_type {};
+
 // Status words are 32-bit while every count fits in 30 bits.
 inline bool wide_status(uint64_t n_max) { return n_max >= (1ull << 30); }
 
@@ -141,6 +149,11 @@ __global__ void __launch_bounds__(THREADS, PASS_MINB) pass_kernel(Src src, Dst d
                 keys[i] = 0;
                 if (i < nv) src.load(base + (uint64_t)i * 32 + lane, keys[i], unused);
             }
+        }
+        if constexpr (has_map<Src>::value) {
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i)
+                if (i < nv) keys[i] = src.map(keys[i]);
         }
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
