@@ -118,7 +118,7 @@ struct UniqueArgs {
     uint32_t *ovf_cnt;
     uint32_t n_vert;          // N
     uint32_t *d_out;          // [N] edges of each row (the out-degree before the filters), zero on entry
-    uint32_t *row_nent;       // [N] entries (distinct (u, v)) of each row, zero on entry
+    uint32_t *row_nent;       // [N] entries (distinct (u, v)) of each row, zero on entry (nullptr: not wanted)
     uint32_t *hist;           // [npasses * 256] column digits, for the transpose
     int npasses;
     int vec;                  // us and vs are 16-byte aligned: load 4 ids at a time
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(UQ_THREADS, 3) unique_kernel(UniqueArgs a) {
                 if (u != row) {
                     if (edges) {
                         atomicAdd(&a.d_out[row], edges);
-                        atomicAdd(&a.row_nent[row], entries);
+                        if (a.row_nent) atomicAdd(&a.row_nent[row], entries);
                     }
                     row = u;
                     edges = entries = 0;
@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(UQ_THREADS, 3) unique_kernel(UniqueArgs a) {
             }
             if (edges) {
                 atomicAdd(&a.d_out[row], edges);
-                atomicAdd(&a.row_nent[row], entries);
+                if (a.row_nent) atomicAdd(&a.row_nent[row], entries);
             }
         }
 
@@ -836,7 +836,7 @@ inline pp_status run(const uint32_t *us, const uint32_t *vs, uint64_t M, uint32_
     cudaMemsetAsync(L.ctr, 0, k2::CTR_WORDS * sizeof(uint32_t), s);
     cudaMemsetAsync(L.deg, 0, (size_t)N * sizeof(unsigned long long), s);
     cudaMemsetAsync(g->d_out, 0, (size_t)N * sizeof(uint32_t), s);
-    cudaMemsetAsync(L.row_nent, 0, (size_t)N * sizeof(uint32_t), s);
+    if (bc) cudaMemsetAsync(L.row_nent, 0, (size_t)N * sizeof(uint32_t), s);  // a batch's per-graph nnz0
     cudaMemsetAsync(L.sort.hist, 0, os::kCtlBytes, s);
     cudaMemsetAsync(L.vsort.hist, 0, os::kCtlBytes, s);
     cudaMemsetAsync(L.uq_status, 0, ceil_div(M ? M : 1, k2::UQ_TILE) * sizeof(uint64_t), s);
@@ -856,7 +856,7 @@ inline pp_status run(const uint32_t *us, const uint32_t *vs, uint64_t M, uint32_
         const unsigned ugrid = (unsigned)std::min<uint64_t>(ceil_div(M, k2::UQ_TILE), (uint64_t)sms * uq_occ);
         const int vec = (((uintptr_t)us | (uintptr_t)vs) & 15u) == 0;
         k2::UniqueArgs ua{us,          vs,         M,  scale, cmax, L.ent[0],    g->ovf_key, g->ovf_cnt, N,
-                          g->d_out, L.row_nent, L.sort.hist, P,   vec,  L.uq_status, L.ctr,      g->info};
+                          g->d_out, bc ? L.row_nent : nullptr, L.sort.hist, P,   vec,  L.uq_status, L.ctr,      g->info};
         k2::unique_kernel<<<ugrid, k2::UQ_THREADS, 0, s>>>(ua);
         count_launch();
     }
