@@ -41,8 +41,8 @@ WORKLOAD = ("Kronecker graph, scale 24 (N=2^24, M=16N=268,435,456 edges, initiat
 # each stage's dominant kernel from one ncu capture (profiles/), valid while
 # its source file is unchanged.
 TRAFFIC = {
-    "k3_pagerank": {"source": "paper_1603_01876_gb300/csrc/k3_pagerank.cu", "sha": "3ad9765f8d47d029",
-                    "bytes_per_launch": 1328332000 + 39151616, "dtype": "fp32", "scale": 24,
+    "k3_pagerank": {"source": "paper_1603_01876_gb300/csrc/k3_pagerank.cu", "sha": "db2b7e9a0668a0ea",
+                    "bytes_per_launch": 1327743000 + 38662912, "dtype": "fp32", "scale": 24,
                     "capture": "profiles/k3_iterate_fp32_scale24.md"},
 }
 
