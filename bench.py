@@ -404,8 +404,8 @@ def run_ours(args):
         per_launch = {"bytes": b3_iter, "ms": iter_ms,
                       "how": "(K3 stage time - same call with 0 iterations) / iterations, CUDA events; bytes: "
                              "4 nnz (packed entries) + 4 N (column ends) + N (x gathered once, 1/d_out, x written) "
-                             "at the stored widths; r itself is written only in the last iteration, so the "
-                             "per-iteration r write of the survey's count is left out"}
+                             "at the stored widths; r itself is written only in the last iteration, so no "
+                             "per-iteration write of r is counted"}
     else:
         kname = "k1 onesweep pass_kernel (8-bit LSD pass)" if dom == "k1_sort" else "k2 stage"
         launches_per_stage = P if dom == "k1_sort" else 1
