@@ -660,12 +660,15 @@ class trace:
 
 def _traced(fn):
     import functools
+    import inspect
+
+    sig = inspect.signature(fn)
 
     @functools.wraps(fn)
     def wrapper(*args, **kwargs):
         if _TRACE is None:
             return fn(*args, **kwargs)
-        stream = kwargs.get("stream") or torch.cuda.current_stream()
+        stream = sig.bind_partial(*args, **kwargs).arguments.get("stream") or torch.cuda.current_stream()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         result = fn(*args, **kwargs)
