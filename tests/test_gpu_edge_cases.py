@@ -132,3 +132,25 @@ def test_out_of_range_id_is_reported(pp):
     pp.sort_edges(u, v, scale)
     assert pp.last_device_error() & pp.DEV_RANGE
     assert pp.last_device_error() == 0  # the word is cleared once read
+
+
+@pytest.mark.parametrize("scale,offset", [(20, 1), (20, 3), (12, 2)])
+def test_unaligned_edge_arrays(pp, oracle_mod, k0, scale, offset):
+    """Kernel 1 reads u and v four ids at a time when both are 16-byte
+    aligned and one at a time otherwise: arrays starting 4, 8 or 12 bytes
+    past an aligned address sort the same as the oracle; so do the outputs
+    written to unaligned places."""
+    import torch
+
+    u, v = k0.edges_host(scale, 77)
+    ud, vd = dev_u32(u), dev_u32(v)
+    bu = torch.empty(len(u) + offset, dtype=torch.int32, device="cuda")
+    bv = torch.empty(len(v) + offset, dtype=torch.int32, device="cuda")
+    bu[offset:].copy_(ud)
+    bv[offset:].copy_(vd)
+    ou = torch.empty(len(u) + 1, dtype=torch.int32, device="cuda")
+    ov = torch.empty(len(v) + 1, dtype=torch.int32, device="cuda")
+    us, vs = pp.sort_edges(bu[offset:], bv[offset:], scale, out=(ou[1:], ov[1:]))
+    ous, ovs = oracle_mod.k1_sort(u, v)
+    assert np.array_equal(host_u32(us), ous) and np.array_equal(host_u32(vs), ovs)
+    assert pp.last_device_error() == 0
