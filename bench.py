@@ -61,22 +61,68 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+
+def _smi_time(ts):
+    """Seconds since the epoch of an nvidia-smi timestamp ("YYYY/MM/DD HH:MM:SS.mmm", local time)."""
+    import datetime
+
+    return datetime.datetime.strptime(ts.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+
+
+def clock_summary(lines, begin=None, end=None, slack=0.05):
+    """Median SM clock, maximum clock and throttle reasons of the samples taken
+    between begin and end (host seconds since the epoch, widened by `slack`
+    for the sampling granularity).  Each line is one nvidia-smi sample:
+    timestamp, index, clocks.sm, clocks.max.sm, power.draw,
+    clocks_event_reasons.active, then the four reasons of REASONS."""
+    rows = []
+    for ln in lines:
+        f = [x.strip() for x in ln.split(",")]
+        if len(f) < 10:
+            continue
+        try:
+            rows.append((_smi_time(f[0]), float(f[2]), float(f[3]), f[6:10]))
+        except ValueError:
+            continue
+    inside = rows
+    if begin is not None and end is not None:
+        inside = [r for r in rows if begin - slack <= r[0] <= end + slack]
+    if not inside:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "samples_outside": len(rows)}
+    reasons = set()
+    for r in inside:
+        for n, val in zip(REASONS, r[3]):
+            if val.lower() == "active":
+                reasons.add(n)
+    return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+            "reasons": sorted(reasons), "samples": len(inside), "samples_outside": len(rows) - len(inside)}
+
+
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """nvidia-smi samples of the SM clock and the throttle reasons, every 50 ms.
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-         "clocks_event_reasons.sw_power_cap")
+    Start it before the warm-up (nvidia-smi takes a moment to begin), call
+    begin() and end() around the timed region, stop() after it; summary()
+    keeps the samples whose nvidia-smi timestamps fall inside the region."""
 
-    def __init__(self, index):
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 50
+
+    def __init__(self, index, exe="nvidia-smi"):
         self.index = index
+        self.exe = exe
         self.proc = None
         self.lines = []
+        self.t_begin = self.t_end = None
 
-    def __enter__(self):
+    def start(self):
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+            self.proc = subprocess.Popen([self.exe, "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -88,8 +134,16 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
-    def __exit__(self, *a):
+    def begin(self):
+        self.t_begin = time.time()
+
+    def end(self):
+        self.t_end = time.time()
+
+    def stop(self):
         if self.proc:
+            # the samples of the region's last moments are written a period later
+            time.sleep(2 * self.PERIOD_MS / 1000.0)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -97,25 +151,17 @@ class ClockSampler:
                 self.proc.kill()
             self.t.join(timeout=5)
 
+    def __enter__(self):
+        self.start()
+        self.begin()
+        return self
+
+    def __exit__(self, *a):
+        self.end()
+        self.stop()
+
     def summary(self):
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
-            except ValueError:
-                continue
-            for n, val in zip(names, f[5:9]):
-                if val.lower() == "active":
-                    reasons.add(n)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return clock_summary(list(self.lines), self.t_begin, self.t_end, slack=self.PERIOD_MS / 1000.0)
 
 
 def dist_env():
@@ -225,20 +271,22 @@ def run_ours(args):
         if ev:
             ev[3].record(stream)
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    err = pp.last_device_error()
-    if err:
-        raise RuntimeError("device error word %#x during warm-up" % err)
-    info = g.info_dict()
+    clocks = ClockSampler(local).start()  # running by the time the timed region starts
+    try:
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        err = pp.last_device_error()
+        if err:
+            raise RuntimeError("device error word %#x during warm-up" % err)
+        info = g.info_dict()
 
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    launches0 = pp.launch_count()
-    with ClockSampler(local) as clocks:
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        launches0 = pp.launch_count()
+        clocks.begin()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
@@ -246,6 +294,9 @@ def run_ours(args):
             step(evs[k])
         t1.record(stream)
         torch.cuda.synchronize()
+        clocks.end()
+    finally:
+        clocks.stop()
     launches = pp.launch_count() - launches0
     total_ms = max_over_ranks(t0.elapsed_time(t1), world, dev)
     if world > 1:
