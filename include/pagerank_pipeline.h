@@ -420,7 +420,9 @@ pp_status pp_parse_tsv(const char *text, uint64_t text_len, uint32_t *u, uint32_
  * M >= 2^20 the edge list crosses in four chunks and Kernel 1 sorts each
  * chunk as soon as it has arrived, then merges the sorted chunks (the result
  * is the sort pp_sort_edges gives); r0, which only Kernel 3 reads, is copied
- * while Kernels 1 and 2 compute.
+ * while Kernels 1 and 2 compute.  On an error return, the copies already
+ * enqueued on the side stream are ordered before later work on `stream`, so
+ * the workspace may be reused on `stream` (or freed) right away.
  */
 pp_status pp_pipeline_workspace(uint64_t M, uint32_t scale, uint32_t iters, pp_dtype dtype,
                                 size_t *bytes);

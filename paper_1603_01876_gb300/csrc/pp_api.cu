@@ -334,39 +334,50 @@ extern "C" pp_status pp_pipeline_host(const uint32_t *u_host, const uint32_t *v_
     // only Kernel 3 reads, while Kernels 1 and 2 compute.  The side stream and
     // its events are released once their work is done.
     SideCopy side;
-    const bool split_copy = chunked(M, scale) && side.open(s);
-    if (split_copy) {
-        st = sort_chunked(L, u_host, v_host, M, scale, side, s);
-        if (st != PP_OK) return st;
-    } else {
-        if (M) {
-            if (cudaMemcpyAsync(L.u, u_host, M * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) return PP_ERR_CUDA;
-            if (cudaMemcpyAsync(L.v, v_host, M * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) return PP_ERR_CUDA;
+    const pp_status result = [&]() -> pp_status {
+        const bool split_copy = chunked(M, scale) && side.open(s);
+        if (split_copy) {
+            st = sort_chunked(L, u_host, v_host, M, scale, side, s);
+            if (st != PP_OK) return st;
+        } else {
+            if (M) {
+                if (cudaMemcpyAsync(L.u, u_host, M * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) return PP_ERR_CUDA;
+                if (cudaMemcpyAsync(L.v, v_host, M * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) return PP_ERR_CUDA;
+            }
+            side.open(s);  // after the edge copies, which the r0 copy would only slow down on the host link
         }
-        side.open(s);  // after the edge copies, which the r0 copy would only slow down on the host link
-    }
-    const cudaEvent_t r0_done = side.stream ? side.done[CHUNKS] : nullptr;
-    if (r0_done) {
-        if (cudaMemcpyAsync(L.r0, r0_host, N * 8, cudaMemcpyHostToDevice, side.stream) != cudaSuccess) return PP_ERR_CUDA;
-        if (cudaEventRecord(r0_done, side.stream) != cudaSuccess) return PP_ERR_CUDA;
-    } else if (cudaMemcpyAsync(L.r0, r0_host, N * 8, cudaMemcpyHostToDevice, s) != cudaSuccess) {
-        return PP_ERR_CUDA;
-    }
-    if (!split_copy) {
-        st = pp_sort_edges(L.u, L.v, M, scale, L.us, L.vs, L.scratch, L.scratch_bytes, stream);
+        const cudaEvent_t r0_done = side.stream ? side.done[CHUNKS] : nullptr;
+        if (r0_done) {
+            if (cudaMemcpyAsync(L.r0, r0_host, N * 8, cudaMemcpyHostToDevice, side.stream) != cudaSuccess)
+                return PP_ERR_CUDA;
+            if (cudaEventRecord(r0_done, side.stream) != cudaSuccess) return PP_ERR_CUDA;
+        } else if (cudaMemcpyAsync(L.r0, r0_host, N * 8, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+            return PP_ERR_CUDA;
+        }
+        if (!split_copy) {
+            st = pp_sort_edges(L.u, L.v, M, scale, L.us, L.vs, L.scratch, L.scratch_bytes, stream);
+            if (st != PP_OK) return st;
+        }
+        st = pp_build_filter_normalize(L.us, L.vs, M, scale, rule, &L.g, L.scratch, L.scratch_bytes, stream);
         if (st != PP_OK) return st;
+        if (r0_done && cudaStreamWaitEvent(s, r0_done, 0) != cudaSuccess) return PP_ERR_CUDA;
+        st = pp_pagerank(&L.g, L.r0, iters, c, dt, L.r_out, nullptr, L.scratch, L.scratch_bytes, stream);
+        if (st != PP_OK) return st;
+        if (cudaMemcpyAsync(r_out_host, L.r_out, N * (dt == PP_FP64 ? 8 : 4), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return PP_ERR_CUDA;
+        if (info_host &&
+            cudaMemcpyAsync(info_host, L.g.info, PP_INFO_LEN * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return PP_ERR_CUDA;
+        return PP_OK;
+    }();
+    if (result != PP_OK && side.stream) {
+        // On an error the main stream may not have waited for every copy on
+        // the side stream; those copies write into the caller's workspace, so
+        // they are ordered before whatever the caller enqueues on `stream` next.
+        if (cudaEventRecord(side.start, side.stream) == cudaSuccess) cudaStreamWaitEvent(s, side.start, 0);
+        cudaGetLastError();
     }
-    st = pp_build_filter_normalize(L.us, L.vs, M, scale, rule, &L.g, L.scratch, L.scratch_bytes, stream);
-    if (st != PP_OK) return st;
-    if (r0_done && cudaStreamWaitEvent(s, r0_done, 0) != cudaSuccess) return PP_ERR_CUDA;
-    st = pp_pagerank(&L.g, L.r0, iters, c, dt, L.r_out, nullptr, L.scratch, L.scratch_bytes, stream);
-    if (st != PP_OK) return st;
-    if (cudaMemcpyAsync(r_out_host, L.r_out, N * (dt == PP_FP64 ? 8 : 4), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        return PP_ERR_CUDA;
-    if (info_host &&
-        cudaMemcpyAsync(info_host, L.g.info, PP_INFO_LEN * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        return PP_ERR_CUDA;
-    return PP_OK;
+    return result;
 }
 
 // ---------------------------------------------------------------------------
