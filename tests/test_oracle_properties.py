@@ -86,3 +86,51 @@ def test_k3_dangling_is_the_stochastic_matrix(O, g, c, iters, rseed):
     assert done == iters
     assert np.abs(got - want).sum() <= 1e-13 * np.abs(want).sum()
     assert abs(got.sum() - 1.0) <= 1e-13
+
+
+def _ref_parse(text):
+    """The edge-file grammar written out: one "digits<TAB>digits" per line,
+    each field 1-10 digits and at most 2^32-1, a line (with its newline) at
+    most 22 bytes, the text ending with a newline; a malformed line reads as
+    (0, 0)."""
+    lines = text.split(b"\n")
+    bad = lines[-1] != b""
+    out = []
+    for ln in lines[:-1]:
+        parts = ln.split(b"\t")
+        ok = (len(ln) + 1 <= 22 and len(parts) == 2
+              and all(p and p.isdigit() and len(p) <= 10 and int(p) <= 2**32 - 1 for p in parts))
+        bad |= not ok
+        out.append((int(parts[0]), int(parts[1])) if ok else (0, 0))
+    return out, bad
+
+
+_field = st.one_of(st.integers(0, 2**32 - 1).map(lambda x: b"%d" % x),
+                   st.text(alphabet="0123456789", min_size=0, max_size=12).map(str.encode),
+                   st.text(alphabet="0123456789 +-a\t", min_size=0, max_size=6).map(str.encode))
+_line = st.one_of(st.tuples(st.integers(0, 2**32 - 1), st.integers(0, 2**32 - 1)).map(lambda t: b"%d\t%d" % t),
+                  st.tuples(_field, _field).map(lambda t: t[0] + b"\t" + t[1]),
+                  _field)
+
+
+@SETTINGS
+@given(lines=st.lists(_line, max_size=40), tail=st.booleans(), room=st.integers(0, 45))
+def test_parse_tsv_is_the_grammar(O, lines, tail, room):
+    text = b"\n".join(lines) + (b"\n" if lines and tail else b"")
+    want, want_bad = _ref_parse(text)
+    u, v, m, bad = O.parse_tsv(text, cap=room)
+    assert m == len(want)
+    assert bad == (want_bad or len(want) > room)
+    k = min(m, room)
+    assert list(zip(u[:k].tolist(), v[:k].tolist())) == want[:k]
+
+
+@SETTINGS
+@given(edges=st.lists(st.tuples(st.integers(0, 2**32 - 1), st.integers(0, 2**32 - 1)), max_size=200))
+def test_format_tsv_is_pythons_decimal(O, edges):
+    u = np.array([a for a, _ in edges], dtype=np.uint32)
+    v = np.array([b for _, b in edges], dtype=np.uint32)
+    text = O.format_tsv(u, v)
+    assert text == b"".join(b"%d\t%d\n" % e for e in edges)
+    pu, pv, m, bad = O.parse_tsv(text)
+    assert not bad and m == len(edges) and pu.tolist() == u.tolist() and pv.tolist() == v.tolist()
