@@ -1,5 +1,5 @@
 """The row-decomposed form of Kernels 1-3 (paper_1603_01876_gb300.parallel)
-with two gloo ranks on the CPU, against the oracle's single-rank pipeline:
+with two or three gloo ranks on the CPU (three: ragged row ranges), against the oracle's single-rank pipeline:
 the ranks' sorted edges one after the other equal Kernel 1's output, every
 rank's rows of the filtered A and the global in-degree equal Kernel 2's, and
 the ranks one after the other equal Kernel 3's within 1e-12 (binary64).  The
@@ -49,13 +49,13 @@ def _rank_main(rank, world, port, rule, q):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("rule", ["lowest", "all_ties"])
-def test_two_ranks_equal_the_single_rank_pipeline(oracle_mod, k0, rule):
+@pytest.mark.parametrize("world,rule", [(2, "lowest"), (2, "all_ties"), (3, "lowest")])
+def test_ranks_equal_the_single_rank_pipeline(oracle_mod, k0, world, rule):
     pytest.importorskip("torch.distributed")
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, rule, q)) for r in range(2)]
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, rule, q)) for r in range(world)]
     for p in procs:
         p.start()
     out = sorted((q.get(timeout=300) for _ in procs), key=lambda t: t[0])
@@ -74,7 +74,7 @@ def test_two_ranks_equal_the_single_rank_pipeline(oracle_mod, k0, rule):
     rowptr = R["rowptr"].astype(np.int64)
     for rank, _, _, d_in, g, _ in out:
         assert np.array_equal(d_in.astype(np.uint32), R["d_in"])
-        lo, hi = rank * N // 2, (rank + 1) * N // 2
+        lo, hi = rank * N // world, (rank + 1) * N // world
         e0, e1 = rowptr[lo], rowptr[hi]
         o = np.lexsort((g["v"], g["u"]))
         assert np.array_equal(g["u"][o], np.repeat(np.arange(lo, hi), np.diff(rowptr[lo:hi + 1])))
